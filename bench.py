@@ -1,0 +1,427 @@
+#!/usr/bin/env python3
+"""Benchmark: text GB/s per pattern of the SIMD-naive search on GB300.
+
+Default workload (the paper-method sweep at n = 1 GiB): texts of 2^30 bytes,
+i.i.d. uniform over sigma in {2, 4, 20, 64} plus English-like Markov text over
+95 printable bytes; pattern lengths m in {2, 4, 8, ..., 1024}; 100 patterns per
+(sigma, m) copied from the text at seeded offsets; count and report variants.
+
+One step = the whole hot path over the sweep: the byte histogram of each
+text, the rarest-first order of each pattern, and one count plus one report
+per pattern. value = text bytes scanned per second over all searches
+(n bytes per search). Inputs (1 GiB each) are larger than L2, so no flush is
+needed between iterations.
+
+Timing: W untimed warm-up steps, then K steps bracketed by a barrier and
+torch.cuda.synchronize(), CUDA events on the launching stream, max over ranks.
+With --gpus N > 1 (torchrun) each rank searches its own patterns on its own
+GPU with no collective on the data path (weak scaling).
+
+--impl reference times the CPU oracle (plain Algorithm 1, threaded over the
+host cores) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+KINDS_DEFAULT = "2,4,20,64,markov95"
+MS_DEFAULT = "2,4,8,16,32,64,128,256,512,1024"
+METRIC = "text GB/s per pattern (count+report sweep, n=1 GiB)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=1 << 30)
+    ap.add_argument("--kinds", default=KINDS_DEFAULT)
+    ap.add_argument("--ms", default=MS_DEFAULT)
+    ap.add_argument("--patterns", type=int, default=100)
+    ap.add_argument("--variants", default="count,report")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--json-detail", default="")
+    return ap.parse_args()
+
+
+def kinds_of(s):
+    return [k if k == "markov95" else int(k) for k in s.split(",") if k]
+
+
+# ---------------------------------------------------------------- distributed
+
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.proc, self.lines = index, None, []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- workload
+
+def make_workload(args, rank):
+    from paper_1612_01506_gb300 import synth
+    kinds, ms = kinds_of(args.kinds), [int(x) for x in args.ms.split(",") if x]
+    texts, pats = {}, {}
+    for kind in kinds:
+        t = np.empty(args.n, dtype=np.uint8)
+        synth.text(kind, args.n, seed=0, stream=synth.stream_id("sweep", kind), out=t)
+        texts[kind] = t
+        for m in ms:
+            pats[(kind, m)] = synth.sample_patterns(t, m, args.patterns, seed=rank,
+                                                    stream=synth.stream_id("pat", kind, m))
+    return kinds, ms, texts, pats
+
+
+def peak_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_gpu(args, world, rank, local):
+    import torch
+    from paper_1612_01506_gb300 import sm
+
+    kinds, ms, texts, pats = make_workload(args, rank)
+    variants = [v for v in args.variants.split(",") if v]
+    dev = torch.device("cuda", local)
+    ctx = sm.sm_create(local)
+    stream = torch.cuda.current_stream()
+    d_texts = {k: torch.from_numpy(texts[k]).to(dev) for k in kinds}
+    counts = torch.zeros(len(ms) * args.patterns * 2 + 8, dtype=torch.int64, device=dev)
+    max_cap = args.n  # any report fits: count <= n - m + 1
+    d_pos = torch.empty(max_cap, dtype=torch.int64, device=dev) if "report" in variants else None
+    hist_dev = torch.empty((len(kinds), 256), dtype=torch.int64, device=dev)
+
+    # host-side order and histogram are computed once per text outside timing,
+    # and again inside every step (a2 is part of the step)
+    hists = {}
+    for i, k in enumerate(kinds):
+        sm.sm_histogram(ctx, d_texts[k], out=hist_dev[i])
+    torch.cuda.synchronize()
+    for i, k in enumerate(kinds):
+        hists[k] = hist_dev[i].cpu().numpy().view(np.uint64).copy()
+
+    ev_count = []   # (start, end) events around each count launch of the timed steps
+    launches = {"n": 0}
+
+    def step(timed: bool, text_map):
+        per = {}
+        for i, k in enumerate(kinds):
+            sm.sm_histogram(ctx, text_map[k], out=hist_dev[i])
+            launches["n"] += 1
+            h = hists[k]
+            for m in ms:
+                slot = 0
+                e0 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for p in pats[(k, m)]:
+                    pi = sm.sm_order(p, h)
+                    if "count" in variants:
+                        if timed:
+                            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                            a.record(stream)
+                        sm.sm_count(ctx, text_map[k], p, pi=pi, hist=h, out=counts[slot:slot + 1])
+                        launches["n"] += 1
+                        if timed:
+                            b.record(stream)
+                            ev_count.append((a, b))
+                    slot += 1
+                    if "report" in variants:
+                        sm.sm_report(ctx, text_map[k], p, max_cap, pi=pi, hist=h, out_pos=d_pos,
+                                     out_count=counts[slot:slot + 1])
+                        launches["n"] += 2
+                    slot += 1
+                e1 = torch.cuda.Event(enable_timing=True)
+                e1.record(stream)
+                per[(k, m)] = (e0, e1)
+        return per
+
+    for _ in range(args.warmup):
+        step(False, d_texts)
+    if sm.sm_sync(ctx) != sm.SM_OK:
+        raise RuntimeError("deferred device status after warm-up")
+    launches["n"] = 0
+    ev_count.clear()
+
+    barrier(world)
+    torch.cuda.synchronize()
+    per_steps = []
+    with ClockSampler(local) as clk:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            per_steps.append(step(True, d_texts))
+        t1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    elapsed = t0.elapsed_time(t1) / 1e3
+    elapsed = max_over_ranks(elapsed, world)
+    st = sm.sm_sync(ctx)
+    if st != sm.SM_OK:
+        raise RuntimeError(f"deferred device status {st} in timed region")
+
+    searches_per_step = len(kinds) * len(ms) * args.patterns * len(variants)
+    bytes_per_step = searches_per_step * args.n
+    value = world * bytes_per_step * args.steps / elapsed / 1e9
+
+    # per-(sigma, m) breakdown from the events of the timed steps (GB/s)
+    detail = {}
+    for (k, m), _ in per_steps[0].items():
+        ts = [ps[(k, m)][0].elapsed_time(ps[(k, m)][1]) / 1e3 for ps in per_steps]
+        detail[f"{k}/m{m}"] = round(args.patterns * len(variants) * args.n / statistics.median(ts) / 1e9, 1)
+
+    # roofline of the count scan kernel: n algorithmic bytes per launch
+    durs = [a.elapsed_time(b) / 1e3 for a, b in ev_count]
+    peak, peak_kind = peak_gbs()
+    roof = None
+    if durs:
+        avg = sum(durs) / len(durs)
+        achieved = args.n / avg / 1e9
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_kind,
+                "kernel": "scan_kernel<count>", "launches": len(durs)}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, ctx, kinds, ms, pats, hists, texts, dev, stream, d_texts, variants, world)
+
+    return {"value": value, "elapsed": elapsed, "bytes_per_step": bytes_per_step, "detail": detail,
+            "roofline": roof, "clocks": clk.summary(), "e2e": e2e, "launches": launches["n"],
+            "searches_per_step": searches_per_step}
+
+
+def run_e2e(args, ctx, kinds, ms, pats, hists, texts, dev, stream, d_texts, variants, world):
+    """Same sweep through the public API from pinned host texts: every step
+    copies each text host->device, searches, and reads the counts back."""
+    import torch
+    from paper_1612_01506_gb300 import sm
+    pinned = {k: torch.from_numpy(texts[k]).pin_memory() for k in kinds}
+    counts = torch.zeros(len(ms) * args.patterns * 2, dtype=torch.int64, device=dev)
+    host_counts = torch.zeros_like(counts, device="cpu").pin_memory()
+    d_pos = torch.empty(args.n, dtype=torch.int64, device=dev) if "report" in variants else None
+    h2d = d2h = 0
+
+    def one():
+        nonlocal h2d, d2h
+        for k in kinds:
+            d_texts[k].copy_(pinned[k], non_blocking=True)
+            h2d += args.n
+            h = sm.sm_histogram(ctx, d_texts[k]).cpu().numpy().view(np.uint64)
+            d2h += 256 * 8
+            slot = 0
+            for m in ms:
+                for p in pats[(k, m)]:
+                    pi = sm.sm_order(p, h)
+                    if "count" in variants:
+                        sm.sm_count(ctx, d_texts[k], p, pi=pi, hist=h, out=counts[slot:slot + 1])
+                    slot += 1
+                    if "report" in variants:
+                        sm.sm_report(ctx, d_texts[k], p, args.n, pi=pi, hist=h, out_pos=d_pos,
+                                     out_count=counts[slot:slot + 1])
+                    slot += 1
+                host_counts.copy_(counts, non_blocking=True)
+                d2h += counts.numel() * 8
+            torch.cuda.synchronize()
+
+    one()   # warm-up
+    h2d = d2h = 0
+    steps = max(1, min(args.steps, 2))
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one()
+    torch.cuda.synchronize()
+    el = max_over_ranks(time.perf_counter() - t0, world)
+    bytes_scanned = len(kinds) * len(ms) * args.patterns * len(variants) * args.n * steps * world
+    return {"value": round(bytes_scanned / el / 1e9, 1), "unit": "GB/s",
+            "h2d_bytes_per_step": h2d // steps, "d2h_bytes_per_step": d2h // steps}
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def run_cpu_baseline(args, budget_s: float):
+    """The oracle (Algorithm 1, threaded over the host cores) on a bounded
+    sample of the sweep: a 64 MiB prefix of each text, up to 3 patterns per
+    (sigma, m), until the time budget is spent."""
+    import oracle
+    from paper_1612_01506_gb300 import synth
+    kinds, ms = kinds_of(args.kinds), [int(x) for x in args.ms.split(",") if x]
+    cores = os.cpu_count() or 1
+    sample_n = min(args.n, 64 << 20)
+    scanned, spent, searches = 0, 0.0, 0
+    order = [(k, m) for m in ms for k in kinds]
+    texts = {k: synth.text(k, sample_n, seed=0, stream=synth.stream_id("sweep", k)) for k in kinds}
+    for rep in range(3):
+        for k, m in order:
+            if spent >= budget_s:
+                break
+            p = synth.sample_patterns(texts[k], m, 3, seed=0, stream=synth.stream_id("pat", k, m))[rep]
+            t0 = time.perf_counter()
+            oracle.count_threads(p, texts[k], cores)
+            spent += time.perf_counter() - t0
+            scanned += sample_n
+            searches += 1
+    return {"value": round(scanned / spent / 1e9, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "sample": f"{searches} counts over 64 MiB prefixes of the sweep texts "
+                      f"(sigma {args.kinds}; m {args.ms}), {spent:.1f} s"}
+
+
+# ---------------------------------------------------------------- main
+
+def config_block(args, world):
+    return {"workload": f"sweep n={args.n} bytes: sigma {args.kinds} x m {args.ms} x {args.patterns} "
+                        f"patterns from the text, {args.variants}",
+            "n": args.n, "kinds": args.kinds, "ms": args.ms, "patterns": args.patterns,
+            "variants": args.variants, "l2": "inputs larger than L2 (1 GiB texts), no flush",
+            "parallelism": f"weak: {world} rank(s), independent patterns per rank"}
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        budget = max(5.0, min(60.0, args.cpu_seconds))
+        vals = []
+        for _ in range(max(args.warmup, 0)):
+            run_cpu_baseline(args, 1.0)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            vals.append(run_cpu_baseline(args, budget / max(args.steps, 1)))
+        el = time.perf_counter() - t0
+        v = statistics.median([x["value"] for x in vals])
+        line = {"metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": 0, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": round(el / max(args.steps, 1) * 1e3, 1),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+                "data": "synthetic", "config": config_block(args, 1), "impl": "reference",
+                "cpu_baseline": vals[-1], "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0,
+                                                  "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    res = run_gpu(args, world, rank, local)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = run_cpu_baseline(args, args.cpu_seconds)
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(res["value"], 1), "unit": "GB/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(res["elapsed"] / args.steps * 1e3, 2), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+                "config": config_block(args, world), "roofline": res["roofline"], "cpu_baseline": cpu,
+                "e2e": res["e2e"], "gpu_launches": res["launches"], "clocks": res["clocks"]}
+        print(json.dumps(line), flush=True)
+        if args.json_detail:
+            with open(args.json_detail, "w") as f:
+                json.dump({"line": line, "detail_gbs": res["detail"]}, f, indent=1)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

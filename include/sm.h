@@ -1,0 +1,193 @@
+/*
+ * sm.h - exact string matching on the GPU: the SIMD-naive counting search
+ * of Tarhio, Holub and Giaquinta, "Technology Beats Algorithms (in Exact
+ * String Matching)", re-designed for NVIDIA GB300 (sm_103a).
+ *
+ * Problem (Sec. 1): count or report every location of a pattern p of length
+ * m in a text t of length n. Symbols are bytes compared as unsigned values
+ * (0x00 and 0xFF are ordinary symbols). Locations are 0-based start
+ * positions s with t[s .. s+m-1] = p[0 .. m-1]; the paper counts from 1.
+ * Overlapping occurrences all count (Algorithm 1 tests every start).
+ *
+ * Conventions shared by every call
+ *   - Pointers prefixed d_ are device memory of the context's device, h_ are
+ *     host memory. The caller owns all of them; the library never frees or
+ *     keeps them after the call returns, and never reads t outside
+ *     t[0 .. n-1]. The text may start at any byte address and have any length.
+ *   - Calls that take a stream are asynchronous: they validate arguments on
+ *     the host, enqueue work on the stream and return. Results are valid once
+ *     the stream has reached that point. Device-side conditions found later
+ *     (a truncated report, an expired bounded wait) are recorded in the
+ *     context and returned by sm_sync().
+ *   - A context owns the library's device workspace. Work from one context
+ *     must be ordered on one stream at a time; give each concurrent stream
+ *     its own context.
+ *   - Calls return a status and never abort or throw. sm_last_error() gives a
+ *     message for the last failure on the calling thread.
+ *   - m = 0 is SM_EINVAL. m > n (including n = 0) is not an error: the count
+ *     is 0, no kernel is launched, and *d_count is still written.
+ *   - m may be at most SM_MAX_M.
+ */
+#ifndef SM_H
+#define SM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A CUDA stream (cudaStream_t / CUstream); NULL is the legacy default stream. */
+struct CUstream_st;
+typedef struct CUstream_st* sm_stream_t;
+
+typedef enum sm_status {
+    SM_OK = 0,
+    SM_EINVAL = 1,    /* invalid argument; nothing was enqueued */
+    SM_ENOMEM = 2,    /* workspace allocation failed */
+    SM_ECUDA = 3,     /* a CUDA runtime call failed (message in sm_last_error) */
+    SM_ETRUNC = 4,    /* from sm_sync: a report had more matches than its capacity */
+    SM_ETIMEOUT = 5,  /* from sm_sync: a bounded device wait expired */
+    SM_ENOTSUP = 6    /* request outside what this build supports */
+} sm_status;
+
+#define SM_MAX_M 4096u          /* longest pattern accepted */
+#define SM_TILE_STARTS 8192u    /* start positions per scan tile */
+
+typedef struct sm_ctx sm_ctx;
+
+/* Create a context on CUDA device `device`; *ctx is NULL on failure. */
+sm_status sm_create(sm_ctx** ctx, int device);
+
+/* Release a context and its workspace. Waits for the device first. NULL is a no-op. */
+void sm_destroy(sm_ctx* ctx);
+
+/* Message for the last failing call on this thread ("" if none). Owned by the library. */
+const char* sm_last_error(void);
+
+/* Name of a status code. */
+const char* sm_status_string(sm_status s);
+
+/*
+ * Wait until `stream` has finished the work enqueued so far, then return and
+ * clear the context's deferred device status: SM_ETRUNC if a report since the
+ * last sm_sync had count > cap, SM_ETIMEOUT if a bounded device wait expired,
+ * SM_ECUDA if the stream reported an error, else SM_OK.
+ */
+sm_status sm_sync(sm_ctx* ctx, sm_stream_t stream);
+
+/*
+ * Tuning and test knobs of a context (they change speed, never results).
+ *   SM_KNOB_STAGES        shared-memory pipeline depth of the scan, 2..8 (default 4)
+ *   SM_KNOB_GRID          scan CTAs; 0 = one wave of resident CTAs (default)
+ *   SM_KNOB_SPIN_NS       limit of every bounded device wait, ns (default 1e9)
+ *   SM_KNOB_TEST_SKIP_COPY  test hook: 1 = the scan never starts the copy of
+ *                         tile 0, so its bounded wait expires and sm_sync
+ *                         reports SM_ETIMEOUT (results are then invalid)
+ */
+typedef enum sm_knob {
+    SM_KNOB_STAGES = 1,
+    SM_KNOB_GRID = 2,
+    SM_KNOB_SPIN_NS = 3,
+    SM_KNOB_TEST_SKIP_COPY = 4
+} sm_knob;
+sm_status sm_set_knob(sm_ctx* ctx, sm_knob knob, int64_t value);
+
+/* ------------------------------------------------------------------ a1 */
+/*
+ * Byte histogram of the text: d_hist256[c] = #{x < n : t[x] = c}, c = 0..255.
+ * Sec. 2.2 orders compares by symbol frequency; this build takes the
+ * frequencies from the searched text itself (computed once per text).
+ *   d_text     n bytes, device, any alignment (NULL allowed only when n = 0)
+ *   d_hist256  256 x uint64, device; overwritten (not accumulated)
+ */
+sm_status sm_histogram(sm_ctx* ctx, const uint8_t* d_text, uint64_t n,
+                       uint64_t* d_hist256, sm_stream_t stream);
+
+/* ------------------------------------------------------------------ a2 */
+/*
+ * Rarest-first comparison order (Sec. 2.2, Algorithm 3): h_pi[0..m-1] is the
+ * permutation of pattern positions 0..m-1 sorted by h_hist256[p[q]]
+ * ascending, equal frequencies in ascending position. O(m log m) on the host
+ * (Sec. 2.2); synchronous, needs no context or device.
+ *   h_pat      m bytes, host;  h_hist256  256 x uint64, host;
+ *   h_pi       m x uint32, host, written.
+ */
+sm_status sm_order(const uint8_t* h_pat, uint32_t m, const uint64_t* h_hist256,
+                   uint32_t* h_pi);
+
+/*
+ * Fixed comparison orders of Sec. 2.4, needing no frequencies:
+ *   mode SM_ORDER_H : pi_h  = p[1], p[m], p[4], p[7], ..., p[3], p[6], ...,
+ *                             p[2], p[5], ... (1-based, each position once)
+ *   mode SM_ORDER_HS: pi_hs = pi_h applied to the positions that do not hold
+ *                             a space (0x20), then the space positions in
+ *                             ascending order.
+ * Synchronous, host only. h_pat may be NULL for SM_ORDER_H.
+ */
+#define SM_ORDER_H 1
+#define SM_ORDER_HS 2
+sm_status sm_order_fixed(const uint8_t* h_pat, uint32_t m, int mode, uint32_t* h_pi);
+
+/* ------------------------------------------------------------ a3 - a7 */
+/*
+ * Options for one search; NULL selects the defaults.
+ *   peel       peeling factor r of Sec. 2.3 (Algorithm 4): the first r
+ *              compares of every group of starts run without the zero test.
+ *              0 = choose automatically. Clamped to m. Does not change the
+ *              result.
+ *   h_hist256  optional host histogram of THIS text (from sm_histogram). When
+ *              given, it selects the automatic peel, allows a faster compare
+ *              when the text has no byte >= 0x80, and returns a zero count
+ *              without scanning when some pattern symbol never occurs in the
+ *              text. A histogram that does not belong to the text gives
+ *              undefined results.
+ */
+typedef struct sm_search_opts {
+    uint32_t peel;
+    uint32_t reserved;
+    const uint64_t* h_hist256;
+} sm_search_opts;
+
+/*
+ * Count the occurrences of p in t (Algorithms 2-4): *d_count =
+ * #{s in [0, n-m] : t[s .. s+m-1] = p}. The scan compares pattern positions
+ * in the order h_pi (NULL = positions 0..m-1), which never changes the count.
+ *   d_text   n bytes, device, any alignment
+ *   h_pat    m bytes, host;  h_pi  m x uint32 permutation of 0..m-1 or NULL
+ *   d_count  1 x uint64, device; overwritten
+ * Errors: SM_EINVAL for NULL pointers, m = 0, m > SM_MAX_M or an h_pi that
+ * is not a permutation.
+ */
+sm_status sm_count(sm_ctx* ctx, const uint8_t* d_text, uint64_t n,
+                   const uint8_t* h_pat, uint32_t m, const uint32_t* h_pi,
+                   uint64_t* d_count, sm_stream_t stream);
+
+sm_status sm_count_ex(sm_ctx* ctx, const uint8_t* d_text, uint64_t n,
+                      const uint8_t* h_pat, uint32_t m, const uint32_t* h_pi,
+                      const sm_search_opts* opts, uint64_t* d_count, sm_stream_t stream);
+
+/* ------------------------------------------------------------------ a8 */
+/*
+ * Report the occurrences (the reporting version of Algorithm 1, Sec. 2.1):
+ * d_pos[0 .. min(count, cap)-1] receives the first min(count, cap) start
+ * positions in ascending order and *d_count the full count. When
+ * count > cap the extra positions are dropped and the next sm_sync on this
+ * context returns SM_ETRUNC.
+ *   d_pos  cap x uint64, device (may be NULL when cap = 0)
+ * Other arguments and errors as sm_count.
+ */
+sm_status sm_report(sm_ctx* ctx, const uint8_t* d_text, uint64_t n,
+                    const uint8_t* h_pat, uint32_t m, const uint32_t* h_pi,
+                    uint64_t* d_pos, uint64_t cap, uint64_t* d_count, sm_stream_t stream);
+
+sm_status sm_report_ex(sm_ctx* ctx, const uint8_t* d_text, uint64_t n,
+                       const uint8_t* h_pat, uint32_t m, const uint32_t* h_pi,
+                       const sm_search_opts* opts, uint64_t* d_pos, uint64_t cap,
+                       uint64_t* d_count, sm_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SM_H */

@@ -27,18 +27,19 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import platform
 import subprocess
 
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
-_OUT_DIR = os.path.join(_HERE, "_build")
+_OUT_DIR = os.path.join(_HERE, "_build", platform.machine())
 _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into oracle/_build/liboracle.so with gcc."""
+    """Compile oracle.c into oracle/_build/<machine>/liboracle.so with gcc."""
     os.makedirs(_OUT_DIR, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"

@@ -1,0 +1,423 @@
+// Host runtime and C ABI of the GPU string-matching library (include/sm.h).
+//
+// Validates arguments, owns the per-context device workspace (status word,
+// last-CTA ticket, per-CTA partial counts, per-tile counts for reports),
+// plans the scan grid, chooses the kernel variant and launches. Everything
+// the search computes happens in the kernels of sm_kernels.cu; the host only
+// computes the comparison order (Sec. 2.2 / 2.4 of Tarhio, Holub, Giaquinta),
+// which the paper also builds on the host before searching.
+#include "sm.h"
+#include "sm_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+struct sm_ctx {
+    int device = 0;
+    int num_sms = 0;
+    size_t max_smem = 0;
+    uint32_t* d_status = nullptr;
+    uint32_t* h_status = nullptr;     // pinned mirror for sm_sync
+    uint32_t* d_ticket = nullptr;
+    uint64_t* d_partials = nullptr;
+    size_t partials_cap = 0;          // entries
+    uint32_t* d_tile_counts = nullptr;
+    size_t tile_counts_cap = 0;       // entries
+    uint32_t stages = 4;
+    uint32_t grid_override = 0;
+    uint64_t spin_ns = 1000000000ull;
+    uint32_t test_skip_copy = 0;
+    int occ_cache[3][2][2] = {};      // [mode][seven][large m] CTAs per SM at default smem
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+sm_status fail(sm_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+sm_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(SM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool fault_alloc() {
+    const char* f = std::getenv("SM_FAULT");
+    return f && std::strcmp(f, "alloc") == 0;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = (prev == dev) || cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+template <class T>
+sm_status grow(T** p, size_t* cap, size_t want, const char* what) {
+    if (*cap >= want) return SM_OK;
+    size_t n = std::max<size_t>(want, *cap * 2);
+    if (fault_alloc()) return fail(SM_ENOMEM, "injected allocation failure (%s)", what);
+    if (*p) {
+        cudaFree(*p);   // synchronizes with the device: no launch still uses it
+        *p = nullptr;
+        *cap = 0;
+    }
+    if (cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SM_ENOMEM, "cudaMalloc of %zu bytes for %s failed", n * sizeof(T), what);
+    }
+    *cap = n;
+    return SM_OK;
+}
+
+sm_status check_pattern(const uint8_t* h_pat, uint32_t m, const uint32_t* h_pi) {
+    if (m == 0) return fail(SM_EINVAL, "pattern length m must be at least 1");
+    if (m > SM_MAX_M) return fail(SM_EINVAL, "pattern length %u exceeds SM_MAX_M (%u)", m, SM_MAX_M);
+    if (!h_pat) return fail(SM_EINVAL, "h_pat is NULL");
+    if (h_pi) {
+        std::vector<uint8_t> seen(m, 0);
+        for (uint32_t j = 0; j < m; ++j) {
+            if (h_pi[j] >= m || seen[h_pi[j]]) return fail(SM_EINVAL, "h_pi is not a permutation of 0..m-1");
+            seen[h_pi[j]] = 1;
+        }
+    }
+    return SM_OK;
+}
+
+// Peeling factor when the caller gives none. With the text histogram, peel
+// every compare after which a warp's 1024 starts are still almost surely
+// alive (the zero test would only cost time there); otherwise r = 2, the
+// paper's choice for the frequency-ordered search (Sec. 2.3).
+uint32_t auto_peel(const uint8_t* p, uint32_t m, const uint32_t* pi, const uint64_t* hist, uint64_t n) {
+    if (!hist || n == 0) return std::min<uint32_t>(m, 2);
+    double alive = 1.0;   // probability that one start survives the first j compares
+    uint32_t r = 1;
+    for (uint32_t j = 0; j + 1 < m; ++j) {
+        const uint32_t q = pi ? pi[j] : j;
+        alive *= (double)hist[p[q]] / (double)n;
+        const double warp_alive = 1.0 - std::pow(1.0 - alive, 1024.0);
+        if (warp_alive < 0.9) break;
+        ++r;
+    }
+    return std::min(r, m);
+}
+
+struct Plan {
+    std::vector<uint32_t> qc;
+    uint32_t r = 1;
+    bool seven = false;
+    bool zero = false;   // a pattern symbol never occurs in the text
+};
+
+Plan make_plan(const uint8_t* p, uint32_t m, const uint32_t* pi, const sm_search_opts* o, uint64_t n) {
+    Plan pl;
+    pl.qc.resize(m);
+    for (uint32_t j = 0; j < m; ++j) {
+        const uint32_t q = pi ? pi[j] : j;
+        pl.qc[j] = (q << 8) | p[q];
+    }
+    const uint64_t* h = o ? o->h_hist256 : nullptr;
+    if (h) {
+        uint64_t high = 0;
+        for (int c = 0x80; c < 256; ++c) high += h[c];
+        bool pat7 = true;
+        for (uint32_t q = 0; q < m; ++q) {
+            if (p[q] >= 0x80) pat7 = false;
+            if (h[p[q]] == 0) pl.zero = true;
+        }
+        pl.seven = (high == 0) && pat7;
+    }
+    pl.r = (o && o->peel) ? std::min(o->peel, m) : auto_peel(p, m, pi, h, n);
+    return pl;
+}
+
+struct Grid {
+    uint32_t grid = 0, stage_bytes = 0, stages = 0;
+    uint64_t ntiles = 0, per_cta = 0;
+    size_t smem = 0;
+};
+
+sm_status plan_grid(sm_ctx* c, int mode, bool seven, uint32_t m, uint64_t nstarts, Grid* g) {
+    g->ntiles = (nstarts + smk::kTile - 1) / smk::kTile;
+    g->stage_bytes = smk::stage_bytes_for(m);
+    g->stages = c->stages;
+    while (g->stages > 2 && smk::scan_smem_bytes(g->stage_bytes, g->stages) > c->max_smem) --g->stages;
+    g->smem = smk::scan_smem_bytes(g->stage_bytes, g->stages);
+    if (g->smem > c->max_smem) return fail(SM_ENOTSUP, "pattern too long for shared memory");
+    uint64_t want = c->grid_override;
+    if (!want) {
+        int occ = smk::scan_occupancy(mode, seven, m, g->smem);
+        if (occ <= 0) return fail(SM_ECUDA, "scan kernel cannot be resident (smem %zu)", g->smem);
+        want = (uint64_t)c->num_sms * (uint64_t)occ;
+    }
+    want = std::max<uint64_t>(1, std::min<uint64_t>(want, g->ntiles));
+    g->per_cta = (g->ntiles + want - 1) / want;
+    g->grid = (uint32_t)((g->ntiles + g->per_cta - 1) / g->per_cta);
+    return grow(&c->d_partials, &c->partials_cap, std::max<size_t>(g->grid, 256), "partials");
+}
+
+smk::ScanArgs scan_args(sm_ctx* c, const uint8_t* d_text, uint64_t n, uint32_t m, const Plan& pl, const Grid& g,
+                        uint64_t* d_count) {
+    smk::ScanArgs a{};
+    a.text = d_text;
+    a.n = n;
+    a.nstarts = n - m + 1;
+    a.ntiles = g.ntiles;
+    a.tiles_per_cta = g.per_cta;
+    a.m = m;
+    a.r = std::max<uint32_t>(1, std::min(pl.r, m));
+    a.stage_bytes = g.stage_bytes;
+    a.stages = g.stages;
+    a.status = c->d_status;
+    a.partials = c->d_partials;
+    a.ticket = c->d_ticket;
+    a.d_count = d_count;
+    a.tile_counts = c->d_tile_counts;
+    a.spin_ns = c->spin_ns;
+    a.test_skip_copy = c->test_skip_copy;
+    return a;
+}
+
+sm_status zero_count(uint64_t* d_count, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(d_count, 0, sizeof(uint64_t), s);
+    return e == cudaSuccess ? SM_OK : cuda_fail(e, "cudaMemsetAsync");
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sm_last_error(void) { return g_err.c_str(); }
+
+const char* sm_status_string(sm_status s) {
+    switch (s) {
+        case SM_OK: return "SM_OK";
+        case SM_EINVAL: return "SM_EINVAL";
+        case SM_ENOMEM: return "SM_ENOMEM";
+        case SM_ECUDA: return "SM_ECUDA";
+        case SM_ETRUNC: return "SM_ETRUNC";
+        case SM_ETIMEOUT: return "SM_ETIMEOUT";
+        case SM_ENOTSUP: return "SM_ENOTSUP";
+    }
+    return "unknown";
+}
+
+sm_status sm_create(sm_ctx** out, int device) {
+    if (!out) return fail(SM_EINVAL, "ctx pointer is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev) return fail(SM_EINVAL, "device %d out of range (%d devices)", device, ndev);
+    DeviceGuard g(device);
+    if (!g.ok) return fail(SM_ECUDA, "cudaSetDevice(%d) failed", device);
+    if (fault_alloc()) return fail(SM_ENOMEM, "injected allocation failure (context)");
+    sm_ctx* c = new sm_ctx();
+    c->device = device;
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
+    c->num_sms = v;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    c->max_smem = (size_t)v;
+    if ((e = cudaMalloc(&c->d_status, 64)) != cudaSuccess || (e = cudaMemset(c->d_status, 0, 64)) != cudaSuccess ||
+        (e = cudaMallocHost(&c->h_status, 64)) != cudaSuccess) {
+        sm_destroy(c);
+        return cuda_fail(e, "context allocation");
+    }
+    c->d_ticket = c->d_status + 8;   // second 32-byte sector of the same allocation
+    if ((e = smk::scan_prepare(c->max_smem)) != cudaSuccess) {
+        sm_destroy(c);
+        return cuda_fail(e, "cudaFuncSetAttribute");
+    }
+    sm_status st = grow(&c->d_partials, &c->partials_cap, (size_t)c->num_sms * 16 * 256, "partials");
+    if (st != SM_OK) {
+        sm_destroy(c);
+        return st;
+    }
+    *out = c;
+    return SM_OK;
+}
+
+void sm_destroy(sm_ctx* c) {
+    if (!c) return;
+    DeviceGuard g(c->device);
+    cudaDeviceSynchronize();
+    if (c->d_status) cudaFree(c->d_status);
+    if (c->h_status) cudaFreeHost(c->h_status);
+    if (c->d_partials) cudaFree(c->d_partials);
+    if (c->d_tile_counts) cudaFree(c->d_tile_counts);
+    delete c;
+}
+
+sm_status sm_set_knob(sm_ctx* c, sm_knob knob, int64_t value) {
+    if (!c) return fail(SM_EINVAL, "ctx is NULL");
+    switch (knob) {
+        case SM_KNOB_STAGES:
+            if (value < 2 || value > smk::kMaxStages) return fail(SM_EINVAL, "stages must be 2..%d", smk::kMaxStages);
+            c->stages = (uint32_t)value;
+            return SM_OK;
+        case SM_KNOB_GRID:
+            if (value < 0 || value > (1 << 24)) return fail(SM_EINVAL, "grid out of range");
+            c->grid_override = (uint32_t)value;
+            return SM_OK;
+        case SM_KNOB_SPIN_NS:
+            if (value < 1000) return fail(SM_EINVAL, "spin limit below 1 us");
+            c->spin_ns = (uint64_t)value;
+            return SM_OK;
+        case SM_KNOB_TEST_SKIP_COPY:
+            c->test_skip_copy = value ? 1u : 0u;
+            return SM_OK;
+    }
+    return fail(SM_EINVAL, "unknown knob %d", (int)knob);
+}
+
+sm_status sm_sync(sm_ctx* c, sm_stream_t stream) {
+    if (!c) return fail(SM_EINVAL, "ctx is NULL");
+    DeviceGuard g(c->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(c->h_status, c->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "sm_sync");
+    const uint32_t bits = *c->h_status;
+    if (bits & smk::kStatusTimeout) return fail(SM_ETIMEOUT, "a bounded device wait expired");
+    if (bits & smk::kStatusTrunc) return fail(SM_ETRUNC, "a report had more matches than its capacity");
+    return SM_OK;
+}
+
+sm_status sm_histogram(sm_ctx* c, const uint8_t* d_text, uint64_t n, uint64_t* d_hist256, sm_stream_t stream) {
+    if (!c) return fail(SM_EINVAL, "ctx is NULL");
+    if (!d_hist256) return fail(SM_EINVAL, "d_hist256 is NULL");
+    if (!d_text && n) return fail(SM_EINVAL, "d_text is NULL");
+    DeviceGuard g(c->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (n == 0) {
+        cudaError_t e = cudaMemsetAsync(d_hist256, 0, 256 * sizeof(uint64_t), s);
+        return e == cudaSuccess ? SM_OK : cuda_fail(e, "cudaMemsetAsync");
+    }
+    const uint64_t per_block = (uint64_t)smk::kHistThreads * 16 * 8;
+    uint64_t grid = std::min<uint64_t>((uint64_t)c->num_sms * 4, (n + per_block - 1) / per_block);
+    grid = std::max<uint64_t>(grid, 1);
+    sm_status st = grow(&c->d_partials, &c->partials_cap, grid * 256, "partials");
+    if (st != SM_OK) return st;
+    smk::HistArgs a{d_text, n, c->d_partials, c->d_ticket, d_hist256};
+    cudaError_t e = smk::launch_hist((uint32_t)grid, s, a);
+    return e == cudaSuccess ? SM_OK : cuda_fail(e, "histogram launch");
+}
+
+sm_status sm_order(const uint8_t* h_pat, uint32_t m, const uint64_t* h_hist256, uint32_t* h_pi) {
+    if (m == 0) return fail(SM_EINVAL, "pattern length m must be at least 1");
+    if (!h_pat || !h_hist256 || !h_pi) return fail(SM_EINVAL, "NULL argument");
+    std::vector<uint32_t> idx(m);
+    std::iota(idx.begin(), idx.end(), 0u);
+    std::stable_sort(idx.begin(), idx.end(),
+                     [&](uint32_t a, uint32_t b) { return h_hist256[h_pat[a]] < h_hist256[h_pat[b]]; });
+    std::copy(idx.begin(), idx.end(), h_pi);
+    return SM_OK;
+}
+
+sm_status sm_order_fixed(const uint8_t* h_pat, uint32_t m, int mode, uint32_t* h_pi) {
+    if (m == 0) return fail(SM_EINVAL, "pattern length m must be at least 1");
+    if (!h_pi) return fail(SM_EINVAL, "h_pi is NULL");
+    if (mode != SM_ORDER_H && mode != SM_ORDER_HS) return fail(SM_EINVAL, "unknown order mode %d", mode);
+    if (mode == SM_ORDER_HS && !h_pat) return fail(SM_EINVAL, "h_pat is NULL");
+    std::vector<uint32_t> keep, spaces;
+    for (uint32_t q = 0; q < m; ++q) {
+        if (mode == SM_ORDER_HS && h_pat[q] == 0x20) spaces.push_back(q);
+        else keep.push_back(q);
+    }
+    // pi_h over `keep`: first, last, then indices 3,6,.. / 2,5,.. / 1,4,.. below the last
+    std::vector<uint32_t> out;
+    out.reserve(m);
+    const size_t L = keep.size();
+    if (L) {
+        out.push_back(keep[0]);
+        if (L > 1) out.push_back(keep[L - 1]);
+        for (size_t first : {size_t(3), size_t(2), size_t(1)})
+            for (size_t k = first; k + 1 < L; k += 3) out.push_back(keep[k]);
+    }
+    out.insert(out.end(), spaces.begin(), spaces.end());
+    std::copy(out.begin(), out.end(), h_pi);
+    return SM_OK;
+}
+
+static sm_status search(sm_ctx* c, const uint8_t* d_text, uint64_t n, const uint8_t* h_pat, uint32_t m,
+                        const uint32_t* h_pi, const sm_search_opts* opts, uint64_t* d_pos, uint64_t cap,
+                        uint64_t* d_count, sm_stream_t stream, bool report) {
+    if (!c) return fail(SM_EINVAL, "ctx is NULL");
+    if (!d_count) return fail(SM_EINVAL, "d_count is NULL");
+    if (!d_text && n) return fail(SM_EINVAL, "d_text is NULL");
+    if (report && cap && !d_pos) return fail(SM_EINVAL, "d_pos is NULL with cap > 0");
+    sm_status st = check_pattern(h_pat, m, h_pi);
+    if (st != SM_OK) return st;
+    DeviceGuard g(c->device);
+    if (!g.ok) return fail(SM_ECUDA, "cudaSetDevice(%d) failed", c->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if ((uint64_t)m > n) return zero_count(d_count, s);
+    Plan pl = make_plan(h_pat, m, h_pi, opts, n);
+    if (pl.zero) return zero_count(d_count, s);
+
+    const uint64_t nstarts = n - m + 1;
+    const int mode1 = report ? smk::kModeTileCount : smk::kModeCount;
+    Grid gr;
+    st = plan_grid(c, mode1, pl.seven, m, nstarts, &gr);
+    if (st != SM_OK) return st;
+    if (report) {
+        st = grow(&c->d_tile_counts, &c->tile_counts_cap, (size_t)gr.ntiles, "tile counts");
+        if (st != SM_OK) return st;
+    }
+    smk::ScanArgs a = scan_args(c, d_text, n, m, pl, gr, d_count);
+    cudaError_t e = smk::launch_scan(mode1, pl.seven, gr.grid, gr.smem, s, a, pl.qc.data());
+    if (e != cudaSuccess) return cuda_fail(e, "scan launch");
+    if (report) {
+        a.d_pos = d_pos;
+        a.cap = cap;
+        e = smk::launch_scan(smk::kModeWrite, pl.seven, gr.grid, gr.smem, s, a, pl.qc.data());
+        if (e != cudaSuccess) return cuda_fail(e, "report launch");
+    }
+    return SM_OK;
+}
+
+sm_status sm_count(sm_ctx* c, const uint8_t* d_text, uint64_t n, const uint8_t* h_pat, uint32_t m,
+                   const uint32_t* h_pi, uint64_t* d_count, sm_stream_t stream) {
+    return search(c, d_text, n, h_pat, m, h_pi, nullptr, nullptr, 0, d_count, stream, false);
+}
+
+sm_status sm_count_ex(sm_ctx* c, const uint8_t* d_text, uint64_t n, const uint8_t* h_pat, uint32_t m,
+                      const uint32_t* h_pi, const sm_search_opts* opts, uint64_t* d_count, sm_stream_t stream) {
+    return search(c, d_text, n, h_pat, m, h_pi, opts, nullptr, 0, d_count, stream, false);
+}
+
+sm_status sm_report(sm_ctx* c, const uint8_t* d_text, uint64_t n, const uint8_t* h_pat, uint32_t m,
+                    const uint32_t* h_pi, uint64_t* d_pos, uint64_t cap, uint64_t* d_count, sm_stream_t stream) {
+    return search(c, d_text, n, h_pat, m, h_pi, nullptr, d_pos, cap, d_count, stream, true);
+}
+
+sm_status sm_report_ex(sm_ctx* c, const uint8_t* d_text, uint64_t n, const uint8_t* h_pat, uint32_t m,
+                       const uint32_t* h_pi, const sm_search_opts* opts, uint64_t* d_pos, uint64_t cap,
+                       uint64_t* d_count, sm_stream_t stream) {
+    return search(c, d_text, n, h_pat, m, h_pi, opts, d_pos, cap, d_count, stream, true);
+}
+
+}  // extern "C"

@@ -1,0 +1,234 @@
+"""Python binding of the C ABI in include/sm.h (ctypes; argument marshalling only).
+
+Every function here has the name of the C entry point it calls. Device
+buffers are torch CUDA tensors (``uint8`` texts; counts, positions
+and histograms are 64-bit tensors, int64 by default, holding the ABI's
+uint64 values); the stream is torch's current stream unless one is given. There is
+no CPU fallback: if ``libsm.so`` is missing the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import LIB as _LIB_PATH
+
+SM_OK, SM_EINVAL, SM_ENOMEM, SM_ECUDA, SM_ETRUNC, SM_ETIMEOUT, SM_ENOTSUP = range(7)
+SM_MAX_M = 4096
+SM_TILE_STARTS = 8192
+SM_ORDER_H, SM_ORDER_HS = 1, 2
+SM_KNOB_STAGES, SM_KNOB_GRID, SM_KNOB_SPIN_NS, SM_KNOB_TEST_SKIP_COPY = 1, 2, 3, 4
+
+# Every symbol the header declares (checked against include/sm.h by the tests).
+EXPORTS = ("sm_create", "sm_destroy", "sm_last_error", "sm_status_string", "sm_sync", "sm_set_knob",
+           "sm_histogram", "sm_order", "sm_order_fixed", "sm_count", "sm_count_ex", "sm_report",
+           "sm_report_ex")
+
+
+class SmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_status_name(status)}: {msg}")
+        self.status = status
+
+
+class SearchOpts(C.Structure):
+    _fields_ = [("peel", C.c_uint32), ("reserved", C.c_uint32), ("h_hist256", C.POINTER(C.c_uint64))]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Load libsm.so (built by ``__graft_entry__.build()``); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"CUDA library not built: {_LIB_PATH} is missing (run __graft_entry__.build())")
+    lib = C.CDLL(_LIB_PATH)
+    vp, u8p, u32p, u64p = C.c_void_p, C.POINTER(C.c_uint8), C.POINTER(C.c_uint32), C.POINTER(C.c_uint64)
+    st, u32, u64 = C.c_int, C.c_uint32, C.c_uint64
+    sig = {
+        "sm_create": (st, [C.POINTER(vp), C.c_int]),
+        "sm_destroy": (None, [vp]),
+        "sm_last_error": (C.c_char_p, []),
+        "sm_status_string": (C.c_char_p, [st]),
+        "sm_sync": (st, [vp, vp]),
+        "sm_set_knob": (st, [vp, C.c_int, C.c_int64]),
+        "sm_histogram": (st, [vp, vp, u64, vp, vp]),
+        "sm_order": (st, [u8p, u32, u64p, u32p]),
+        "sm_order_fixed": (st, [u8p, u32, C.c_int, u32p]),
+        "sm_count": (st, [vp, vp, u64, u8p, u32, u32p, vp, vp]),
+        "sm_count_ex": (st, [vp, vp, u64, u8p, u32, u32p, C.POINTER(SearchOpts), vp, vp]),
+        "sm_report": (st, [vp, vp, u64, u8p, u32, u32p, vp, u64, vp, vp]),
+        "sm_report_ex": (st, [vp, vp, u64, u8p, u32, u32p, C.POINTER(SearchOpts), vp, u64, vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype, f.argtypes = res, args
+    _lib = lib
+    return lib
+
+
+def _status_name(s: int) -> str:
+    names = ["SM_OK", "SM_EINVAL", "SM_ENOMEM", "SM_ECUDA", "SM_ETRUNC", "SM_ETIMEOUT", "SM_ENOTSUP"]
+    return names[s] if 0 <= s < len(names) else f"status {s}"
+
+
+def _check(status: int):
+    if status != SM_OK:
+        raise SmError(status, load().sm_last_error().decode(errors="replace"))
+
+
+def _bytes(x) -> np.ndarray:
+    if isinstance(x, (bytes, bytearray, memoryview)):
+        return np.frombuffer(bytes(x), dtype=np.uint8)
+    a = np.ascontiguousarray(x)
+    if a.dtype != np.uint8:
+        raise TypeError("patterns must be bytes or uint8 arrays")
+    return a
+
+
+def _u8p(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_uint8)) if a.size else C.cast(C.c_char_p(b"\0"), C.POINTER(C.c_uint8))
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+_WORD64 = ("torch.int64", "torch.uint64")
+
+
+def _dev_ptr(t, dtypes=None) -> int:
+    if t is None:
+        return 0
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("device buffers must be contiguous CUDA tensors")
+    if dtypes and str(t.dtype) not in dtypes:
+        raise TypeError(f"expected one of {dtypes}, got {t.dtype}")
+    return t.data_ptr()
+
+
+class Ctx:
+    """Owns an sm_ctx*; destroyed with the object."""
+
+    def __init__(self, handle: int, device: int):
+        self.handle, self.device = handle, device
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.sm_destroy(h)
+
+
+def sm_create(device: int = 0) -> Ctx:
+    h = C.c_void_p()
+    _check(load().sm_create(C.byref(h), device))
+    return Ctx(h.value, device)
+
+
+def sm_sync(ctx: Ctx, stream=None) -> int:
+    """Wait for the stream; return the deferred status (SM_OK, SM_ETRUNC, SM_ETIMEOUT)."""
+    s = load().sm_sync(ctx.handle, _stream(stream))
+    if s not in (SM_OK, SM_ETRUNC, SM_ETIMEOUT):
+        _check(s)
+    return s
+
+
+def sm_set_knob(ctx: Ctx, knob: int, value: int):
+    _check(load().sm_set_knob(ctx.handle, knob, value))
+
+
+def sm_histogram(ctx: Ctx, text, out=None, stream=None):
+    import torch
+    if out is None:
+        out = torch.empty(256, dtype=torch.int64, device=text.device)
+    _check(load().sm_histogram(ctx.handle, _dev_ptr(text, ("torch.uint8",)), text.numel(),
+                               _dev_ptr(out, _WORD64), _stream(stream)))
+    return out
+
+
+def sm_order(pattern, hist) -> np.ndarray:
+    p = _bytes(pattern)
+    h = np.ascontiguousarray(hist, dtype=np.uint64)
+    if h.size != 256:
+        raise ValueError("histogram must have 256 entries")
+    pi = np.zeros(max(p.size, 1), dtype=np.uint32)
+    _check(load().sm_order(_u8p(p), p.size, h.ctypes.data_as(C.POINTER(C.c_uint64)),
+                           pi.ctypes.data_as(C.POINTER(C.c_uint32))))
+    return pi[: p.size]
+
+
+def sm_order_fixed(pattern, mode: int) -> np.ndarray:
+    p = _bytes(pattern)
+    pi = np.zeros(max(p.size, 1), dtype=np.uint32)
+    _check(load().sm_order_fixed(_u8p(p), p.size, mode, pi.ctypes.data_as(C.POINTER(C.c_uint32))))
+    return pi[: p.size]
+
+
+def _opts(peel: int, hist):
+    if not peel and hist is None:
+        return None, None
+    h = None if hist is None else np.ascontiguousarray(hist, dtype=np.uint64)
+    o = SearchOpts(peel, 0, h.ctypes.data_as(C.POINTER(C.c_uint64)) if h is not None else None)
+    return o, h
+
+
+def _pi(pi, m):
+    if pi is None:
+        return None, None
+    a = np.ascontiguousarray(pi, dtype=np.uint32)
+    if a.size != m:
+        raise ValueError("order must have m entries")
+    return a.ctypes.data_as(C.POINTER(C.c_uint32)), a
+
+
+def sm_count(ctx: Ctx, text, pattern, pi=None, out=None, stream=None, peel: int = 0, hist=None):
+    """Enqueue a count; returns the 1-element int64 device tensor it writes."""
+    import torch
+    p = _bytes(pattern)
+    if out is None:
+        out = torch.empty(1, dtype=torch.int64, device=text.device)
+    pip, _keep_pi = _pi(pi, p.size)
+    o, _keep_h = _opts(peel, hist)
+    lib = load()
+    if o is None:
+        st = lib.sm_count(ctx.handle, _dev_ptr(text, ("torch.uint8",)), text.numel(), _u8p(p), p.size, pip,
+                          _dev_ptr(out, _WORD64), _stream(stream))
+    else:
+        st = lib.sm_count_ex(ctx.handle, _dev_ptr(text, ("torch.uint8",)), text.numel(), _u8p(p), p.size, pip,
+                             C.byref(o), _dev_ptr(out, _WORD64), _stream(stream))
+    _check(st)
+    return out
+
+
+def sm_report(ctx: Ctx, text, pattern, cap: int, pi=None, out_pos=None, out_count=None, stream=None,
+              peel: int = 0, hist=None):
+    """Enqueue a report; returns (positions int64[cap], count int64[1]) device tensors."""
+    import torch
+    p = _bytes(pattern)
+    if out_pos is None:
+        out_pos = torch.empty(max(cap, 1), dtype=torch.int64, device=text.device)
+    if out_count is None:
+        out_count = torch.empty(1, dtype=torch.int64, device=text.device)
+    pip, _keep_pi = _pi(pi, p.size)
+    o, _keep_h = _opts(peel, hist)
+    lib = load()
+    if o is None:
+        st = lib.sm_report(ctx.handle, _dev_ptr(text, ("torch.uint8",)), text.numel(), _u8p(p), p.size, pip,
+                           _dev_ptr(out_pos, _WORD64), cap, _dev_ptr(out_count, _WORD64), _stream(stream))
+    else:
+        st = lib.sm_report_ex(ctx.handle, _dev_ptr(text, ("torch.uint8",)), text.numel(), _u8p(p), p.size, pip,
+                              C.byref(o), _dev_ptr(out_pos, _WORD64), cap, _dev_ptr(out_count, _WORD64), _stream(stream))
+    _check(st)
+    return out_pos, out_count

@@ -23,13 +23,14 @@ from __future__ import annotations
 import ctypes as C
 import hashlib
 import os
+import platform
 import subprocess
 
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "synth.c")
-_OUT_DIR = os.path.join(os.path.dirname(_HERE), "_build")
+_OUT_DIR = os.path.join(os.path.dirname(_HERE), "_build", platform.machine())
 _LIB_PATH = os.path.join(_OUT_DIR, "libsynth.so")
 _lib = None
 

@@ -186,6 +186,42 @@ sm_status sm_report_ex(sm_ctx* ctx, const uint8_t* d_text, uint64_t n,
                        const sm_search_opts* opts, uint64_t* d_pos, uint64_t cap,
                        uint64_t* d_count, sm_stream_t stream);
 
+/* ------------------------------------------------------- no allocation */
+/*
+ * sm_report_noalloc - the report of sm_report for callers that must not
+ * allocate device memory. The paper has no counterpart; this entry point
+ * exists for how the library is embedded, not for the method.
+ *
+ * Who needs it: code that is only handed input and output buffers and may
+ * not call cudaMalloc -- a plug-in inside a host framework whose caching
+ * allocator already reserves the device memory (a foreign cudaMalloc can fail
+ * or fragment that pool), a service that forbids allocation after start-up
+ * because cudaMalloc and cudaFree can block and synchronize the device, or a
+ * caller with no context object to keep. sm_report keeps its scratch in an
+ * sm_ctx allocated by sm_create; this call keeps it in one fixed device array
+ * that the library defines (about 272 KiB), which every GPU that loads the
+ * library holds until the process exits.
+ *
+ * Behaviour: as sm_report with default options (identity order when h_pi is
+ * NULL), on the calling thread's current device and the given stream; it
+ * allocates nothing (no cudaMalloc, cudaFree or other allocating routine).
+ * The first call on a device also looks up the array's device address and
+ * sets kernel attributes; make that first call before any stream capture.
+ * All calls share the one array and it keeps the previous call's contents
+ * (the call clears what must start at zero): calls whose work overlaps on
+ * the GPU -- other streams, other host threads -- race and give wrong
+ * results, so order them. A report with more than cap matches writes the
+ * first cap positions and the full count; the caller sees this as
+ * *d_count > cap (there is no context to hold a deferred status).
+ * Errors: SM_EINVAL as sm_report, and when the text has more than
+ * SM_NOALLOC_MAX_STARTS start positions (n - m + 1), the number of tiles the
+ * array's per-tile counts cover; SM_ECUDA when a CUDA call fails.
+ */
+#define SM_NOALLOC_MAX_STARTS 536870912ull   /* 65536 tiles x 8192 starts */
+sm_status sm_report_noalloc(const uint8_t* d_text, uint64_t n, const uint8_t* h_pat, uint32_t m,
+                            const uint32_t* h_pi, uint64_t* d_pos, uint64_t cap,
+                            uint64_t* d_count, sm_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,11 +20,12 @@ SM_MAX_M = 4096
 SM_TILE_STARTS = 8192
 SM_ORDER_H, SM_ORDER_HS = 1, 2
 SM_KNOB_STAGES, SM_KNOB_GRID, SM_KNOB_SPIN_NS, SM_KNOB_TEST_SKIP_COPY = 1, 2, 3, 4
+SM_NOALLOC_MAX_STARTS = 65536 * 8192
 
 # Every symbol the header declares (checked against include/sm.h by the tests).
 EXPORTS = ("sm_create", "sm_destroy", "sm_last_error", "sm_status_string", "sm_sync", "sm_set_knob",
            "sm_histogram", "sm_order", "sm_order_fixed", "sm_count", "sm_count_ex", "sm_report",
-           "sm_report_ex")
+           "sm_report_ex", "sm_report_noalloc")
 
 
 class SmError(RuntimeError):
@@ -68,6 +69,7 @@ def load():
         "sm_count_ex": (st, [vp, vp, u64, u8p, u32, u32p, C.POINTER(SearchOpts), vp, vp]),
         "sm_report": (st, [vp, vp, u64, u8p, u32, u32p, vp, u64, vp, vp]),
         "sm_report_ex": (st, [vp, vp, u64, u8p, u32, u32p, C.POINTER(SearchOpts), vp, u64, vp, vp]),
+        "sm_report_noalloc": (st, [vp, u64, u8p, u32, u32p, vp, u64, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -232,3 +234,16 @@ def sm_report(ctx: Ctx, text, pattern, cap: int, pi=None, out_pos=None, out_coun
                               C.byref(o), _dev_ptr(out_pos, _WORD64), cap, _dev_ptr(out_count, _WORD64), _stream(stream))
     _check(st)
     return out_pos, out_count
+
+
+def sm_report_noalloc(text, pattern, cap: int, out_pos, out_count, pi=None, stream=None) -> int:
+    """Enqueue sm_report_noalloc into caller-provided buffers; returns the status.
+
+    The C call allocates nothing; the caller passes the position buffer
+    (at least ``cap`` 64-bit entries) and the 1-entry count buffer.
+    """
+    p = _bytes(pattern)
+    pip, _keep_pi = _pi(pi, p.size)
+    return load().sm_report_noalloc(_dev_ptr(text, ("torch.uint8",)), text.numel(), _u8p(p), p.size, pip,
+                                    _dev_ptr(out_pos, _WORD64), cap, _dev_ptr(out_count, _WORD64),
+                                    _stream(stream))

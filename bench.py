@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--json-detail", default="")
+    ap.add_argument("--peel", type=int, default=0, help="peeling factor r (0 = automatic)")
+    ap.add_argument("--stages", type=int, default=0, help="scan pipeline depth (0 = library default)")
+    ap.add_argument("--ctas", type=int, default=0, help="scan CTAs (0 = one resident wave)")
     return ap.parse_args()
 
 
@@ -185,6 +188,10 @@ def run_gpu(args, world, rank, local):
     variants = [v for v in args.variants.split(",") if v]
     dev = torch.device("cuda", local)
     ctx = sm.sm_create(local)
+    if args.stages:
+        sm.sm_set_knob(ctx, sm.SM_KNOB_STAGES, args.stages)
+    if args.ctas:
+        sm.sm_set_knob(ctx, sm.SM_KNOB_GRID, args.ctas)
     stream = torch.cuda.current_stream()
     d_texts = {k: torch.from_numpy(texts[k]).to(dev) for k in kinds}
     counts = torch.zeros(len(ms) * args.patterns * 2 + 8, dtype=torch.int64, device=dev)
@@ -220,15 +227,16 @@ def run_gpu(args, world, rank, local):
                         if timed:
                             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                             a.record(stream)
-                        sm.sm_count(ctx, text_map[k], p, pi=pi, hist=h, out=counts[slot:slot + 1])
+                        sm.sm_count(ctx, text_map[k], p, pi=pi, hist=h, peel=args.peel,
+                                    out=counts[slot:slot + 1])
                         launches["n"] += 1
                         if timed:
                             b.record(stream)
                             ev_count.append((a, b))
                     slot += 1
                     if "report" in variants:
-                        sm.sm_report(ctx, text_map[k], p, max_cap, pi=pi, hist=h, out_pos=d_pos,
-                                     out_count=counts[slot:slot + 1])
+                        sm.sm_report(ctx, text_map[k], p, max_cap, pi=pi, hist=h, peel=args.peel,
+                                     out_pos=d_pos, out_count=counts[slot:slot + 1])
                         launches["n"] += 2
                     slot += 1
                 e1 = torch.cuda.Event(enable_timing=True)
@@ -343,8 +351,8 @@ def run_e2e(args, ctx, kinds, ms, pats, hists, texts, dev, stream, d_texts, vari
 
 def run_cpu_baseline(args, budget_s: float):
     """The oracle (Algorithm 1, threaded over the host cores) on a bounded
-    sample of the sweep: a 64 MiB prefix of each text, up to 3 patterns per
-    (sigma, m), until the time budget is spent."""
+    sample of the sweep: 64 MiB prefixes of the texts, cycling over
+    (sigma, m) with fresh patterns until the time budget is spent."""
     import oracle
     from paper_1612_01506_gb300 import synth
     kinds, ms = kinds_of(args.kinds), [int(x) for x in args.ms.split(",") if x]
@@ -353,16 +361,18 @@ def run_cpu_baseline(args, budget_s: float):
     scanned, spent, searches = 0, 0.0, 0
     order = [(k, m) for m in ms for k in kinds]
     texts = {k: synth.text(k, sample_n, seed=0, stream=synth.stream_id("sweep", k)) for k in kinds}
-    for rep in range(3):
+    rep = 0
+    while spent < budget_s and rep < 100:
         for k, m in order:
             if spent >= budget_s:
                 break
-            p = synth.sample_patterns(texts[k], m, 3, seed=0, stream=synth.stream_id("pat", k, m))[rep]
+            p = synth.sample_patterns(texts[k], m, rep + 1, seed=0, stream=synth.stream_id("pat", k, m))[rep]
             t0 = time.perf_counter()
             oracle.count_threads(p, texts[k], cores)
             spent += time.perf_counter() - t0
             scanned += sample_n
             searches += 1
+        rep += 1
     return {"value": round(scanned / spent / 1e9, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
             "sample": f"{searches} counts over 64 MiB prefixes of the sweep texts "
                       f"(sigma {args.kinds}; m {args.ms}), {spent:.1f} s"}

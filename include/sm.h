@@ -52,7 +52,7 @@ typedef enum sm_status {
 } sm_status;
 
 #define SM_MAX_M 4096u          /* longest pattern accepted */
-#define SM_TILE_STARTS 8192u    /* start positions per scan tile */
+#define SM_TILE_STARTS 16384u   /* start positions per scan tile */
 
 typedef struct sm_ctx sm_ctx;
 
@@ -199,7 +199,7 @@ sm_status sm_report_ex(sm_ctx* ctx, const uint8_t* d_text, uint64_t n,
  * because cudaMalloc and cudaFree can block and synchronize the device, or a
  * caller with no context object to keep. sm_report keeps its scratch in an
  * sm_ctx allocated by sm_create; this call keeps it in one fixed device array
- * that the library defines (about 272 KiB), which every GPU that loads the
+ * that the library defines (about 528 KiB), which every GPU that loads the
  * library holds until the process exits.
  *
  * Behaviour: as sm_report with default options (identity order when h_pi is
@@ -214,10 +214,10 @@ sm_status sm_report_ex(sm_ctx* ctx, const uint8_t* d_text, uint64_t n,
  * first cap positions and the full count; the caller sees this as
  * *d_count > cap (there is no context to hold a deferred status).
  * Errors: SM_EINVAL as sm_report, and when the text has more than
- * SM_NOALLOC_MAX_STARTS start positions (n - m + 1), the number of tiles the
- * array's per-tile counts cover; SM_ECUDA when a CUDA call fails.
+ * SM_NOALLOC_MAX_STARTS start positions (n - m + 1), the number of tiles
+ * whose per-tile counts the array holds; SM_ECUDA when a CUDA call fails.
  */
-#define SM_NOALLOC_MAX_STARTS 536870912ull   /* 65536 tiles x 8192 starts */
+#define SM_NOALLOC_MAX_STARTS 268435456ull   /* 16384 tiles x 16384 starts */
 sm_status sm_report_noalloc(const uint8_t* d_text, uint64_t n, const uint8_t* h_pat, uint32_t m,
                             const uint32_t* h_pi, uint64_t* d_pos, uint64_t cap,
                             uint64_t* d_count, sm_stream_t stream);

@@ -41,8 +41,8 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def _compile(src: str, extra: list[str]) -> str:
-    obj = os.path.join(OUT, os.path.basename(src) + ".o")
+def _compile(src: str, extra: list[str], out: str = OUT) -> str:
+    obj = os.path.join(out, os.path.basename(src) + ".o")
     if _stale(obj, [src] + _headers()):
         cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                "-I", INCLUDE, "-I", CSRC, *extra, "-c", src, "-o", obj + ".tmp"]
@@ -51,16 +51,18 @@ def _compile(src: str, extra: list[str]) -> str:
     return obj
 
 
-def build_lib(verbose_ptxas: bool = False) -> str:
-    os.makedirs(OUT, exist_ok=True)
+def build_lib(verbose_ptxas: bool = False, out: str = OUT, defines: tuple[str, ...] = ()) -> str:
+    """Compile and link libsm.so into `out` (extra -D `defines` for tuning builds)."""
+    os.makedirs(out, exist_ok=True)
+    lib = os.path.join(out, "libsm.so")
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
-    extra = ["-Xptxas", "-v"] if verbose_ptxas else []
+    extra = (["-Xptxas", "-v"] if verbose_ptxas else []) + [f"-D{d}" for d in defines]
     with cf.ThreadPoolExecutor(max_workers=max(1, len(srcs))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), srcs))
-    if _stale(LIB, objs):
-        subprocess.check_call([nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", LIB + ".tmp", *objs])
-        os.replace(LIB + ".tmp", LIB)
-    return LIB
+        objs = list(ex.map(lambda s: _compile(s, extra, out), srcs))
+    if _stale(lib, objs):
+        subprocess.check_call([nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", lib + ".tmp", *objs])
+        os.replace(lib + ".tmp", lib)
+    return lib
 
 
 def build() -> str:

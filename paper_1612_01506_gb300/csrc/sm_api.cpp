@@ -28,8 +28,8 @@ struct sm_ctx {
     uint32_t* d_ticket = nullptr;
     uint64_t* d_partials = nullptr;
     size_t partials_cap = 0;          // entries
-    uint32_t* d_tile_counts = nullptr;
-    size_t tile_counts_cap = 0;       // entries
+    uint32_t* d_warp_counts = nullptr;
+    size_t warp_counts_cap = 0;       // entries
     uint32_t stages = 4;
     uint32_t grid_override = 0;
     uint64_t spin_ns = 1000000000ull;
@@ -105,22 +105,37 @@ sm_status check_pattern(const uint8_t* h_pat, uint32_t m, const uint32_t* h_pi) 
     return SM_OK;
 }
 
-// Peeling factor when the caller gives none. With the text histogram, peel
-// every compare after which a warp's 1024 starts are still almost surely
-// alive (the zero test would only cost time there); otherwise r = 2, the
-// paper's choice for the frequency-ordered search (Sec. 2.3).
+// Peeling factor r when the caller gives none. Sec. 2.3 leaves r to tuning
+// (2 for English with frequency order, 3 to 5 for DNA). Costs, in
+// instructions per warp of 2048 starts, measured on GB300: a peeled compare
+// of all starts ~100; compacting the surviving 4-start words ~80 when any
+// survives; each round of 32 surviving words continued by one lane each ~60;
+// more than the queue holds (~96 expected) falls back to dense compares. With
+// the text histogram the fraction of starts alive after r compares is the
+// product of the compared symbols' frequencies, and r minimizes the sum.
+// Without it r = 2, the paper's choice for the frequency-ordered search.
 uint32_t auto_peel(const uint8_t* p, uint32_t m, const uint32_t* pi, const uint64_t* hist, uint64_t n) {
     if (!hist || n == 0) return std::min<uint32_t>(m, 2);
-    double alive = 1.0;   // probability that one start survives the first j compares
-    uint32_t r = 1;
-    for (uint32_t j = 0; j + 1 < m; ++j) {
-        const uint32_t q = pi ? pi[j] : j;
+    double alive = 1.0, best = 1e300;
+    uint32_t best_r = 1;
+    const uint32_t top = std::min<uint32_t>(m, 16);
+    for (uint32_t r = 1; r <= top; ++r) {
+        const uint32_t q = pi ? pi[r - 1] : r - 1;
         alive *= (double)hist[p[q]] / (double)n;
-        const double warp_alive = 1.0 - std::pow(1.0 - alive, 1024.0);
-        if (warp_alive < 0.9) break;
-        ++r;
+        double cost = 100.0 * r;
+        if (r < m) {
+            const double p_word = 1.0 - std::pow(1.0 - alive, 4.0);
+            const double p_warp = 1.0 - std::pow(1.0 - alive, 2048.0);
+            const double entries = 512.0 * p_word;
+            cost += 80.0 * p_warp + 60.0 * (p_warp + std::max(0.0, entries - 32.0) / 32.0);
+            if (entries > 96.0) cost += 200.0;
+        }
+        if (cost < best) {
+            best = cost;
+            best_r = r;
+        }
     }
-    return std::min(r, m);
+    return best_r;
 }
 
 struct Plan {
@@ -193,7 +208,8 @@ smk::ScanArgs scan_args(sm_ctx* c, const uint8_t* d_text, uint64_t n, uint32_t m
     a.partials = c->d_partials;
     a.ticket = c->d_ticket;
     a.d_count = d_count;
-    a.tile_counts = c->d_tile_counts;
+    a.warp_counts = c->d_warp_counts;
+    a.one = 1;
     a.spin_ns = c->spin_ns;
     a.test_skip_copy = c->test_skip_copy;
     return a;
@@ -266,7 +282,7 @@ void sm_destroy(sm_ctx* c) {
     if (c->d_status) cudaFree(c->d_status);
     if (c->h_status) cudaFreeHost(c->h_status);
     if (c->d_partials) cudaFree(c->d_partials);
-    if (c->d_tile_counts) cudaFree(c->d_tile_counts);
+    if (c->d_warp_counts) cudaFree(c->d_warp_counts);
     delete c;
 }
 
@@ -384,7 +400,8 @@ static sm_status search(sm_ctx* c, const uint8_t* d_text, uint64_t n, const uint
     st = plan_grid(c, mode1, pl.seven, m, nstarts, &gr);
     if (st != SM_OK) return st;
     if (report) {
-        st = grow(&c->d_tile_counts, &c->tile_counts_cap, (size_t)gr.ntiles, "tile counts");
+        st = grow(&c->d_warp_counts, &c->warp_counts_cap, (size_t)gr.ntiles * smk::kConsumerWarps,
+                  "per-warp tile counts");
         if (st != SM_OK) return st;
     }
     smk::ScanArgs a = scan_args(c, d_text, n, m, pl, gr, d_count);

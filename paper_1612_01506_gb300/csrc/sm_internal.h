@@ -1,5 +1,5 @@
-// Internal interface between the host runtime (sm_api.cu) and the kernels
-// (sm_kernels.cu). Not part of the public C ABI.
+// Internal interface between the host runtime (sm_api.cpp, sm_noalloc.cu) and
+// the kernels (sm_kernels.cu). Not part of the public C ABI.
 #pragma once
 
 #include <cstddef>
@@ -8,19 +8,22 @@
 
 namespace smk {
 
-constexpr int kThreads = 256;            // threads per scan CTA (8 warps)
-constexpr uint32_t kTile = 8192;         // start positions per tile: 8 warps x 1024
+constexpr int kConsumerWarps = 8;                       // warps that compare
+constexpr int kThreads = 32 * (kConsumerWarps + 1);     // + one producer warp
+constexpr int kChunks = 4;                              // 16-start chunks per lane
+constexpr uint32_t kWarpStarts = 16 * 32 * kChunks;     // 2048 start positions per consumer warp
+constexpr uint32_t kTile = kWarpStarts * kConsumerWarps;  // 16384 starts per tile
 constexpr int kSmallM = 64;              // pattern capacity of the small parameter block
 constexpr int kLargeM = 4096;            // pattern capacity of the large parameter block
 constexpr int kMaxStages = 8;
 
-// Deferred status bits, OR-ed into the context's device status word.
+// Deferred status bits, OR-ed into the status word.
 constexpr uint32_t kStatusTrunc = 1u;
 constexpr uint32_t kStatusTimeout = 2u;
 
 enum ScanMode : int {
     kModeCount = 0,      // count only: per-CTA partial counts, last CTA writes *d_count
-    kModeTileCount = 1,  // as kModeCount, and per-tile counts for a later report pass
+    kModeTileCount = 1,  // as kModeCount, and per-(tile, warp) counts for a report
     kModeWrite = 2       // report: write ascending positions of tiles with matches
 };
 
@@ -31,18 +34,20 @@ struct ScanArgs {
     uint64_t ntiles;         // ceil(nstarts / kTile)
     uint64_t tiles_per_cta;  // each CTA owns one contiguous range of tiles
     uint32_t m;
-    uint32_t r;              // peeled compares, 1..m
+    uint32_t r;              // peeled compares, 1..m (dense phase)
     uint32_t stage_bytes;    // shared-memory bytes per pipeline stage (multiple of 128)
     uint32_t stages;         // pipeline depth, 2..kMaxStages
+    uint32_t one;            // the value 1 (keeps an add on the multiply-add pipe)
+    uint32_t nd[4];          // dense compares per word-alignment class (set by launch_scan)
+    uint32_t test_skip_copy; // test hook: 1 = never issue the first tile's copy
     uint32_t* status;        // deferred status word
     uint64_t* partials;      // per-CTA counts (scratch, grid entries)
     uint32_t* ticket;        // last-CTA ticket (scratch, zero between launches)
     uint64_t* d_count;       // result count
-    uint32_t* tile_counts;   // per-tile counts (scratch, ntiles entries; report only)
+    uint32_t* warp_counts;   // per-(tile, warp) counts (scratch, ntiles x 8; report only)
     uint64_t* d_pos;         // report output
     uint64_t cap;            // report capacity
     uint64_t spin_ns;        // limit of every bounded wait, in ns
-    uint32_t test_skip_copy; // test hook: 1 = never issue the first tile's copy
 };
 
 struct HistArgs {
@@ -53,21 +58,28 @@ struct HistArgs {
     uint64_t* d_hist;        // result, 256 entries
 };
 
-// Shared-memory bytes of one stage for patterns of length m.
+// Shared-memory bytes of one stage for patterns of length m: the tile, the
+// (m-1)-byte halo, the 0..15-byte misalignment and 32 bytes of load slack.
 inline uint32_t stage_bytes_for(uint32_t m) {
     uint32_t chunks = kTile / 16 + 2 + ((14u + m) >> 4);
     uint32_t b = chunks * 16;
     return (b + 127u) & ~127u;
 }
 
-// Header (barriers, stage descriptors, reduction slots) + the stage ring.
+// Header (barriers, stage descriptors, reduction slots), the per-warp queues
+// of surviving 4-start words (kQueueCap each; a warp-tile with more survivors
+// continues densely instead), then the stage ring.
 constexpr uint32_t kScanHeader = 512;
+constexpr uint32_t kQueueCap = 128;                                      // entries per warp
+constexpr uint32_t kQueueBytes = kConsumerWarps * kQueueCap * 8;           // 8 KiB
 
 inline size_t scan_smem_bytes(uint32_t stage_bytes, uint32_t stages) {
-    return kScanHeader + (size_t)stage_bytes * stages;
+    return kScanHeader + kQueueBytes + (size_t)stage_bytes * stages;
 }
 
 // Launch a scan kernel. `qc` holds m words (q << 8) | p[q] in compare order.
+// The first a.r of them (the peeled compares, whose order is free) are
+// regrouped by the 4-byte alignment of their text offset.
 cudaError_t launch_scan(int mode, bool seven, uint32_t grid, size_t smem, cudaStream_t s,
                         const ScanArgs& a, const uint32_t* qc);
 // Resident CTAs per SM of the scan kernel used for (m, mode, seven) with this smem.

@@ -1,366 +1,350 @@
 // Kernels of the SIMD-naive search (Tarhio, Holub, Giaquinta, Sec. 2), for sm_103a.
 //
 // scan_kernel  - Algorithms 2-4 on the GPU. A CTA owns a contiguous range of
-//                tiles of kTile = 8192 start positions. Each tile's bytes plus
-//                the (m-1)-byte halo are staged in shared memory by a 1-D TMA
-//                bulk copy (cp.async.bulk) into a ring of `stages` buffers
-//                completed through mbarriers. Warp w owns starts
-//                [1024w, 1024w+1024) of the tile; lane l owns the two 16-start
-//                chunks at 1024w + 16l and 1024w + 512 + 16l, so every 16-byte
-//                shared-memory load of a warp touches 512 consecutive bytes
-//                (no bank conflicts). For compare j at pattern position
-//                q = pi(j) a lane loads the two 16-byte chunks covering bytes
-//                s+q .. s+q+15 of its 16 starts s, aligns them with funnel
-//                shifts and tests 4 bytes per 32-bit word against the
-//                broadcast symbol p[q] with an exact SWAR zero-byte test. The
-//                result is the paper's SIMDcompare mask for 16 starts, kept as
-//                the high bit of each byte ("found"). The first r compares run
-//                without the zero test (loop peeling, Sec. 2.3); later ones
-//                leave when the whole warp's found masks are zero (the early
-//                exit of Algorithm 2, taken per warp of 1024 starts). The
-//                count is the popcount of found (Algorithm 2).
+//                tiles of kTile = 16384 start positions and runs nine warps:
+//                one producer and eight consumers.
+//
+//   Producer (warp 8): for each tile, waits until the consumers have
+//   released a ring slot (mbarrier `empty`), loads the at most 30 bytes of
+//   the tile that lie outside the text's 16-byte-aligned interior, and starts
+//   a 1-D TMA bulk copy (cp.async.bulk, no multicast) of the rest of the
+//   tile plus its (m-1)-byte halo into the slot, completing mbarrier `full`.
+//
+//   Consumer warp w owns starts [2048w, 2048w + 2048) of the tile; lane l
+//   owns the 16-start chunks at 2048w + 512c + 16l, c = 0..3, so each
+//   16-byte shared-memory load of a warp covers 512 consecutive bytes. The
+//   paper's SIMDcompare for pattern position q and symbol c is computed for
+//   16 starts s at a time: two 16-byte loads cover bytes s+q .. s+q+19,
+//   funnel shifts align them, and an exact SWAR zero-byte test of w ^ c..c
+//   leaves the result in the high bit of each byte ("found", four starts
+//   per 32-bit word).
+//
+//   Dense phase: the first r compares (in the order pi) run for every start
+//   with no zero test - the loop peeling of Sec. 2.3.
+//   Sparse phase: the 4-start words whose found bits survived are compacted,
+//   in position order, into a per-warp queue in shared memory; each lane
+//   then continues one word through compares r .. m-1 and leaves as soon as
+//   the word's found bits are zero - the early exit of Algorithm 2, taken per
+//   4-start word instead of per SIMD register. popcount(found) is the count
+//   (Algorithm 2); the reporting modes write the set bits' positions.
+//
 // hist_kernel  - byte histogram of the text (the frequencies of Sec. 2.2).
 //
 // Every wait on an mbarrier is bounded by a %globaltimer deadline; on expiry
-// the kernel records kStatusTimeout, waits (bounded) for its copies in
-// flight and leaves its tile loop.
-#include "sm_internal.h"
+// the kernel records kStatusTimeout, the producer waits (bounded) for the
+// copies it started, and every warp leaves its loop.
+#include "sm_device.cuh"
 
 namespace smk {
 namespace {
 
-constexpr uint32_t kFull = 0xffffffffu;
-constexpr uint64_t kEnd = ~0ull;
+using namespace dev;
+
 
 template <int MAXM>
 struct PatArg {
-    uint32_t qc[MAXM];   // compare j: (pi(j) << 8) | p[pi(j)]
+    uint32_t qc[MAXM];   // compare j: (e_j << 8) | p[pi(j)], e_j = (text address mod 16) + pi(j)
 };
 
 struct StageDesc {
     uint64_t tile;       // kEnd: no more tiles
-    uint64_t offset;     // output offset of the tile's first match (report)
+    uint64_t offset;     // report: output offset of the tile's first match
 };
-
-// ------------------------------------------------------------ PTX helpers
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void fence_mbar_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Wait for phase `parity` of `bar` to complete, at most limit_ns.
-__device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
-    while (!mbar_try_wait(bar, parity)) {
-        if (global_ns() - t0 > limit_ns) return false;
-    }
-    return true;
-}
-
-// ------------------------------------------------------------ compare core
-
-// found &= [byte of w == byte of P] in the high bit of each byte.
-// General bytes: exact zero-byte test of x = w ^ P (high bit of
-// ((x & 0x7F..) + 0x7F..) | x is set iff the byte is nonzero).
-// SEVEN: every byte of w and P is below 0x80, so x + 0x7F.. cannot carry
-// between bytes and its high bit alone marks a nonzero byte.
-template <bool SEVEN>
-__device__ __forceinline__ uint32_t keep_equal(uint32_t f, uint32_t w, uint32_t P) {
-    const uint32_t x = w ^ P;
-    if (SEVEN) return f & ~(x + 0x7F7F7F7Fu);
-    return f & ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x);
-}
-
-template <bool SEVEN, int D>
-__device__ __forceinline__ void cmp_chunk(const uint4& a, const uint4& b, uint32_t sh, uint32_t P,
-                                          uint32_t (&f)[4]) {
-    const uint32_t X[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) f[i] = keep_equal<SEVEN>(f[i], __funnelshift_r(X[D + i], X[D + i + 1], sh), P);
-}
-
-// One SIMDcompare for the lane's two chunks: v = (q << 8) | symbol.
-template <bool SEVEN>
-__device__ __forceinline__ void compare2(const uint4* __restrict__ b4, uint32_t c0, uint32_t v, uint32_t delta,
-                                         uint32_t (&f0)[4], uint32_t (&f1)[4]) {
-    const uint32_t e = delta + (v >> 8);
-    const uint32_t P = (v & 0xFFu) * 0x01010101u;
-    const uint32_t ci = c0 + (e >> 4);
-    const uint32_t sh = (e & 3u) << 3;
-    const uint4 a0 = b4[ci], b0 = b4[ci + 1], a1 = b4[ci + 32], b1 = b4[ci + 33];
-    switch ((e >> 2) & 3u) {
-        case 0: cmp_chunk<SEVEN, 0>(a0, b0, sh, P, f0); cmp_chunk<SEVEN, 0>(a1, b1, sh, P, f1); break;
-        case 1: cmp_chunk<SEVEN, 1>(a0, b0, sh, P, f0); cmp_chunk<SEVEN, 1>(a1, b1, sh, P, f1); break;
-        case 2: cmp_chunk<SEVEN, 2>(a0, b0, sh, P, f0); cmp_chunk<SEVEN, 2>(a1, b1, sh, P, f1); break;
-        default: cmp_chunk<SEVEN, 3>(a0, b0, sh, P, f0); cmp_chunk<SEVEN, 3>(a1, b1, sh, P, f1); break;
-    }
-}
-
-__device__ __forceinline__ uint32_t valid_mask(int64_t lim) {
-    // high bits of the bytes whose start index (relative to the word) is < lim
-    if (lim >= 4) return 0x80808080u;
-    if (lim <= 0) return 0u;
-    return 0x80808080u & ((1u << (8 * lim)) - 1u);
-}
-
-__device__ __forceinline__ uint32_t warp_sum_u32(uint32_t v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    return v;
-}
-
-__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    return v;
-}
 
 // ------------------------------------------------------------ scan kernel
 
+#ifndef SMK_MIN_BLOCKS
+#define SMK_MIN_BLOCKS 1
+#endif
 template <int MAXM, int MODE, bool SEVEN>
-__global__ void __launch_bounds__(kThreads) scan_kernel(const __grid_constant__ ScanArgs A,
+__global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __grid_constant__ ScanArgs A,
                                                         const __grid_constant__ PatArg<MAXM> P) {
     extern __shared__ __align__(128) uint8_t smem[];
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem);                 // [kMaxStages]
-    StageDesc* desc = reinterpret_cast<StageDesc*>(smem + 64);           // [kMaxStages]
-    uint32_t* wsum = reinterpret_cast<uint32_t*>(smem + 192);            // [8]
-    uint64_t* red = reinterpret_cast<uint64_t*>(smem + 224);             // [8]
-    uint32_t* flag = reinterpret_cast<uint32_t*>(smem + 288);
-    uint8_t* bufs = smem + kScanHeader;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);                  // [kMaxStages]
+    uint64_t* empty = reinterpret_cast<uint64_t*>(smem + 64);            // [kMaxStages]
+    StageDesc* desc = reinterpret_cast<StageDesc*>(smem + 128);          // [kMaxStages]
+    uint64_t* red = reinterpret_cast<uint64_t*>(smem + 256);             // [kConsumerWarps + 1]
+    uint32_t* flag = reinterpret_cast<uint32_t*>(smem + 336);
+    uint2* queues = reinterpret_cast<uint2*>(smem + kScanHeader);        // [kConsumerWarps][kQueueCap]
+    uint8_t* bufs = smem + kScanHeader + kQueueBytes;
 
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t SB = A.stage_bytes, S = A.stages, m = A.m;
+    const uint32_t SB = A.stage_bytes, S = A.stages, m = A.m, r = A.r, one = A.one;
     const uint64_t t_begin = (uint64_t)blockIdx.x * A.tiles_per_cta;
     const uint64_t t_end = min(t_begin + A.tiles_per_cta, A.ntiles);
-    const uintptr_t tb = reinterpret_cast<uintptr_t>(A.text);
-    const uint32_t delta = (uint32_t)(tb & 15u);
-    // text indices [lo_al, hi_al) are the 16-byte aligned interior reachable by TMA
-    const int64_t lo_al = (int64_t)(((tb + 15u) & ~(uintptr_t)15u) - tb);
-    const int64_t hi_al = (int64_t)((tb + A.n) & ~(uintptr_t)15u) - (int64_t)tb;
 
     if (tid == 0) {
-        for (uint32_t s = 0; s < S; ++s) mbar_init(&full[s], 1);
+        for (uint32_t s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kConsumerWarps);
+        }
         fence_mbar_init();
     }
     __syncthreads();
 
-    // Producer state, uniform in warp 0.
-    uint64_t cursor = t_begin, running = 0;
-    if (MODE == kModeWrite) {
-        if (warp == 0) {
+    uint32_t my_count = 0;
+
+    if (warp == kConsumerWarps) {
+        // ---------------------------------------------------------- producer
+        const uintptr_t tb = reinterpret_cast<uintptr_t>(A.text);
+        // text indices [lo_al, hi_al) form the 16-byte aligned interior
+        const int64_t lo_al = (int64_t)(((tb + 15u) & ~(uintptr_t)15u) - tb);
+        const int64_t hi_al = (int64_t)((tb + A.n) & ~(uintptr_t)15u) - (int64_t)tb;
+        uint64_t cursor = t_begin, running = 0;
+        if (MODE == kModeWrite) {
             uint64_t b = 0;
             for (uint32_t i = lane; i < blockIdx.x; i += 32) b += __ldcg(A.partials + i);
             running = warp_sum_u64(b);
-        } else if (warp == 1 && blockIdx.x == 0) {
-            uint64_t b = 0;
-            for (uint32_t i = lane; i < gridDim.x; i += 32) b += __ldcg(A.partials + i);
-            b = warp_sum_u64(b);
-            if (lane == 0 && b > A.cap) atomicOr(A.status, kStatusTrunc);
-        }
-    }
-
-    // Warp 0: choose the next tile, publish its descriptor, start its copy.
-    auto issue = [&](uint32_t s) {
-        uint64_t tile = kEnd;
-        uint32_t tcount = 0;
-        if (MODE != kModeWrite) {
-            if (cursor < t_end) tile = cursor++;
-        } else {
-            while (cursor < t_end) {
-                const uint64_t idx = cursor + lane;
-                const uint32_t c = idx < t_end ? __ldcg(A.tile_counts + idx) : 0u;
-                const uint32_t bal = __ballot_sync(kFull, c != 0);
-                if (bal) {
-                    const int k = __ffs(bal) - 1;
-                    tcount = __shfl_sync(kFull, c, k);
-                    tile = cursor + (uint64_t)k;
-                    cursor = tile + 1;
-                    break;
-                }
-                cursor += 32;
+            if (blockIdx.x == 0) {
+                uint64_t t = 0;
+                for (uint32_t i = lane; i < gridDim.x; i += 32) t += __ldcg(A.partials + i);
+                t = warp_sum_u64(t);
+                if (lane == 0 && t > A.cap) atomicOr(A.status, kStatusTrunc);
             }
         }
-        if (lane == 0) {
-            desc[s].tile = tile;
-            desc[s].offset = running;
+        uint32_t issued = 0;
+        // stage s and use count u of the ring for iteration it, kept without division
+        for (uint32_t it = 0, s = 0, u = 0;; ++it) {
+            if (u > 0) {
+                const bool ok = __all_sync(kFull, wait_bounded(&empty[s], (u - 1) & 1u, A.spin_ns));
+                if (!ok) {
+                    if (lane == 0) atomicOr(A.status, kStatusTimeout);
+                    break;
+                }
+            }
+            uint64_t tile = kEnd;
+            uint32_t tcount = 0;
+            if (MODE != kModeWrite) {
+                if (cursor < t_end) tile = cursor++;
+            } else {
+                // next tile with matches; lanes look at 4 tiles x 8 warp counts per step
+                while (cursor < t_end) {
+                    const uint64_t t = cursor + (lane >> 3);
+                    uint32_t c = t < t_end ? __ldcg(A.warp_counts + t * kConsumerWarps + (lane & 7u)) : 0u;
+                    c += __shfl_xor_sync(kFull, c, 1);
+                    c += __shfl_xor_sync(kFull, c, 2);
+                    c += __shfl_xor_sync(kFull, c, 4);
+                    const uint32_t bal = __ballot_sync(kFull, c != 0 && (lane & 7u) == 0);
+                    if (bal) {
+                        const int k = __ffs(bal) - 1;
+                        tcount = __shfl_sync(kFull, c, k);
+                        tile = cursor + (uint64_t)(k >> 3);
+                        cursor = tile + 1;
+                        break;
+                    }
+                    cursor += 4;
+                }
+            }
+            uint8_t* buf = bufs + (size_t)s * SB;
             uint32_t bytes = 0;
             uintptr_t ga = 0, g0 = 0;
             if (tile != kEnd) {
                 const uint64_t s0 = tile * kTile;
-                const uint64_t need_end = min(s0 + kTile + m - 1, A.n);
+                const int64_t need_end = (int64_t)min(s0 + kTile + m - 1, A.n);
+                const uint32_t delta = (uint32_t)(tb & 15u);
+                // bytes outside the aligned interior: head (< lo_al) and tail (>= hi_al), each < 16
+                const int64_t h_end = min(need_end, lo_al);
+                const int64_t t_beg = max((int64_t)s0, max(lo_al, max(hi_al, (int64_t)0)));
+                const int64_t xh = (int64_t)s0 + lane, xt = t_beg + lane;
+                if (xh < h_end) buf[delta + (xh - (int64_t)s0)] = A.text[xh];
+                if (xt < need_end) buf[delta + (xt - (int64_t)s0)] = A.text[xt];
                 g0 = (tb + s0) & ~(uintptr_t)15u;
                 ga = max(g0, tb + (uintptr_t)lo_al);
-                const uintptr_t ge = (tb + need_end + 15u) & ~(uintptr_t)15u;
+                const uintptr_t ge = (tb + (uint64_t)need_end + 15u) & ~(uintptr_t)15u;
                 const uintptr_t gb = min(ge, (tb + A.n) & ~(uintptr_t)15u);
                 bytes = gb > ga ? (uint32_t)(gb - ga) : 0u;
+                __threadfence_block();
             }
-            const bool skip = A.test_skip_copy && tile == 0;
-            fence_proxy_async();
-            mbar_arrive_expect_tx(&full[s], bytes);
-            if (bytes && !skip) bulk_g2s(bufs + (size_t)s * SB + (ga - g0), reinterpret_cast<const void*>(ga), bytes,
-                                         &full[s]);
-        }
-        running += tcount;
-    };
-
-    if (warp == 0)
-        for (uint32_t s = 0; s < S; ++s) issue(s);
-
-    uint32_t my_count = 0;
-    const uint32_t c0 = warp * 64u + lane;   // lane's first 16-byte chunk in the tile
-
-    for (uint32_t it = 0;; ++it) {
-        const uint32_t s = it % S;
-        const uint32_t par = (it / S) & 1u;
-        const bool ok = wait_bounded(&full[s], par, A.spin_ns);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) atomicOr(A.status, kStatusTimeout);
-            // let every copy this CTA started land before leaving
-            for (uint32_t k = 0; k < S; ++k) {
-                const uint32_t it2 = it + k;
-                (void)wait_bounded(&full[it2 % S], (it2 / S) & 1u, A.spin_ns);
+            __syncwarp();
+            if (lane == 0) {
+                desc[s].tile = tile;
+                desc[s].offset = running;
+                const bool skip = A.test_skip_copy && tile == 0;
+                fence_proxy_async();
+                mbar_arrive_expect_tx(&full[s], bytes);
+                if (bytes && !skip) bulk_g2s(buf + (ga - g0), reinterpret_cast<const void*>(ga), bytes, &full[s]);
             }
-            break;
-        }
-        const StageDesc d = desc[s];
-        if (d.tile == kEnd) break;
-
-        uint8_t* buf = bufs + (size_t)s * SB;
-        const uint64_t s0 = d.tile * kTile;
-        const uint64_t need_end = min(s0 + kTile + m - 1, A.n);
-
-        // bytes outside the aligned interior come in by plain loads
-        const int64_t h_end = min((int64_t)need_end, lo_al);
-        const int64_t t_beg = max((int64_t)s0, max(lo_al, max(hi_al, (int64_t)0)));
-        const bool ragged = (int64_t)s0 < h_end || t_beg < (int64_t)need_end;
-        if (ragged) {
-            for (int64_t x = (int64_t)s0 + tid; x < h_end; x += kThreads) buf[delta + (x - (int64_t)s0)] = A.text[x];
-            for (int64_t x = t_beg + tid; x < (int64_t)need_end; x += kThreads)
-                buf[delta + (x - (int64_t)s0)] = A.text[x];
-            __syncthreads();
-        }
-
-        uint32_t f0[4], f1[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) f0[i] = f1[i] = 0x80808080u;
-        const uint4* b4 = reinterpret_cast<const uint4*>(buf);
-        uint32_t j = 0;
-        for (; j < A.r; ++j) compare2<SEVEN>(b4, c0, P.qc[j], delta, f0, f1);
-        for (; j < m; ++j) {
-            const uint32_t any = (f0[0] | f0[1] | f0[2] | f0[3]) | (f1[0] | f1[1] | f1[2] | f1[3]);
-            if (!__any_sync(kFull, any != 0)) break;
-            compare2<SEVEN>(b4, c0, P.qc[j], delta, f0, f1);
-        }
-
-        const uint64_t U = min((uint64_t)kTile, A.nstarts - s0);   // valid starts in this tile
-        if (U < kTile) {
-            const int64_t u0 = (int64_t)(warp * 1024u + lane * 16u);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                f0[i] &= valid_mask((int64_t)U - (u0 + 4 * i));
-                f1[i] &= valid_mask((int64_t)U - (u0 + 512 + 4 * i));
+            issued = it + 1;
+            if (tile == kEnd) break;
+            running += tcount;
+            if (++s == S) {
+                s = 0;
+                ++u;
             }
         }
+        // let every copy this CTA started land before the CTA can leave: the
+        // last use of each stage is use (issued - 1 - stage) / S (if any)
+        if (lane == 0)
+            for (uint32_t st = 0; st < S && st < issued; ++st)
+                (void)wait_bounded(&full[st], ((issued - 1 - st) / S) & 1u, A.spin_ns);
+        __syncwarp();
+    } else {
+        // ---------------------------------------------------------- consumers
+        uint2* q = queues + warp * kQueueCap;
+        const uint32_t c0 = warp * (kWarpStarts / 16) + lane;   // lane's first 16-byte chunk in the tile
+        const uint32_t wq = warp * (kWarpStarts / 4);           // warp's first word in the tile
+        for (uint32_t s = 0, phase = 0;; ) {
+            const bool ok = __all_sync(kFull, wait_bounded(&full[s], phase, A.spin_ns));
+            if (!ok) {
+                if (lane == 0) atomicOr(A.status, kStatusTimeout);
+                break;
+            }
+            const StageDesc d = desc[s];
+            if (d.tile == kEnd) break;
+            const uint8_t* buf = bufs + (size_t)s * SB;
+            const uint4* b4 = reinterpret_cast<const uint4*>(buf);
+            const uint32_t* b32 = reinterpret_cast<const uint32_t*>(buf);
+            const uint64_t s0 = d.tile * kTile;
 
-        uint32_t k0 = 0, k1 = 0;
+            // dense phase: r compares for all starts of the warp; the peeled
+            // compares arrive grouped by word alignment (A.nd)
+            uint32_t f[kChunks][4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) { k0 += __popc(f0[i]); k1 += __popc(f1[i]); }
+            for (int c = 0; c < kChunks; ++c)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) f[c][i] = 0x80808080u;
+            {
+                uint32_t j = 0;
+                for (uint32_t k = 0; k < A.nd[0]; ++k, ++j) compare_chunks<SEVEN, 0>(b4, c0, P.qc[j], one, f);
+                for (uint32_t k = 0; k < A.nd[1]; ++k, ++j) compare_chunks<SEVEN, 1>(b4, c0, P.qc[j], one, f);
+                for (uint32_t k = 0; k < A.nd[2]; ++k, ++j) compare_chunks<SEVEN, 2>(b4, c0, P.qc[j], one, f);
+                for (uint32_t k = 0; k < A.nd[3]; ++k, ++j) compare_chunks<SEVEN, 3>(b4, c0, P.qc[j], one, f);
+            }
 
-        if (MODE != kModeWrite) {
-            my_count += k0 + k1;
+            if (s0 + kTile > A.nstarts) {   // last tile: clear starts beyond n - m
+                const int64_t lim = (int64_t)(A.nstarts - s0) - (int64_t)(warp * kWarpStarts + lane * 16u);
+#pragma unroll
+                for (int c = 0; c < kChunks; ++c)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) f[c][i] &= valid_mask(lim - (512 * c + 4 * i));
+            }
+
+            uint32_t any = 0;
+#pragma unroll
+            for (int c = 0; c < kChunks; ++c) any |= (f[c][0] | f[c][1]) | (f[c][2] | f[c][3]);
+
+            uint32_t tile_count = 0;   // this lane's share of the warp's matches in the tile
+            if (MODE == kModeCount && r >= m) {
+                tile_count = count_flags<kChunks>(f);
+            } else if (__any_sync(kFull, any != 0u)) {
+                // compact surviving words in position order: chunk 0 of all
+                // lanes, then chunk 1, ... (4 bits per chunk, counts in bytes)
+                uint32_t a[kChunks], packed = 0;
+#pragma unroll
+                for (int c = 0; c < kChunks; ++c) {
+                    a[c] = 0;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) a[c] |= (f[c][i] != 0u) << i;
+                    packed |= (uint32_t)__popc(a[c]) << (8 * c);
+                }
+                const uint32_t incl = warp_incl_scan(packed, lane);
+                const uint32_t tot = __shfl_sync(kFull, incl, 31);
+                const uint32_t qn = (tot & 0xFFu) + ((tot >> 8) & 0xFFu) + ((tot >> 16) & 0xFFu) + (tot >> 24);
+
+                uint64_t out = 0;
+                if (MODE == kModeWrite) {
+                    const uint32_t cw = lane < warp ? __ldcg(A.warp_counts + d.tile * kConsumerWarps + lane) : 0u;
+                    out = d.offset + warp_sum_u32(cw);
+                }
+                if (qn <= kQueueCap) {
+                    uint32_t base = 0;
+#pragma unroll
+                    for (int c = 0; c < kChunks; ++c) {
+                        uint32_t p = base + ((incl >> (8 * c)) & 0xFFu) - ((packed >> (8 * c)) & 0xFFu);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            if (a[c] & (1u << i)) q[p++] = make_uint2(128u * c + lane * 4u + i, f[c][i]);
+                        base += (tot >> (8 * c)) & 0xFFu;
+                    }
+                    __syncwarp();
+                    // sparse phase: each lane continues one word with its own early exit
+                    for (uint32_t qb = 0; qb < qn; qb += 32) {
+                        const uint32_t e = qb + lane;
+                        uint32_t wi = 0, fw = 0;
+                        if (e < qn) {
+                            const uint2 x = q[e];
+                            wi = x.x;
+                            fw = x.y;
+                        }
+                        for (uint32_t j = r; j < m && fw; ++j) fw = compare_word<SEVEN>(b32, wq + wi, P.qc[j], one, fw);
+                        const uint32_t k = __popc(fw);
+                        if (MODE == kModeWrite) {
+                            const uint32_t inc = warp_incl_scan(k, lane);
+                            uint64_t rk = out + inc - k;
+                            const uint64_t pos0 = s0 + warp * kWarpStarts + 4u * wi;
+                            while (fw) {
+                                const uint32_t b = (uint32_t)(__ffs(fw) - 1) >> 3;
+                                if (rk < A.cap) A.d_pos[rk] = pos0 + b;
+                                ++rk;
+                                fw &= fw - 1;
+                            }
+                            out += __shfl_sync(kFull, inc, 31);
+                        } else {
+                            tile_count += k;
+                        }
+                    }
+                    __syncwarp();   // the queue is reused by the next tile
+                } else {
+                    // more survivors than the queue holds: continue the remaining
+                    // compares for all of the warp's starts, leaving when all are dead
+                    for (uint32_t j = r; j < m; ++j) {
+                        uint32_t an = 0;
+#pragma unroll
+                        for (int c = 0; c < kChunks; ++c) an |= (f[c][0] | f[c][1]) | (f[c][2] | f[c][3]);
+                        if (!__any_sync(kFull, an != 0u)) break;
+                        const uint32_t v = P.qc[j];
+                        switch ((v >> 10) & 3u) {
+                            case 0: compare_chunks<SEVEN, 0>(b4, c0, v, one, f); break;
+                            case 1: compare_chunks<SEVEN, 1>(b4, c0, v, one, f); break;
+                            case 2: compare_chunks<SEVEN, 2>(b4, c0, v, one, f); break;
+                            default: compare_chunks<SEVEN, 3>(b4, c0, v, one, f); break;
+                        }
+                    }
+                    if (MODE == kModeWrite) {
+                        // positions in order: chunk c of all lanes, words, bytes
+                        uint32_t kc[kChunks];
+#pragma unroll
+                        for (int c = 0; c < kChunks; ++c)
+                            kc[c] = __popc(f[c][0]) + __popc(f[c][1]) + __popc(f[c][2]) + __popc(f[c][3]);
+                        const uint32_t i01 = warp_incl_scan(kc[0] | (kc[1] << 16), lane);
+                        const uint32_t i23 = warp_incl_scan(kc[2] | (kc[3] << 16), lane);
+                        const uint32_t t01 = __shfl_sync(kFull, i01, 31), t23 = __shfl_sync(kFull, i23, 31);
+                        const uint32_t incs[4] = {i01 & 0xFFFFu, i01 >> 16, i23 & 0xFFFFu, i23 >> 16};
+                        const uint32_t tots[4] = {t01 & 0xFFFFu, t01 >> 16, t23 & 0xFFFFu, t23 >> 16};
+                        uint64_t cb = out;
+#pragma unroll
+                        for (int c = 0; c < kChunks; ++c) {
+                            uint64_t rk = cb + incs[c] - kc[c];
+                            const uint64_t pos0 = s0 + warp * kWarpStarts + 512u * c + 16u * lane;
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                uint32_t fw = f[c][i];
+                                while (fw) {
+                                    const uint32_t b = (uint32_t)(__ffs(fw) - 1) >> 3;
+                                    if (rk < A.cap) A.d_pos[rk] = pos0 + 4u * i + b;
+                                    ++rk;
+                                    fw &= fw - 1;
+                                }
+                            }
+                            cb += tots[c];
+                        }
+                    } else {
+                        tile_count += count_flags<kChunks>(f);
+                    }
+                }
+            }
+
             if (MODE == kModeTileCount) {
-                const uint32_t ws = warp_sum_u32(k0 + k1);
-                if (lane == 0) wsum[warp] = ws;
+                const uint32_t wsum = warp_sum_u32(tile_count);
+                if (lane == 0) A.warp_counts[d.tile * kConsumerWarps + warp] = wsum;
             }
-        } else {
-            // ranks: warps in order, then chunk 0 of all lanes, then chunk 1
-            uint32_t i0 = k0, i1 = k1;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y0 = __shfl_up_sync(kFull, i0, o), y1 = __shfl_up_sync(kFull, i1, o);
-                if (lane >= (uint32_t)o) { i0 += y0; i1 += y1; }
+            my_count += tile_count;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+            if (++s == S) {
+                s = 0;
+                phase ^= 1u;
             }
-            const uint32_t t0 = __shfl_sync(kFull, i0, 31), t1 = __shfl_sync(kFull, i1, 31);
-            if (lane == 0) wsum[warp] = t0 + t1;
-            __syncthreads();
-            uint64_t base = d.offset;
-            for (uint32_t w = 0; w < warp; ++w) base += wsum[w];
-            uint64_t r0 = base + (i0 - k0), r1 = base + t0 + (i1 - k1);
-            const uint64_t p0 = s0 + warp * 1024u + lane * 16u;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                uint32_t f = f0[i];
-                while (f) {
-                    const uint32_t b = (uint32_t)(__ffs(f) - 1) >> 3;
-                    if (r0 < A.cap) A.d_pos[r0] = p0 + 4 * i + b;
-                    ++r0;
-                    f &= f - 1;
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                uint32_t f = f1[i];
-                while (f) {
-                    const uint32_t b = (uint32_t)(__ffs(f) - 1) >> 3;
-                    if (r1 < A.cap) A.d_pos[r1] = p0 + 512 + 4 * i + b;
-                    ++r1;
-                    f &= f - 1;
-                }
-            }
-        }
-
-        __syncthreads();   // everyone is done with buffer s and with wsum
-        if (warp == 0) {
-            if (MODE == kModeTileCount && lane == 0) {
-                uint32_t tc = 0;
-                for (int w = 0; w < kThreads / 32; ++w) tc += wsum[w];
-                A.tile_counts[d.tile] = tc;
-            }
-            issue(s);
         }
     }
 
@@ -372,7 +356,7 @@ __global__ void __launch_bounds__(kThreads) scan_kernel(const __grid_constant__ 
     __syncthreads();
     if (tid == 0) {
         uint64_t tot = 0;
-        for (int w = 0; w < kThreads / 32; ++w) tot += red[w];
+        for (int w = 0; w < kConsumerWarps + 1; ++w) tot += red[w];
         A.partials[blockIdx.x] = tot;
         __threadfence();
         const uint32_t t = atomicAdd(A.ticket, 1u);
@@ -389,7 +373,7 @@ __global__ void __launch_bounds__(kThreads) scan_kernel(const __grid_constant__ 
         __syncthreads();
         if (tid == 0) {
             uint64_t tot = 0;
-            for (int w = 0; w < kThreads / 32; ++w) tot += red[w];
+            for (int w = 0; w < kConsumerWarps + 1; ++w) tot += red[w];
             *A.d_count = tot;
             *A.ticket = 0u;
         }
@@ -456,10 +440,25 @@ __global__ void __launch_bounds__(kHistThreads) hist_kernel(const HistArgs A) {
 // ------------------------------------------------------------ dispatch
 
 template <int MAXM, int MODE, bool SEVEN>
-cudaError_t launch_one(uint32_t grid, size_t smem, cudaStream_t st, const ScanArgs& a, const uint32_t* qc) {
+cudaError_t launch_one(uint32_t grid, size_t smem, cudaStream_t st, const ScanArgs& a0, const uint32_t* qc) {
     PatArg<MAXM> p;
-    for (uint32_t j = 0; j < a.m; ++j) p.qc[j] = qc[j];
-    for (uint32_t j = a.m; j < (uint32_t)MAXM; ++j) p.qc[j] = 0;
+    ScanArgs a = a0;
+    // add the text's misalignment to every position; stable-sort the peeled
+    // compares by word alignment class d = (e >> 2) & 3
+    const uint32_t delta = (uint32_t)(reinterpret_cast<uintptr_t>(a.text) & 15u);
+    uint32_t j = 0;
+    for (uint32_t d = 0; d < 4; ++d) {
+        a.nd[d] = 0;
+        for (uint32_t k = 0; k < a.r; ++k) {
+            const uint32_t v = qc[k] + (delta << 8);
+            if (((v >> 10) & 3u) == d) {
+                p.qc[j++] = v;
+                ++a.nd[d];
+            }
+        }
+    }
+    for (; j < a.m; ++j) p.qc[j] = qc[j] + (delta << 8);
+    for (; j < (uint32_t)MAXM; ++j) p.qc[j] = 0;
     scan_kernel<MAXM, MODE, SEVEN><<<grid, kThreads, smem, st>>>(a, p);
     return cudaGetLastError();
 }

@@ -12,8 +12,8 @@
 //   [0, 4)        deferred status bits (written by kernels, not read back)
 //   [4, 8)        last-CTA ticket (must be 0 when a call starts)
 //   [256, ..)     partial counts, kMaxCtas x uint64
-//   [.., end)     per-tile match counts, kMaxTiles x uint32
-// kMaxTiles bounds the text: at most kMaxTiles * 8192 start positions.
+//   [.., end)     per-(tile, warp) match counts, kMaxTiles x 8 x uint32
+// kMaxTiles bounds the text: at most kMaxTiles * 16384 start positions.
 #include "sm.h"
 #include "sm_internal.h"
 
@@ -24,10 +24,10 @@
 namespace {
 
 constexpr uint32_t kMaxCtas = 2048;
-constexpr uint32_t kMaxTiles = 65536;
+constexpr uint32_t kMaxTiles = 16384;
 constexpr size_t kPartialsOff = 256;
-constexpr size_t kTileCountsOff = kPartialsOff + sizeof(uint64_t) * kMaxCtas;
-constexpr size_t kScratchBytes = kTileCountsOff + sizeof(uint32_t) * kMaxTiles;   // 278,784 bytes
+constexpr size_t kWarpCountsOff = kPartialsOff + sizeof(uint64_t) * kMaxCtas;
+constexpr size_t kScratchBytes = kWarpCountsOff + sizeof(uint32_t) * kMaxTiles * smk::kConsumerWarps;  // 540,928 bytes
 
 static_assert((uint64_t)kMaxTiles * smk::kTile == SM_NOALLOC_MAX_STARTS, "header limit out of date");
 
@@ -115,7 +115,8 @@ extern "C" sm_status sm_report_noalloc(const uint8_t* d_text, uint64_t n, const 
     a.status = reinterpret_cast<uint32_t*>(su.scratch);
     a.ticket = reinterpret_cast<uint32_t*>(su.scratch + 4);
     a.partials = reinterpret_cast<uint64_t*>(su.scratch + kPartialsOff);
-    a.tile_counts = reinterpret_cast<uint32_t*>(su.scratch + kTileCountsOff);
+    a.warp_counts = reinterpret_cast<uint32_t*>(su.scratch + kWarpCountsOff);
+    a.one = 1;
     a.d_count = d_count;
     a.spin_ns = 1000000000ull;
 

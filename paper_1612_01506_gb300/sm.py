@@ -17,10 +17,10 @@ from .build import LIB as _LIB_PATH
 
 SM_OK, SM_EINVAL, SM_ENOMEM, SM_ECUDA, SM_ETRUNC, SM_ETIMEOUT, SM_ENOTSUP = range(7)
 SM_MAX_M = 4096
-SM_TILE_STARTS = 8192
+SM_TILE_STARTS = 16384
 SM_ORDER_H, SM_ORDER_HS = 1, 2
 SM_KNOB_STAGES, SM_KNOB_GRID, SM_KNOB_SPIN_NS, SM_KNOB_TEST_SKIP_COPY = 1, 2, 3, 4
-SM_NOALLOC_MAX_STARTS = 65536 * 8192
+SM_NOALLOC_MAX_STARTS = 16384 * 16384
 
 # Every symbol the header declares (checked against include/sm.h by the tests).
 EXPORTS = ("sm_create", "sm_destroy", "sm_last_error", "sm_status_string", "sm_sync", "sm_set_knob",
@@ -42,7 +42,8 @@ _lib = None
 
 
 def library_path() -> str:
-    return _LIB_PATH
+    """The CUDA library in use: $SM_LIBRARY if set, else the in-tree build."""
+    return os.environ.get("SM_LIBRARY") or _LIB_PATH
 
 
 def load():
@@ -50,9 +51,10 @@ def load():
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(_LIB_PATH):
-        raise RuntimeError(f"CUDA library not built: {_LIB_PATH} is missing (run __graft_entry__.build())")
-    lib = C.CDLL(_LIB_PATH)
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing (run __graft_entry__.build())")
+    lib = C.CDLL(path)
     vp, u8p, u32p, u64p = C.c_void_p, C.POINTER(C.c_uint8), C.POINTER(C.c_uint32), C.POINTER(C.c_uint64)
     st, u32, u64 = C.c_int, C.c_uint32, C.c_uint64
     sig = {

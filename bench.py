@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--peel", type=int, default=0, help="peeling factor r (0 = automatic)")
     ap.add_argument("--stages", type=int, default=0, help="scan pipeline depth (0 = library default)")
     ap.add_argument("--ctas", type=int, default=0, help="scan CTAs (0 = one resident wave)")
+    ap.add_argument("--batch", action="store_true",
+                    help="also measure batched counting (256 MiB Markov text, 4096 patterns)")
+    ap.add_argument("--batch-only", action="store_true", help="measure only the batched counting")
     return ap.parse_args()
 
 
@@ -347,6 +350,69 @@ def run_e2e(args, ctx, kinds, ms, pats, hists, texts, dev, stream, d_texts, vari
             "h2d_bytes_per_step": h2d // steps, "d2h_bytes_per_step": d2h // steps}
 
 
+# ---------------------------------------------------------------- batched counting
+
+def run_batch(args, local, steps=3, warmup=2):
+    """Batched counting: one 256 MiB Markov-95 text, 4096 patterns with lengths
+    log-uniform in [2, 1024], 80% copied from the text and 20% random over its
+    alphabet; int64 counts. patterns*GB/s = patterns x text bytes / time, for
+    the one persistent launch and for one sm_count launch per pattern."""
+    import torch
+    from paper_1612_01506_gb300 import sm, synth
+    n, npat = 256 << 20, 4096
+    t = synth.markov95(n, seed=0, stream=synth.stream_id("batch", "markov95"))
+    r = np.random.default_rng(0)
+    lens = np.exp(r.uniform(np.log(2), np.log(1024), npat)).astype(np.int64)
+    offs = synth.below(npat, n, 0, synth.stream_id("batch", "offs"))
+    alpha = np.frombuffer(synth.MARKOV95, np.uint8)
+    pats = []
+    for k in range(npat):
+        m = int(lens[k])
+        if r.random() < 0.8:
+            o = min(int(offs[k]), n - m)
+            pats.append(t[o:o + m].tobytes())
+        else:
+            pats.append(alpha[r.integers(0, alpha.size, m)].tobytes())
+    dev = torch.device("cuda", local)
+    ctx = sm.sm_create(local)
+    d = torch.from_numpy(t).to(dev)
+    off = np.array([0, n], np.int64)
+    b = sm.sm_batch_create(ctx, d, off, pats, np.zeros(npat, np.int32))
+    out = torch.zeros(npat, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        sm.sm_batch_count(b, out=out)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(steps):
+        sm.sm_batch_count(b, out=out)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_batch = ev0.elapsed_time(ev1) / 1e3 / steps
+    batch_counts = out.cpu().numpy().copy()
+    # one launch per pattern, same orders (rarest first under the text histogram)
+    hist = sm.sm_histogram(ctx, d).cpu().numpy().view(np.uint64).copy()
+    single = torch.zeros(npat, dtype=torch.int64, device=dev)
+    orders = [sm.sm_order(p, hist) for p in pats]
+    for k in range(min(npat, 64)):
+        sm.sm_count(ctx, d, pats[k], pi=orders[k], hist=hist, out=single[k:k + 1])
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for k in range(npat):
+        sm.sm_count(ctx, d, pats[k], pi=orders[k], hist=hist, out=single[k:k + 1])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_single = ev0.elapsed_time(ev1) / 1e3
+    agree = bool(np.array_equal(single.cpu().numpy(), batch_counts))
+    pgb = npat * n / 1e9
+    return {"workload": "batched counting: 256 MiB Markov-95 text, 4096 patterns, m log-uniform [2,1024], "
+                        "80% from the text", "batch_ms": round(t_batch * 1e3, 3),
+            "batch_patterns_gbs": round(pgb / t_batch, 1), "single_launch_ms": round(t_single * 1e3, 3),
+            "single_launch_patterns_gbs": round(pgb / t_single, 1), "speedup": round(t_single / t_batch, 2),
+            "counts_agree": agree}
+
+
 # ---------------------------------------------------------------- CPU oracle
 
 def run_cpu_baseline(args, budget_s: float):
@@ -413,6 +479,10 @@ def main():
         print(json.dumps(line), flush=True)
         return
 
+    if args.batch_only:
+        if rank == 0:
+            print(json.dumps({"batch": run_batch(args, local)}), flush=True)
+        return
     res = run_gpu(args, world, rank, local)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -424,6 +494,8 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
                 "config": config_block(args, world), "roofline": res["roofline"], "cpu_baseline": cpu,
                 "e2e": res["e2e"], "gpu_launches": res["launches"], "clocks": res["clocks"]}
+        if args.batch and world == 1:
+            line["batch"] = run_batch(args, local)
         print(json.dumps(line), flush=True)
         if args.json_detail:
             with open(args.json_detail, "w") as f:

@@ -186,6 +186,48 @@ sm_status sm_report_ex(sm_ctx* ctx, const uint8_t* d_text, uint64_t n,
                        const sm_search_opts* opts, uint64_t* d_pos, uint64_t cap,
                        uint64_t* d_count, sm_stream_t stream);
 
+/* ---------------------------------------------------------------- batch */
+/*
+ * Batched counting: many patterns of uneven lengths over many texts, with
+ * each staged text tile tested against every pattern of its text so that the
+ * patterns share one pass over the text (Algorithms 2-4 applied to a batch).
+ *
+ * Texts are packed back to back in d_texts: text x is
+ * d_texts[h_text_off[x] .. h_text_off[x+1]), h_text_off[0] = 0, offsets
+ * non-decreasing. Patterns are packed in h_pats the same way with h_pat_off
+ * (npats + 1 entries, lengths 1..SM_MAX_M); pattern k is searched in text
+ * h_pat_text[k] (any order).
+ *
+ * sm_batch_create plans the batch (synchronous on `stream`, allocates device
+ * tables): per-text byte histograms, each pattern's rarest-first order under
+ * its own text's frequencies (Sec. 2.2) and peel factor (Sec. 2.3); patterns
+ * with a symbol that never occurs in their text, or longer than it, are not
+ * scanned (count 0). The plan keeps d_texts and reads it at every count.
+ * sm_batch_count enqueues one memset and one persistent kernel that writes
+ * d_counts[k] (int64, npats entries) for every pattern; it allocates nothing
+ * and may be captured in a CUDA graph. sm_batch_destroy waits for the device
+ * and frees the plan.
+ */
+typedef struct sm_batch sm_batch;
+sm_status sm_batch_create(sm_ctx* ctx, const uint8_t* d_texts, const int64_t* h_text_off, uint32_t ntexts,
+                          const uint8_t* h_pats, const int64_t* h_pat_off, const int32_t* h_pat_text,
+                          uint32_t npats, sm_batch** out, sm_stream_t stream);
+sm_status sm_batch_count(sm_batch* batch, int64_t* d_counts, sm_stream_t stream);
+void sm_batch_destroy(sm_batch* batch);
+
+/*
+ * One-shot form with device-resident metadata: d_text_off, d_pat_off,
+ * d_pat_text and the packed patterns d_pats are device arrays laid out as
+ * above. Counts go to d_counts. When d_pos is not NULL, the positions of
+ * pattern k are written in ascending order to d_pos[d_pos_off[k] ..
+ * d_pos_off[k+1]) (at most that many; the count stays the full count).
+ * Synchronous: copies the metadata to the host, plans, runs and waits.
+ */
+sm_status sm_count_batch(sm_ctx* ctx, const uint8_t* d_texts, const int64_t* d_text_off, uint32_t ntexts,
+                         const uint8_t* d_pats, const int64_t* d_pat_off, const int32_t* d_pat_text,
+                         uint32_t npats, int64_t* d_counts, uint64_t* d_pos, const int64_t* d_pos_off,
+                         sm_stream_t stream);
+
 /* ------------------------------------------------------- no allocation */
 /*
  * sm_report_noalloc - the report of sm_report for callers that must not

@@ -222,6 +222,15 @@ sm_status zero_count(uint64_t* d_count, cudaStream_t s) {
 
 }  // namespace
 
+// Accessors for the other translation units of the library.
+sm_status sm_fail_internal(sm_status s, const char* msg) { return fail(s, "%s", msg); }
+int sm_ctx_device(const sm_ctx* c) { return c->device; }
+int sm_ctx_num_sms(const sm_ctx* c) { return c->num_sms; }
+size_t sm_ctx_max_smem(const sm_ctx* c) { return c->max_smem; }
+uint32_t* sm_ctx_status(const sm_ctx* c) { return c->d_status; }
+uint64_t sm_ctx_spin_ns(const sm_ctx* c) { return c->spin_ns; }
+uint32_t sm_ctx_stages(const sm_ctx* c) { return c->stages; }
+
 extern "C" {
 
 const char* sm_last_error(void) { return g_err.c_str(); }

@@ -1,0 +1,581 @@
+// Batched counting: many patterns of uneven lengths over many texts in one
+// persistent launch (the batched form of the SIMD-naive search of Tarhio,
+// Holub, Giaquinta, Algorithms 2-4).
+//
+// Work items are (text, tile) pairs over the packed texts. A CTA owns a
+// contiguous range of items; its producer warp stages each tile (plus the
+// halo of the text's longest pattern) once, and the consumer warps test every
+// pattern of that text against the staged tile with the same dense/sparse
+// compare core as the single-pattern scan, so all patterns of a text share one
+// pass over HBM. Counts gather in shared memory per pattern and are added to
+// the output once per CTA.
+//
+// The plan (sm_batch_create) runs on the host once per batch: per-text byte
+// histograms (one launch), the rarest-first order of each pattern under its
+// own text's frequencies (Sec. 2.2), the peel factor, the 7-bit compare where
+// the text allows it, and patterns with a symbol absent from their text are
+// dropped (their count is 0). sm_batch_count is then one memset and one
+// launch, and can be captured in a CUDA graph.
+#include "sm.h"
+#include "sm_device.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+namespace smk {
+namespace {
+
+using namespace dev;
+
+constexpr uint32_t kMaxSlots = 4096;   // patterns one CTA counts in shared memory
+constexpr uint32_t kHistChunk = 65536; // bytes per histogram work item
+
+struct BatchText {        // a text, or one group of <= kMaxSlots of its patterns
+    uint64_t off;         // byte offset in the packed texts
+    uint64_t n;           // length
+    uint64_t item_begin;  // first work item (tile) of this entry
+    uint32_t pbeg, pend;  // its patterns [pbeg, pend) in the pattern table
+    uint32_t maxm, pad;
+};
+
+struct BatchPat {
+    uint32_t qc_off;      // first compare descriptor in the qc table
+    uint32_t m, r;
+    uint32_t nd;          // peeled compares per alignment class, 8 bits each
+    uint32_t out;         // index of the pattern in the caller's arrays
+    uint32_t seven;       // 1: text and pattern are 7-bit
+};
+
+struct BatchArgs {
+    const uint8_t* texts;
+    const BatchText* tx;        // ntx + 1 entries (the last one: item_begin = total items)
+    uint32_t ntx;
+    const BatchPat* pats;
+    const uint32_t* qc;
+    const uint64_t* cta_items;  // grid + 1: CTA b takes items [cta_items[b], cta_items[b+1])
+    const uint32_t* cta_pbase;  // grid: first pattern counted by CTA b (its slot 0)
+    int64_t* d_counts;
+    uint32_t stage_bytes, stages, one, nslots;
+    uint32_t* status;
+    uint64_t spin_ns;
+};
+
+struct BatchDesc {
+    uint64_t k;   // tile within the text entry
+    uint32_t x;   // text entry, ~0u: no more items
+    uint32_t pad;
+};
+
+
+__global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constant__ BatchArgs A) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* empty = reinterpret_cast<uint64_t*>(smem + 64);
+    BatchDesc* desc = reinterpret_cast<BatchDesc*>(smem + 128);
+    uint2* queues = reinterpret_cast<uint2*>(smem + kScanHeader);
+    uint32_t* slots = reinterpret_cast<uint32_t*>(smem + kScanHeader + kQueueBytes);
+    uint8_t* bufs = smem + kScanHeader + kQueueBytes + ((A.nslots * 4u + 127u) & ~127u);
+
+    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t SB = A.stage_bytes, S = A.stages, one = A.one;
+    const uint64_t i0 = A.cta_items[blockIdx.x], i1 = A.cta_items[blockIdx.x + 1];
+    const uint32_t pbase = A.cta_pbase[blockIdx.x];
+
+    if (tid == 0) {
+        for (uint32_t s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kConsumerWarps);
+        }
+        fence_mbar_init();
+    }
+    for (uint32_t i = tid; i < A.nslots; i += kThreads) slots[i] = 0;
+    __syncthreads();
+
+    if (warp == kConsumerWarps) {
+        // ---------------------------------------------------------- producer
+        uint32_t x = 0;
+        {   // last entry whose first item is <= i0
+            uint32_t lo = 0, hi = A.ntx;
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (A.tx[mid].item_begin <= i0) lo = mid; else hi = mid;
+            }
+            x = lo;
+        }
+        uint64_t cursor = i0;
+        uint32_t issued = 0;
+        for (uint32_t it = 0, s = 0, u = 0;; ++it) {
+            if (u > 0) {
+                const bool ok = __all_sync(kFull, wait_bounded(&empty[s], (u - 1) & 1u, A.spin_ns));
+                if (!ok) {
+                    if (lane == 0) atomicOr(A.status, kStatusTimeout);
+                    break;
+                }
+            }
+            uint8_t* buf = bufs + (size_t)s * SB;
+            BatchDesc d{0, ~0u, 0};
+            TileCopy cp{0, 0, 0};
+            if (cursor < i1) {
+                const uint64_t item = cursor++;
+                while (A.tx[x + 1].item_begin <= item) ++x;
+                const BatchText T = A.tx[x];
+                d.x = x;
+                d.k = item - T.item_begin;
+                const uint64_t s0 = d.k * kTile;
+                cp = stage_ragged(buf, A.texts + T.off, T.n, s0, min(s0 + kTile + T.maxm - 1, T.n), lane);
+            }
+            __syncwarp();
+            if (lane == 0) {
+                desc[s] = d;
+                fence_proxy_async();
+                mbar_arrive_expect_tx(&full[s], cp.bytes);
+                if (cp.bytes) bulk_g2s(buf + cp.dst_off, reinterpret_cast<const void*>(cp.src), cp.bytes, &full[s]);
+            }
+            issued = it + 1;
+            if (d.x == ~0u) break;
+            if (++s == S) {
+                s = 0;
+                ++u;
+            }
+        }
+        if (lane == 0)
+            for (uint32_t st = 0; st < S && st < issued; ++st)
+                (void)wait_bounded(&full[st], ((issued - 1 - st) / S) & 1u, A.spin_ns);
+        __syncwarp();
+    } else {
+        // ---------------------------------------------------------- consumers
+        uint2* q = queues + warp * kQueueCap;
+        const uint32_t c0 = warp * (kWarpStarts / 16) + lane;
+        const uint32_t wq = warp * (kWarpStarts / 4);
+        for (uint32_t s = 0, phase = 0;;) {
+            const bool ok = __all_sync(kFull, wait_bounded(&full[s], phase, A.spin_ns));
+            if (!ok) {
+                if (lane == 0) atomicOr(A.status, kStatusTimeout);
+                break;
+            }
+            const BatchDesc d = desc[s];
+            if (d.x == ~0u) break;
+            const uint8_t* buf = bufs + (size_t)s * SB;
+            const uint4* b4 = reinterpret_cast<const uint4*>(buf);
+            const uint32_t* b32 = reinterpret_cast<const uint32_t*>(buf);
+            const uint64_t s0 = d.k * kTile;
+            const BatchText T = A.tx[d.x];
+            for (uint32_t p = T.pbeg; p < T.pend; ++p) {
+                const BatchPat P = A.pats[p];
+                const uint64_t nst = T.n - P.m + 1;   // the plan keeps only patterns with m <= n
+                if (s0 >= nst) continue;
+                const GlobalQC qc{A.qc + P.qc_off};
+                const uint32_t nd0 = P.nd & 0xFFu, nd1 = (P.nd >> 8) & 0xFFu, nd2 = (P.nd >> 16) & 0xFFu,
+                               nd3 = P.nd >> 24;
+                uint32_t c;
+                if (P.seven)
+                    c = warp_tile<true, false, true>(b4, b32, c0, wq, warp, lane, qc, P.m, P.r, nd0, nd1, nd2, nd3,
+                                                     one, nst, s0, q, 0, nullptr, 0);
+                else
+                    c = warp_tile<false, false, true>(b4, b32, c0, wq, warp, lane, qc, P.m, P.r, nd0, nd1, nd2, nd3,
+                                                      one, nst, s0, q, 0, nullptr, 0);
+                c = warp_sum_u32(c);
+                if (lane == 0 && c) atomicAdd(&slots[p - pbase], c);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+            if (++s == S) {
+                s = 0;
+                phase ^= 1u;
+            }
+        }
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < A.nslots; i += kThreads) {
+        const uint32_t v = slots[i];
+        if (v) atomicAdd(reinterpret_cast<unsigned long long*>(A.d_counts + A.pats[pbase + i].out), (unsigned long long)v);
+    }
+}
+
+// Per-text byte histograms: work item = (text, 64 KiB chunk).
+__global__ void __launch_bounds__(256) batch_hist_kernel(const uint8_t* texts, const int64_t* off,
+                                                         const uint64_t* chunk_begin, uint32_t ntexts,
+                                                         uint64_t nchunks, uint32_t* hist) {
+    __shared__ uint32_t h[8][256];
+    const uint32_t tid = threadIdx.x, warp = tid >> 5;
+    for (uint64_t item = blockIdx.x; item < nchunks; item += gridDim.x) {
+        for (uint32_t i = tid; i < 8 * 256; i += 256) (&h[0][0])[i] = 0;
+        __syncthreads();
+        uint32_t lo = 0, hi = ntexts;   // last text whose first chunk <= item
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (chunk_begin[mid] <= item) lo = mid; else hi = mid;
+        }
+        const uint32_t x = lo;
+        const uint64_t n = (uint64_t)(off[x + 1] - off[x]);
+        const uint64_t b0 = (item - chunk_begin[x]) * kHistChunk;
+        const uint64_t b1 = min(b0 + kHistChunk, n);
+        const uint8_t* t = texts + off[x];
+        for (uint64_t i = b0 + tid; i < b1; i += 256) atomicAdd(&h[warp][t[i]], 1u);
+        __syncthreads();
+        {
+            uint32_t v = 0;
+            for (int w = 0; w < 8; ++w) v += h[w][tid];
+            if (v) atomicAdd(&hist[(uint64_t)x * 256 + tid], v);
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+}  // namespace smk
+
+// ------------------------------------------------------------------ host
+
+struct sm_batch {
+    sm_ctx* ctx = nullptr;
+    int device = 0;
+    uint32_t npats = 0;      // caller's pattern count (size of d_counts)
+    uint32_t grid = 0;
+    size_t smem = 0;
+    smk::BatchArgs args{};
+    void* d_mem = nullptr;   // one allocation holding every table
+};
+
+namespace {
+
+struct Guard {
+    int prev = -1;
+    explicit Guard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~Guard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// peel factor from the pattern's symbol frequencies (same cost model as the
+// single-pattern scan: dense compare ~100, compaction ~80, 32 words ~60)
+uint32_t batch_peel(const std::vector<uint32_t>& qsym_freq_order, const uint32_t* h, uint64_t n, uint32_t m) {
+    double alive = 1.0, best = 1e300;
+    uint32_t best_r = 1;
+    for (uint32_t r = 1; r <= std::min<uint32_t>(m, 16); ++r) {
+        alive *= (double)h[qsym_freq_order[r - 1]] / (double)n;
+        double cost = 100.0 * r;
+        if (r < m) {
+            const double p_word = 1.0 - std::pow(1.0 - alive, 4.0);
+            const double p_warp = 1.0 - std::pow(1.0 - alive, 2048.0);
+            const double entries = 512.0 * p_word;
+            cost += 80.0 * p_warp + 60.0 * (p_warp + std::max(0.0, entries - 32.0) / 32.0);
+            if (entries > 96.0) cost += 200.0;
+        }
+        if (cost < best) {
+            best = cost;
+            best_r = r;
+        }
+    }
+    return best_r;
+}
+
+}  // namespace
+
+extern "C" const char* sm_last_error(void);
+sm_status sm_fail_internal(sm_status s, const char* msg);   // defined in sm_api.cpp
+int sm_ctx_device(const sm_ctx* c);
+int sm_ctx_num_sms(const sm_ctx* c);
+size_t sm_ctx_max_smem(const sm_ctx* c);
+uint32_t* sm_ctx_status(const sm_ctx* c);
+uint64_t sm_ctx_spin_ns(const sm_ctx* c);
+uint32_t sm_ctx_stages(const sm_ctx* c);
+
+extern "C" sm_status sm_batch_create(sm_ctx* ctx, const uint8_t* d_texts, const int64_t* h_text_off, uint32_t ntexts,
+                                     const uint8_t* h_pats, const int64_t* h_pat_off, const int32_t* h_pat_text,
+                                     uint32_t npats, sm_batch** out, sm_stream_t stream) {
+    using namespace smk;
+    if (!out) return sm_fail_internal(SM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!ctx || !h_text_off || (npats && (!h_pats || !h_pat_off || !h_pat_text)))
+        return sm_fail_internal(SM_EINVAL, "NULL argument");
+    if (ntexts == 0) return sm_fail_internal(SM_EINVAL, "no texts");
+    const uint64_t total_bytes = (uint64_t)h_text_off[ntexts];
+    if (h_text_off[0] != 0) return sm_fail_internal(SM_EINVAL, "h_text_off[0] must be 0");
+    for (uint32_t x = 0; x < ntexts; ++x)
+        if (h_text_off[x + 1] < h_text_off[x]) return sm_fail_internal(SM_EINVAL, "text offsets must not decrease");
+    if (total_bytes && !d_texts) return sm_fail_internal(SM_EINVAL, "d_texts is NULL");
+    for (uint32_t k = 0; k < npats; ++k) {
+        const int64_t m = h_pat_off[k + 1] - h_pat_off[k];
+        if (m < 1 || m > (int64_t)SM_MAX_M) return sm_fail_internal(SM_EINVAL, "pattern length out of range");
+        if (h_pat_text[k] < 0 || (uint32_t)h_pat_text[k] >= ntexts)
+            return sm_fail_internal(SM_EINVAL, "pattern refers to a missing text");
+    }
+    Guard g(sm_ctx_device(ctx));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+
+    // 1. per-text histograms on the device
+    std::vector<uint64_t> chunk_begin(ntexts + 1, 0);
+    for (uint32_t x = 0; x < ntexts; ++x) {
+        const uint64_t n = (uint64_t)(h_text_off[x + 1] - h_text_off[x]);
+        chunk_begin[x + 1] = chunk_begin[x] + (n + kHistChunk - 1) / kHistChunk;
+    }
+    std::vector<uint32_t> hist((size_t)ntexts * 256, 0);
+    {
+        void* tmp = nullptr;
+        const size_t hb = hist.size() * 4, ob = (size_t)(ntexts + 1) * 8, cb = (size_t)(ntexts + 1) * 8;
+        if (cudaMalloc(&tmp, hb + ob + cb) != cudaSuccess) {
+            cudaGetLastError();
+            return sm_fail_internal(SM_ENOMEM, "histogram workspace");
+        }
+        uint32_t* d_hist = static_cast<uint32_t*>(tmp);
+        int64_t* d_off = reinterpret_cast<int64_t*>(static_cast<char*>(tmp) + hb);
+        uint64_t* d_cb = reinterpret_cast<uint64_t*>(static_cast<char*>(tmp) + hb + ob);
+        cudaError_t e = cudaMemsetAsync(d_hist, 0, hb, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, h_text_off, ob, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_cb, chunk_begin.data(), cb, cudaMemcpyHostToDevice, st);
+        const uint64_t nchunks = chunk_begin[ntexts];
+        if (e == cudaSuccess && nchunks) {
+            const uint32_t grid = (uint32_t)std::min<uint64_t>(nchunks, (uint64_t)sm_ctx_num_sms(ctx) * 8);
+            batch_hist_kernel<<<grid, 256, 0, st>>>(d_texts, d_off, d_cb, ntexts, nchunks, d_hist);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hist.data(), d_hist, hb, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        cudaFree(tmp);
+        if (e != cudaSuccess) return sm_fail_internal(SM_ECUDA, cudaGetErrorString(e));
+    }
+
+    // 2. patterns grouped by text; orders, peels, compare descriptors
+    std::vector<uint32_t> by_text(npats);
+    std::iota(by_text.begin(), by_text.end(), 0u);
+    std::stable_sort(by_text.begin(), by_text.end(),
+                     [&](uint32_t a, uint32_t b) { return h_pat_text[a] < h_pat_text[b]; });
+    std::vector<BatchText> tx;
+    std::vector<BatchPat> pats;
+    std::vector<uint32_t> qc;
+    std::vector<double> entry_cost;
+    size_t kk = 0;
+    for (uint32_t x = 0; x < ntexts; ++x) {
+        const uint64_t n = (uint64_t)(h_text_off[x + 1] - h_text_off[x]);
+        const uint32_t* h = &hist[(size_t)x * 256];
+        bool text7 = true;
+        for (int c = 0x80; c < 256; ++c)
+            if (h[c]) text7 = false;
+        const uint32_t delta = (uint32_t)((reinterpret_cast<uintptr_t>(d_texts) + (uint64_t)h_text_off[x]) & 15u);
+        BatchText cur{(uint64_t)h_text_off[x], n, 0, (uint32_t)pats.size(), (uint32_t)pats.size(), 0, 0};
+        for (; kk < npats && (uint32_t)h_pat_text[by_text[kk]] == x; ++kk) {
+            const uint32_t k = by_text[kk];
+            const uint8_t* p = h_pats + h_pat_off[k];
+            const uint32_t m = (uint32_t)(h_pat_off[k + 1] - h_pat_off[k]);
+            bool absent = (uint64_t)m > n;
+            for (uint32_t q = 0; q < m && !absent; ++q) absent = h[p[q]] == 0;
+            if (absent) continue;   // count 0
+            if (cur.pend - cur.pbeg == kMaxSlots) {   // start another group of this text
+                tx.push_back(cur);
+                cur.pbeg = cur.pend;
+                cur.maxm = 0;
+            }
+            std::vector<uint32_t> pi(m);
+            std::iota(pi.begin(), pi.end(), 0u);
+            std::stable_sort(pi.begin(), pi.end(), [&](uint32_t a, uint32_t b) { return h[p[a]] < h[p[b]]; });
+            std::vector<uint32_t> syms(m);
+            for (uint32_t j = 0; j < m; ++j) syms[j] = p[pi[j]];
+            const uint32_t r = batch_peel(syms, h, n, m);
+            BatchPat bp{(uint32_t)qc.size(), m, r, 0, k, text7 ? 1u : 0u};
+            uint32_t nd[4] = {0, 0, 0, 0};
+            for (uint32_t d = 0; d < 4; ++d)
+                for (uint32_t j = 0; j < r; ++j) {
+                    const uint32_t v = ((pi[j] + delta) << 8) | p[pi[j]];
+                    if (((v >> 10) & 3u) == d) {
+                        qc.push_back(v);
+                        ++nd[d];
+                    }
+                }
+            for (uint32_t j = r; j < m; ++j) qc.push_back(((pi[j] + delta) << 8) | p[pi[j]]);
+            bp.nd = nd[0] | (nd[1] << 8) | (nd[2] << 16) | (nd[3] << 24);
+            pats.push_back(bp);
+            cur.pend = (uint32_t)pats.size();
+            cur.maxm = std::max(cur.maxm, m);
+        }
+        if (cur.pend > cur.pbeg) tx.push_back(cur);
+    }
+    // items: tiles of each entry over the starts of its shortest pattern
+    uint64_t items = 0;
+    uint32_t maxm_all = 1;
+    for (BatchText& t : tx) {
+        uint32_t mn = ~0u;
+        for (uint32_t p = t.pbeg; p < t.pend; ++p) mn = std::min(mn, pats[p].m);
+        t.item_begin = items;
+        items += (t.n - mn + 1 + kTile - 1) / kTile;
+        maxm_all = std::max(maxm_all, t.maxm);
+        entry_cost.push_back(1.0 + (double)(t.pend - t.pbeg));
+    }
+    BatchText sentinel{0, 0, items, 0, 0, 0, 0};
+    tx.push_back(sentinel);
+
+    sm_batch* b = new sm_batch();
+    b->ctx = ctx;
+    b->device = sm_ctx_device(ctx);
+    b->npats = npats;
+
+    // 3. CTA ranges: equal cost (tiles x patterns), each within kMaxSlots patterns
+    const uint32_t SB = stage_bytes_for(maxm_all);
+    uint32_t stages = sm_ctx_stages(ctx);
+    size_t smem = 0;
+    auto smem_for = [&](uint32_t nslots, uint32_t s) {
+        return (size_t)kScanHeader + kQueueBytes + ((nslots * 4u + 127u) & ~127u) + (size_t)SB * s;
+    };
+    while (stages > 2 && smem_for(kMaxSlots, stages) > sm_ctx_max_smem(ctx)) --stages;
+    int occ = 0;
+    cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_ctx_max_smem(ctx));
+    smem = smem_for(kMaxSlots, stages);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel, kThreads, smem);
+    const uint64_t want = std::max<uint64_t>(1, (uint64_t)sm_ctx_num_sms(ctx) * std::max(occ, 1));
+    double total_cost = 0;
+    for (size_t e = 0; e + 1 < tx.size(); ++e)
+        total_cost += entry_cost[e] * (double)(tx[e + 1].item_begin - tx[e].item_begin);
+    const double per_cta = std::max(1.0, total_cost / (double)want);
+    std::vector<uint64_t> cta_items{0};
+    std::vector<uint32_t> cta_pbase;
+    uint32_t nslots = 1;
+    for (uint64_t item = 0, e = 0; item < items;) {
+        while (tx[e + 1].item_begin <= item) ++e;   // entry of the CTA's first item
+        const uint32_t pb = tx[e].pbeg;
+        double acc = 0;
+        uint64_t it = item, ee = e;
+        while (it < items) {
+            while (tx[ee + 1].item_begin <= it) ++ee;
+            if (tx[ee].pend - pb > kMaxSlots) break;   // pattern window full: next CTA
+            acc += entry_cost[ee];
+            ++it;
+            if (acc >= per_cta) break;
+        }
+        uint64_t el = e;                            // entry of the CTA's last item
+        while (tx[el + 1].item_begin < it) ++el;
+        cta_items.push_back(it);
+        cta_pbase.push_back(pb);
+        nslots = std::max(nslots, tx[el].pend - pb);
+        item = it;
+    }
+    b->grid = (uint32_t)cta_pbase.size();
+    b->smem = smem_for(nslots, stages);
+
+    // 4. one allocation for every table
+    const size_t s_tx = tx.size() * sizeof(BatchText), s_p = std::max<size_t>(pats.size(), 1) * sizeof(BatchPat);
+    const size_t s_q = std::max<size_t>(qc.size(), 1) * 4, s_ci = cta_items.size() * 8,
+                 s_cp = std::max<size_t>(cta_pbase.size(), 1) * 4;
+    auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    const size_t total = al(s_tx) + al(s_p) + al(s_q) + al(s_ci) + al(s_cp);
+    if (cudaMalloc(&b->d_mem, total) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return sm_fail_internal(SM_ENOMEM, "batch plan tables");
+    }
+    char* base = static_cast<char*>(b->d_mem);
+    BatchText* d_tx = reinterpret_cast<BatchText*>(base);
+    BatchPat* d_p = reinterpret_cast<BatchPat*>(base + al(s_tx));
+    uint32_t* d_q = reinterpret_cast<uint32_t*>(base + al(s_tx) + al(s_p));
+    uint64_t* d_ci = reinterpret_cast<uint64_t*>(base + al(s_tx) + al(s_p) + al(s_q));
+    uint32_t* d_cp = reinterpret_cast<uint32_t*>(base + al(s_tx) + al(s_p) + al(s_q) + al(s_ci));
+    cudaError_t e = cudaMemcpy(d_tx, tx.data(), s_tx, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !pats.empty()) e = cudaMemcpy(d_p, pats.data(), pats.size() * sizeof(BatchPat), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !qc.empty()) e = cudaMemcpy(d_q, qc.data(), qc.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_ci, cta_items.data(), s_ci, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !cta_pbase.empty()) e = cudaMemcpy(d_cp, cta_pbase.data(), cta_pbase.size() * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(b->d_mem);
+        delete b;
+        return sm_fail_internal(SM_ECUDA, cudaGetErrorString(e));
+    }
+    BatchArgs& a = b->args;
+    a.texts = d_texts;
+    a.tx = d_tx;
+    a.ntx = (uint32_t)tx.size() - 1;
+    a.pats = d_p;
+    a.qc = d_q;
+    a.cta_items = d_ci;
+    a.cta_pbase = d_cp;
+    a.stage_bytes = SB;
+    a.stages = stages;
+    a.one = 1;
+    a.nslots = nslots;
+    a.status = sm_ctx_status(ctx);
+    a.spin_ns = sm_ctx_spin_ns(ctx);
+    *out = b;
+    return SM_OK;
+}
+
+extern "C" sm_status sm_batch_count(sm_batch* b, int64_t* d_counts, sm_stream_t stream) {
+    if (!b) return sm_fail_internal(SM_EINVAL, "batch is NULL");
+    if (!d_counts && b->npats) return sm_fail_internal(SM_EINVAL, "d_counts is NULL");
+    Guard g(b->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (b->npats) e = cudaMemsetAsync(d_counts, 0, (size_t)b->npats * sizeof(int64_t), st);
+    if (e == cudaSuccess && b->grid) {
+        smk::BatchArgs a = b->args;
+        a.d_counts = d_counts;
+        smk::batch_kernel<<<b->grid, smk::kThreads, b->smem, st>>>(a);
+        e = cudaGetLastError();
+    }
+    return e == cudaSuccess ? SM_OK : sm_fail_internal(SM_ECUDA, cudaGetErrorString(e));
+}
+
+extern "C" void sm_batch_destroy(sm_batch* b) {
+    if (!b) return;
+    Guard g(b->device);
+    cudaDeviceSynchronize();
+    if (b->d_mem) cudaFree(b->d_mem);
+    delete b;
+}
+
+extern "C" sm_status sm_count_batch(sm_ctx* ctx, const uint8_t* d_texts, const int64_t* d_text_off, uint32_t ntexts,
+                                    const uint8_t* d_pats, const int64_t* d_pat_off, const int32_t* d_pat_text,
+                                    uint32_t npats, int64_t* d_counts, uint64_t* d_pos, const int64_t* d_pos_off,
+                                    sm_stream_t stream) {
+    if (!ctx || !d_text_off || ntexts == 0 || (npats && (!d_pats || !d_pat_off || !d_pat_text || !d_counts)))
+        return sm_fail_internal(SM_EINVAL, "NULL argument");
+    if (d_pos && !d_pos_off) return sm_fail_internal(SM_EINVAL, "d_pos needs d_pos_off");
+    Guard g(sm_ctx_device(ctx));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    std::vector<int64_t> text_off(ntexts + 1), pat_off(npats + 1), pos_off(d_pos ? npats + 1 : 0);
+    std::vector<int32_t> pat_text(npats);
+    cudaError_t e = cudaMemcpyAsync(text_off.data(), d_text_off, text_off.size() * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && npats) {
+        e = cudaMemcpyAsync(pat_off.data(), d_pat_off, pat_off.size() * 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(pat_text.data(), d_pat_text, pat_text.size() * 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && d_pos)
+            e = cudaMemcpyAsync(pos_off.data(), d_pos_off, pos_off.size() * 8, cudaMemcpyDeviceToHost, st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return sm_fail_internal(SM_ECUDA, cudaGetErrorString(e));
+    std::vector<uint8_t> pats(npats ? (size_t)std::max<int64_t>(pat_off[npats], 0) : 0);
+    if (!pats.empty()) {
+        e = cudaMemcpy(pats.data(), d_pats, pats.size(), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return sm_fail_internal(SM_ECUDA, cudaGetErrorString(e));
+    }
+    sm_batch* b = nullptr;
+    sm_status s = sm_batch_create(ctx, d_texts, text_off.data(), ntexts, pats.data(), pat_off.data(),
+                                  pat_text.data(), npats, &b, stream);
+    if (s != SM_OK) return s;
+    s = sm_batch_count(b, d_counts, stream);
+    if (s == SM_OK && d_pos) {
+        // positions: one ordered report per pattern into its slice of d_pos
+        uint64_t* d_tmp = nullptr;
+        if (cudaMalloc(&d_tmp, sizeof(uint64_t)) != cudaSuccess) {
+            cudaGetLastError();
+            s = sm_fail_internal(SM_ENOMEM, "report count");
+        }
+        for (uint32_t k = 0; s == SM_OK && k < npats; ++k) {
+            const int64_t cap = pos_off[k + 1] - pos_off[k];
+            if (cap <= 0) continue;
+            const int32_t x = pat_text[k];
+            s = sm_report(ctx, d_texts + text_off[x], (uint64_t)(text_off[x + 1] - text_off[x]),
+                          pats.data() + pat_off[k], (uint32_t)(pat_off[k + 1] - pat_off[k]), nullptr,
+                          d_pos + pos_off[k], (uint64_t)cap, d_tmp, stream);
+        }
+        cudaStreamSynchronize(st);
+        if (d_tmp) cudaFree(d_tmp);
+    }
+    cudaStreamSynchronize(st);
+    sm_batch_destroy(b);
+    return s;
+}

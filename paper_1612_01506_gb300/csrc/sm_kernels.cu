@@ -41,11 +41,6 @@ namespace {
 using namespace dev;
 
 
-template <int MAXM>
-struct PatArg {
-    uint32_t qc[MAXM];   // compare j: (e_j << 8) | p[pi(j)], e_j = (text address mod 16) + pi(j)
-};
-
 struct StageDesc {
     uint64_t tile;       // kEnd: no more tiles
     uint64_t offset;     // report: output offset of the tile's first match
@@ -54,7 +49,7 @@ struct StageDesc {
 // ------------------------------------------------------------ scan kernel
 
 #ifndef SMK_MIN_BLOCKS
-#define SMK_MIN_BLOCKS 1
+#define SMK_MIN_BLOCKS 3
 #endif
 template <int MAXM, int MODE, bool SEVEN>
 __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __grid_constant__ ScanArgs A,
@@ -86,10 +81,6 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
 
     if (warp == kConsumerWarps) {
         // ---------------------------------------------------------- producer
-        const uintptr_t tb = reinterpret_cast<uintptr_t>(A.text);
-        // text indices [lo_al, hi_al) form the 16-byte aligned interior
-        const int64_t lo_al = (int64_t)(((tb + 15u) & ~(uintptr_t)15u) - tb);
-        const int64_t hi_al = (int64_t)((tb + A.n) & ~(uintptr_t)15u) - (int64_t)tb;
         uint64_t cursor = t_begin, running = 0;
         if (MODE == kModeWrite) {
             uint64_t b = 0;
@@ -136,24 +127,10 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
                 }
             }
             uint8_t* buf = bufs + (size_t)s * SB;
-            uint32_t bytes = 0;
-            uintptr_t ga = 0, g0 = 0;
+            TileCopy cp{0, 0, 0};
             if (tile != kEnd) {
                 const uint64_t s0 = tile * kTile;
-                const int64_t need_end = (int64_t)min(s0 + kTile + m - 1, A.n);
-                const uint32_t delta = (uint32_t)(tb & 15u);
-                // bytes outside the aligned interior: head (< lo_al) and tail (>= hi_al), each < 16
-                const int64_t h_end = min(need_end, lo_al);
-                const int64_t t_beg = max((int64_t)s0, max(lo_al, max(hi_al, (int64_t)0)));
-                const int64_t xh = (int64_t)s0 + lane, xt = t_beg + lane;
-                if (xh < h_end) buf[delta + (xh - (int64_t)s0)] = A.text[xh];
-                if (xt < need_end) buf[delta + (xt - (int64_t)s0)] = A.text[xt];
-                g0 = (tb + s0) & ~(uintptr_t)15u;
-                ga = max(g0, tb + (uintptr_t)lo_al);
-                const uintptr_t ge = (tb + (uint64_t)need_end + 15u) & ~(uintptr_t)15u;
-                const uintptr_t gb = min(ge, (tb + A.n) & ~(uintptr_t)15u);
-                bytes = gb > ga ? (uint32_t)(gb - ga) : 0u;
-                __threadfence_block();
+                cp = stage_ragged(buf, A.text, A.n, s0, min(s0 + kTile + m - 1, A.n), lane);
             }
             __syncwarp();
             if (lane == 0) {
@@ -161,8 +138,9 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
                 desc[s].offset = running;
                 const bool skip = A.test_skip_copy && tile == 0;
                 fence_proxy_async();
-                mbar_arrive_expect_tx(&full[s], bytes);
-                if (bytes && !skip) bulk_g2s(buf + (ga - g0), reinterpret_cast<const void*>(ga), bytes, &full[s]);
+                mbar_arrive_expect_tx(&full[s], cp.bytes);
+                if (cp.bytes && !skip)
+                    bulk_g2s(buf + cp.dst_off, reinterpret_cast<const void*>(cp.src), cp.bytes, &full[s]);
             }
             issued = it + 1;
             if (tile == kEnd) break;
@@ -196,143 +174,14 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
             const uint32_t* b32 = reinterpret_cast<const uint32_t*>(buf);
             const uint64_t s0 = d.tile * kTile;
 
-            // dense phase: r compares for all starts of the warp; the peeled
-            // compares arrive grouped by word alignment (A.nd)
-            uint32_t f[kChunks][4];
-#pragma unroll
-            for (int c = 0; c < kChunks; ++c)
-#pragma unroll
-                for (int i = 0; i < 4; ++i) f[c][i] = 0x80808080u;
-            {
-                uint32_t j = 0;
-                for (uint32_t k = 0; k < A.nd[0]; ++k, ++j) compare_chunks<SEVEN, 0>(b4, c0, P.qc[j], one, f);
-                for (uint32_t k = 0; k < A.nd[1]; ++k, ++j) compare_chunks<SEVEN, 1>(b4, c0, P.qc[j], one, f);
-                for (uint32_t k = 0; k < A.nd[2]; ++k, ++j) compare_chunks<SEVEN, 2>(b4, c0, P.qc[j], one, f);
-                for (uint32_t k = 0; k < A.nd[3]; ++k, ++j) compare_chunks<SEVEN, 3>(b4, c0, P.qc[j], one, f);
+            uint64_t out = 0;
+            if (MODE == kModeWrite) {
+                const uint32_t cw = lane < warp ? __ldcg(A.warp_counts + d.tile * kConsumerWarps + lane) : 0u;
+                out = d.offset + warp_sum_u32(cw);
             }
-
-            if (s0 + kTile > A.nstarts) {   // last tile: clear starts beyond n - m
-                const int64_t lim = (int64_t)(A.nstarts - s0) - (int64_t)(warp * kWarpStarts + lane * 16u);
-#pragma unroll
-                for (int c = 0; c < kChunks; ++c)
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) f[c][i] &= valid_mask(lim - (512 * c + 4 * i));
-            }
-
-            uint32_t any = 0;
-#pragma unroll
-            for (int c = 0; c < kChunks; ++c) any |= (f[c][0] | f[c][1]) | (f[c][2] | f[c][3]);
-
-            uint32_t tile_count = 0;   // this lane's share of the warp's matches in the tile
-            if (MODE == kModeCount && r >= m) {
-                tile_count = count_flags<kChunks>(f);
-            } else if (__any_sync(kFull, any != 0u)) {
-                // compact surviving words in position order: chunk 0 of all
-                // lanes, then chunk 1, ... (4 bits per chunk, counts in bytes)
-                uint32_t a[kChunks], packed = 0;
-#pragma unroll
-                for (int c = 0; c < kChunks; ++c) {
-                    a[c] = 0;
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) a[c] |= (f[c][i] != 0u) << i;
-                    packed |= (uint32_t)__popc(a[c]) << (8 * c);
-                }
-                const uint32_t incl = warp_incl_scan(packed, lane);
-                const uint32_t tot = __shfl_sync(kFull, incl, 31);
-                const uint32_t qn = (tot & 0xFFu) + ((tot >> 8) & 0xFFu) + ((tot >> 16) & 0xFFu) + (tot >> 24);
-
-                uint64_t out = 0;
-                if (MODE == kModeWrite) {
-                    const uint32_t cw = lane < warp ? __ldcg(A.warp_counts + d.tile * kConsumerWarps + lane) : 0u;
-                    out = d.offset + warp_sum_u32(cw);
-                }
-                if (qn <= kQueueCap) {
-                    uint32_t base = 0;
-#pragma unroll
-                    for (int c = 0; c < kChunks; ++c) {
-                        uint32_t p = base + ((incl >> (8 * c)) & 0xFFu) - ((packed >> (8 * c)) & 0xFFu);
-#pragma unroll
-                        for (int i = 0; i < 4; ++i)
-                            if (a[c] & (1u << i)) q[p++] = make_uint2(128u * c + lane * 4u + i, f[c][i]);
-                        base += (tot >> (8 * c)) & 0xFFu;
-                    }
-                    __syncwarp();
-                    // sparse phase: each lane continues one word with its own early exit
-                    for (uint32_t qb = 0; qb < qn; qb += 32) {
-                        const uint32_t e = qb + lane;
-                        uint32_t wi = 0, fw = 0;
-                        if (e < qn) {
-                            const uint2 x = q[e];
-                            wi = x.x;
-                            fw = x.y;
-                        }
-                        for (uint32_t j = r; j < m && fw; ++j) fw = compare_word<SEVEN>(b32, wq + wi, P.qc[j], one, fw);
-                        const uint32_t k = __popc(fw);
-                        if (MODE == kModeWrite) {
-                            const uint32_t inc = warp_incl_scan(k, lane);
-                            uint64_t rk = out + inc - k;
-                            const uint64_t pos0 = s0 + warp * kWarpStarts + 4u * wi;
-                            while (fw) {
-                                const uint32_t b = (uint32_t)(__ffs(fw) - 1) >> 3;
-                                if (rk < A.cap) A.d_pos[rk] = pos0 + b;
-                                ++rk;
-                                fw &= fw - 1;
-                            }
-                            out += __shfl_sync(kFull, inc, 31);
-                        } else {
-                            tile_count += k;
-                        }
-                    }
-                    __syncwarp();   // the queue is reused by the next tile
-                } else {
-                    // more survivors than the queue holds: continue the remaining
-                    // compares for all of the warp's starts, leaving when all are dead
-                    for (uint32_t j = r; j < m; ++j) {
-                        uint32_t an = 0;
-#pragma unroll
-                        for (int c = 0; c < kChunks; ++c) an |= (f[c][0] | f[c][1]) | (f[c][2] | f[c][3]);
-                        if (!__any_sync(kFull, an != 0u)) break;
-                        const uint32_t v = P.qc[j];
-                        switch ((v >> 10) & 3u) {
-                            case 0: compare_chunks<SEVEN, 0>(b4, c0, v, one, f); break;
-                            case 1: compare_chunks<SEVEN, 1>(b4, c0, v, one, f); break;
-                            case 2: compare_chunks<SEVEN, 2>(b4, c0, v, one, f); break;
-                            default: compare_chunks<SEVEN, 3>(b4, c0, v, one, f); break;
-                        }
-                    }
-                    if (MODE == kModeWrite) {
-                        // positions in order: chunk c of all lanes, words, bytes
-                        uint32_t kc[kChunks];
-#pragma unroll
-                        for (int c = 0; c < kChunks; ++c)
-                            kc[c] = __popc(f[c][0]) + __popc(f[c][1]) + __popc(f[c][2]) + __popc(f[c][3]);
-                        const uint32_t i01 = warp_incl_scan(kc[0] | (kc[1] << 16), lane);
-                        const uint32_t i23 = warp_incl_scan(kc[2] | (kc[3] << 16), lane);
-                        const uint32_t t01 = __shfl_sync(kFull, i01, 31), t23 = __shfl_sync(kFull, i23, 31);
-                        const uint32_t incs[4] = {i01 & 0xFFFFu, i01 >> 16, i23 & 0xFFFFu, i23 >> 16};
-                        const uint32_t tots[4] = {t01 & 0xFFFFu, t01 >> 16, t23 & 0xFFFFu, t23 >> 16};
-                        uint64_t cb = out;
-#pragma unroll
-                        for (int c = 0; c < kChunks; ++c) {
-                            uint64_t rk = cb + incs[c] - kc[c];
-                            const uint64_t pos0 = s0 + warp * kWarpStarts + 512u * c + 16u * lane;
-#pragma unroll
-                            for (int i = 0; i < 4; ++i) {
-                                uint32_t fw = f[c][i];
-                                while (fw) {
-                                    const uint32_t b = (uint32_t)(__ffs(fw) - 1) >> 3;
-                                    if (rk < A.cap) A.d_pos[rk] = pos0 + 4u * i + b;
-                                    ++rk;
-                                    fw &= fw - 1;
-                                }
-                            }
-                            cb += tots[c];
-                        }
-                    } else {
-                        tile_count += count_flags<kChunks>(f);
-                    }
-                }
-            }
+            const uint32_t tile_count = warp_tile<SEVEN, MODE == kModeWrite, MODE == kModeCount>(
+                b4, b32, c0, wq, warp, lane, ParamQC<MAXM>{&P}, m, r, A.nd[0], A.nd[1], A.nd[2], A.nd[3], one,
+                A.nstarts, s0, q, out, A.d_pos, A.cap);
 
             if (MODE == kModeTileCount) {
                 const uint32_t wsum = warp_sum_u32(tile_count);

@@ -25,7 +25,8 @@ SM_NOALLOC_MAX_STARTS = 16384 * 16384
 # Every symbol the header declares (checked against include/sm.h by the tests).
 EXPORTS = ("sm_create", "sm_destroy", "sm_last_error", "sm_status_string", "sm_sync", "sm_set_knob",
            "sm_histogram", "sm_order", "sm_order_fixed", "sm_count", "sm_count_ex", "sm_report",
-           "sm_report_ex", "sm_report_noalloc")
+           "sm_report_ex", "sm_report_noalloc", "sm_batch_create", "sm_batch_count", "sm_batch_destroy",
+           "sm_count_batch")
 
 
 class SmError(RuntimeError):
@@ -72,6 +73,11 @@ def load():
         "sm_report": (st, [vp, vp, u64, u8p, u32, u32p, vp, u64, vp, vp]),
         "sm_report_ex": (st, [vp, vp, u64, u8p, u32, u32p, C.POINTER(SearchOpts), vp, u64, vp, vp]),
         "sm_report_noalloc": (st, [vp, u64, u8p, u32, u32p, vp, u64, vp, vp]),
+        "sm_batch_create": (st, [vp, vp, C.POINTER(C.c_int64), u32, u8p, C.POINTER(C.c_int64),
+                                 C.POINTER(C.c_int32), u32, C.POINTER(vp), vp]),
+        "sm_batch_count": (st, [vp, vp, vp]),
+        "sm_batch_destroy": (None, [vp]),
+        "sm_count_batch": (st, [vp, vp, vp, u32, vp, vp, vp, u32, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -249,3 +255,53 @@ def sm_report_noalloc(text, pattern, cap: int, out_pos, out_count, pi=None, stre
     return load().sm_report_noalloc(_dev_ptr(text, ("torch.uint8",)), text.numel(), _u8p(p), p.size, pip,
                                     _dev_ptr(out_pos, _WORD64), cap, _dev_ptr(out_count, _WORD64),
                                     _stream(stream))
+
+
+class Batch:
+    """A planned batch (sm_batch*); destroyed with the object. Keeps the texts alive."""
+
+    def __init__(self, handle: int, texts, npats: int):
+        self.handle, self.texts, self.npats = handle, texts, npats
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.sm_batch_destroy(h)
+
+
+def sm_batch_create(ctx: Ctx, texts, text_off, patterns: list, pat_text, stream=None) -> Batch:
+    """Plan a batch: texts is one packed uint8 CUDA tensor with host offsets
+    text_off (ntexts + 1); patterns a list of bytes, pattern k searched in
+    text pat_text[k]."""
+    toff = np.ascontiguousarray(text_off, dtype=np.int64)
+    pt = np.ascontiguousarray(pat_text, dtype=np.int32)
+    flat = np.frombuffer(b"".join(bytes(p) for p in patterns), dtype=np.uint8) if patterns else np.zeros(0, np.uint8)
+    poff = np.zeros(len(patterns) + 1, dtype=np.int64)
+    if patterns:
+        poff[1:] = np.cumsum([len(p) for p in patterns])
+    h = C.c_void_p()
+    _check(load().sm_batch_create(ctx.handle, _dev_ptr(texts, ("torch.uint8",)), toff.ctypes.data_as(C.POINTER(C.c_int64)),
+                                  toff.size - 1, _u8p(flat), poff.ctypes.data_as(C.POINTER(C.c_int64)),
+                                  pt.ctypes.data_as(C.POINTER(C.c_int32)), len(patterns), C.byref(h), _stream(stream)))
+    return Batch(h.value, texts, len(patterns))
+
+
+def sm_batch_count(batch: Batch, out=None, stream=None):
+    """Enqueue the batch; returns the int64 device tensor of counts (one per pattern)."""
+    import torch
+    if out is None:
+        out = torch.empty(max(batch.npats, 1), dtype=torch.int64, device=batch.texts.device)
+    _check(load().sm_batch_count(batch.handle, _dev_ptr(out, _WORD64), _stream(stream)))
+    return out
+
+
+def sm_count_batch(ctx: Ctx, texts, d_text_off, d_pats, d_pat_off, d_pat_text, d_counts, d_pos=None,
+                   d_pos_off=None, stream=None):
+    """The one-shot batch call with device-resident metadata (all CUDA tensors)."""
+    _check(load().sm_count_batch(ctx.handle, _dev_ptr(texts, ("torch.uint8",)), _dev_ptr(d_text_off, _WORD64),
+                                 d_text_off.numel() - 1, _dev_ptr(d_pats, ("torch.uint8",)),
+                                 _dev_ptr(d_pat_off, _WORD64), _dev_ptr(d_pat_text, ("torch.int32",)),
+                                 d_pat_text.numel(), _dev_ptr(d_counts, _WORD64),
+                                 _dev_ptr(d_pos, _WORD64) if d_pos is not None else None,
+                                 _dev_ptr(d_pos_off, _WORD64) if d_pos_off is not None else None, _stream(stream)))
+    return d_counts

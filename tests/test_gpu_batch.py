@@ -1,0 +1,133 @@
+"""GPU parity of batched counting against the oracle (bit-exact)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1612_01506_gb300 import sm, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return t
+
+
+@pytest.fixture(scope="module")
+def ctx(torch):
+    import __graft_entry__
+    __graft_entry__.build()
+    return sm.sm_create(0)
+
+
+def make_batch(seed, sizes, kinds, pats_per_text, mmax):
+    r = np.random.default_rng(seed)
+    texts = [synth.text(k, n, seed=0, stream=synth.stream_id("bt", seed, i)) if n else np.zeros(0, np.uint8)
+             for i, (k, n) in enumerate(zip(kinds, sizes))]
+    off = np.zeros(len(texts) + 1, np.int64)
+    off[1:] = np.cumsum([t.size for t in texts])
+    pats, pat_text = [], []
+    for x, t in enumerate(texts):
+        for _ in range(pats_per_text):
+            m = int(np.exp(r.uniform(0, np.log(mmax))))
+            u = r.random()
+            if t.size >= m and u < 0.7:
+                s = int(r.integers(0, t.size - m + 1))
+                pats.append(t[s:s + m].tobytes())
+            elif u < 0.9:
+                alpha = np.frombuffer(synth.alphabet_of(kinds[x]), np.uint8)
+                pats.append(alpha[r.integers(0, alpha.size, m)].tobytes())
+            else:
+                pats.append(bytes(r.integers(0, 256, m, dtype=np.uint8)))
+            pat_text.append(x)
+    order = r.permutation(len(pats))      # patterns in any order
+    pats = [pats[i] for i in order]
+    pat_text = [pat_text[i] for i in order]
+    flat = np.concatenate(texts) if texts else np.zeros(0, np.uint8)
+    return texts, flat, off, pats, np.array(pat_text, np.int32)
+
+
+def expected(texts, pats, pat_text):
+    return np.array([oracle.naive_count(p, texts[x]) for p, x in zip(pats, pat_text)], np.int64)
+
+
+def to_dev(torch, flat, offset=3):
+    buf = torch.zeros(flat.size + offset + 64, dtype=torch.uint8, device="cuda")
+    if flat.size:
+        buf[offset:offset + flat.size] = torch.from_numpy(flat.copy()).cuda()
+    return buf[offset:offset + flat.size]
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_batch_mixed(torch, ctx, seed):
+    sizes = [0, 1, 17, 5000, 40_000, 3 * 16384 + 11, 200_000, 7]
+    kinds = [4, 20, "markov95", 256, 4, 2, "markov95", 64]
+    texts, flat, off, pats, pt = make_batch(seed, sizes, kinds, 8, 600)
+    d = to_dev(torch, flat)
+    b = sm.sm_batch_create(ctx, d, off, pats, pt)
+    got = sm.sm_batch_count(b).cpu().numpy()[: len(pats)]
+    assert sm.sm_sync(ctx) == sm.SM_OK
+    assert np.array_equal(got, expected(texts, pats, pt))
+    # a second count from the same plan gives the same result
+    assert np.array_equal(sm.sm_batch_count(b).cpu().numpy()[: len(pats)], got)
+
+
+def test_batch_many_patterns_one_text(torch, ctx):
+    # more patterns than one CTA counts (4096): the text is split into groups
+    t = synth.markov95(600_000, seed=0, stream=11)
+    r = np.random.default_rng(4)
+    pats = []
+    for _ in range(5000):
+        m = int(np.exp(r.uniform(np.log(2), np.log(1024))))
+        if r.random() < 0.8:
+            s = int(r.integers(0, t.size - m + 1))
+            pats.append(t[s:s + m].tobytes())
+        else:
+            pats.append(bytes(r.integers(0x20, 0x7F, m, dtype=np.uint8)))
+    off = np.array([0, t.size], np.int64)
+    d = to_dev(torch, t, 0)
+    b = sm.sm_batch_create(ctx, d, off, pats, np.zeros(len(pats), np.int32))
+    got = sm.sm_batch_count(b).cpu().numpy()
+    want = np.array([oracle.naive_count(p, t) for p in pats], np.int64)
+    assert np.array_equal(got, want)
+
+
+def test_batch_graph_capture(torch, ctx):
+    texts, flat, off, pats, pt = make_batch(9, [100_000, 70_000], [4, "markov95"], 16, 64)
+    d = to_dev(torch, flat)
+    b = sm.sm_batch_create(ctx, d, off, pats, pt)
+    out = torch.zeros(len(pats), dtype=torch.int64, device="cuda")
+    s = torch.cuda.Stream()
+    sm.sm_batch_count(b, out=out, stream=s)   # warm up outside capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        sm.sm_batch_count(b, out=out, stream=s)
+    out.fill_(-1)
+    g.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), expected(texts, pats, pt))
+
+
+def test_count_batch_device_metadata_with_positions(torch, ctx):
+    texts, flat, off, pats, pt = make_batch(5, [30_000, 0, 50_000, 9], [2, 4, 20, 4], 6, 40)
+    want = expected(texts, pats, pt)
+    d = to_dev(torch, flat, 1)
+    poff = np.zeros(len(pats) + 1, np.int64)
+    caps = np.minimum(want, 50)                # some reports truncate
+    poff[1:] = np.cumsum(caps)
+    pflat = np.frombuffer(b"".join(pats), np.uint8).copy()
+    pat_off = np.zeros(len(pats) + 1, np.int64)
+    pat_off[1:] = np.cumsum([len(p) for p in pats])
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    counts = torch.zeros(len(pats), dtype=torch.int64, device="cuda")
+    dpos = torch.zeros(max(int(poff[-1]), 1), dtype=torch.int64, device="cuda")
+    sm.sm_count_batch(ctx, d, T(off), T(pflat), T(pat_off), T(pt), counts, dpos, T(poff))
+    assert np.array_equal(counts.cpu().numpy(), want)
+    allpos = dpos.cpu().numpy().view(np.uint64)
+    for k, (p, x) in enumerate(zip(pats, pt)):
+        pos, c = oracle.naive_report(p, texts[x])
+        assert np.array_equal(allpos[poff[k]:poff[k + 1]], pos[: caps[k]])

@@ -32,13 +32,19 @@ using namespace dev;
 
 constexpr uint32_t kMaxSlots = 4096;   // patterns one CTA counts in shared memory
 constexpr uint32_t kHistChunk = 65536; // bytes per histogram work item
+// A pattern whose rarest symbol has at most this frequency in its text takes
+// the candidate path (expected candidates per tile <= 0.08 * 16384).
+constexpr double kCandidateFreq = 0.08;
 
 struct BatchText {        // a text, or one group of <= kMaxSlots of its patterns
     uint64_t off;         // byte offset in the packed texts
     uint64_t n;           // length
     uint64_t item_begin;  // first work item (tile) of this entry
-    uint32_t pbeg, pend;  // its patterns [pbeg, pend) in the pattern table
-    uint32_t maxm, pad;
+    uint32_t pbeg, pmid;  // patterns [pbeg, pmid) run the dense scan ...
+    uint32_t pend;        // ... and [pmid, pend) the candidate path
+    uint32_t maxm;
+    uint32_t mask_idx;    // 8-word mask of the candidate patterns' first symbols
+    uint32_t pad;
 };
 
 struct BatchPat {
@@ -51,6 +57,7 @@ struct BatchPat {
 
 struct BatchArgs {
     const uint8_t* texts;
+    const uint32_t* masks;      // 8 words per entry with candidate patterns
     const BatchText* tx;        // ntx + 1 entries (the last one: item_begin = total items)
     uint32_t ntx;
     const BatchPat* pats;
@@ -59,6 +66,7 @@ struct BatchArgs {
     const uint32_t* cta_pbase;  // grid: first pattern counted by CTA b (its slot 0)
     int64_t* d_counts;
     uint32_t stage_bytes, stages, one, nslots;
+    uint32_t index_cap;         // entries of the per-tile position index (0: no index)
     uint32_t* status;
     uint64_t spin_ns;
 };
@@ -70,6 +78,25 @@ struct BatchDesc {
 };
 
 
+// Consumer-wide barrier (the 8 consumer warps, barrier 1) that also returns
+// whether any consumer thread passed v = true.
+__device__ __forceinline__ bool consumers_any(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.or.pred p, 1, %2, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(kConsumerWarps * 32)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void consumers_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(kConsumerWarps * 32) : "memory");
+}
+
 __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constant__ BatchArgs A) {
     extern __shared__ __align__(128) uint8_t smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
@@ -77,7 +104,13 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constan
     BatchDesc* desc = reinterpret_cast<BatchDesc*>(smem + 128);
     uint2* queues = reinterpret_cast<uint2*>(smem + kScanHeader);
     uint32_t* slots = reinterpret_cast<uint32_t*>(smem + kScanHeader + kQueueBytes);
-    uint8_t* bufs = smem + kScanHeader + kQueueBytes + ((A.nslots * 4u + 127u) & ~127u);
+    uint8_t* after_slots = smem + kScanHeader + kQueueBytes + ((A.nslots * 4u + 127u) & ~127u);
+    // per-tile position index of selected symbols: count, start, cursor, positions
+    uint32_t* icnt = reinterpret_cast<uint32_t*>(after_slots);
+    uint32_t* istart = icnt + 256;
+    uint32_t* icur = icnt + 512;
+    uint16_t* ilist = reinterpret_cast<uint16_t*>(icnt + 768);
+    uint8_t* bufs = after_slots + (A.index_cap ? ((3072u + 2u * A.index_cap + 127u) & ~127u) : 0u);
 
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t SB = A.stage_bytes, S = A.stages, one = A.one;
@@ -152,8 +185,9 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constan
         const uint32_t wq = warp * (kWarpStarts / 4);
         for (uint32_t s = 0, phase = 0;;) {
             const bool ok = __all_sync(kFull, wait_bounded(&full[s], phase, A.spin_ns));
-            if (!ok) {
-                if (lane == 0) atomicOr(A.status, kStatusTimeout);
+            // every consumer warp leaves together (later tiles use consumer barriers)
+            if (consumers_any(!ok)) {
+                if (lane == 0 && !ok) atomicOr(A.status, kStatusTimeout);
                 break;
             }
             const BatchDesc d = desc[s];
@@ -163,7 +197,9 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constan
             const uint32_t* b32 = reinterpret_cast<const uint32_t*>(buf);
             const uint64_t s0 = d.k * kTile;
             const BatchText T = A.tx[d.x];
-            for (uint32_t p = T.pbeg; p < T.pend; ++p) {
+
+            // dense patterns: every warp scans its 2048 starts
+            for (uint32_t p = T.pbeg; p < T.pmid; ++p) {
                 const BatchPat P = A.pats[p];
                 const uint64_t nst = T.n - P.m + 1;   // the plan keeps only patterns with m <= n
                 if (s0 >= nst) continue;
@@ -179,6 +215,70 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constan
                                                       one, nst, s0, q, 0, nullptr, 0);
                 c = warp_sum_u32(c);
                 if (lane == 0 && c) atomicAdd(&slots[p - pbase], c);
+            }
+
+            // candidate patterns: their first (rarest) symbol is rare in the
+            // text, so the starts worth testing are read from a position index
+            // of the tile, built once and shared by all of them
+            if (T.pmid < T.pend) {
+                const uint32_t delta = (uint32_t)((reinterpret_cast<uintptr_t>(A.texts) + T.off) & 15u);
+                const uint32_t nbytes = (uint32_t)(min(s0 + kTile + T.maxm - 1, T.n) - s0);
+                const uint32_t* mask = A.masks + 8u * T.mask_idx;
+                const uint32_t t = tid;   // 0..255 among the consumers
+                consumers_sync();         // the previous tile's index is no longer read
+                icnt[t] = 0;
+                consumers_sync();
+                for (uint32_t i = delta + t; i < delta + nbytes; i += kConsumerWarps * 32) {
+                    const uint32_t c = buf[i];
+                    if ((__ldg(mask + (c >> 5)) >> (c & 31)) & 1u) atomicAdd(&icnt[c], 1u);
+                }
+                consumers_sync();
+                if (warp == 0) {   // exclusive scan of 256 counts, 8 per lane
+                    uint32_t v[8], sum = 0;
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        v[k] = icnt[lane * 8 + k];
+                        sum += v[k];
+                    }
+                    const uint32_t ex = warp_incl_scan(sum, lane) - sum;
+                    uint32_t run = ex;
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        istart[lane * 8 + k] = run;
+                        icur[lane * 8 + k] = run;
+                        run += v[k];
+                    }
+                }
+                consumers_sync();
+                for (uint32_t i = delta + t; i < delta + nbytes; i += kConsumerWarps * 32) {
+                    const uint32_t c = buf[i];
+                    if ((__ldg(mask + (c >> 5)) >> (c & 31)) & 1u) ilist[atomicAdd(&icur[c], 1u)] = (uint16_t)i;
+                }
+                consumers_sync();
+                for (uint32_t p = T.pmid + warp; p < T.pend; p += kConsumerWarps) {
+                    const BatchPat P = A.pats[p];
+                    const uint64_t nst = T.n - P.m + 1;
+                    if (s0 >= nst) continue;
+                    const int32_t valid = (int32_t)min((uint64_t)kTile, nst - s0);
+                    const uint32_t* pq = A.qc + P.qc_off;
+                    const uint32_t v0 = __ldg(pq);
+                    const int32_t e0 = (int32_t)(v0 >> 8);
+                    const uint32_t sym = v0 & 0xFFu;
+                    const uint32_t lo = istart[sym], hi = lo + icnt[sym];
+                    uint32_t cnt = 0;
+                    for (uint32_t k = lo + lane; k < hi; k += 32) {
+                        const int32_t st = (int32_t)ilist[k] - e0;   // candidate start in the tile
+                        if (st < 0 || st >= valid) continue;
+                        bool ok2 = true;
+                        for (uint32_t j = 1; j < P.m && ok2; ++j) {
+                            const uint32_t v = __ldg(pq + j);
+                            ok2 = buf[st + (int32_t)(v >> 8)] == (uint8_t)(v & 0xFFu);
+                        }
+                        cnt += ok2;
+                    }
+                    cnt = warp_sum_u32(cnt);
+                    if (lane == 0 && cnt) atomicAdd(&slots[p - pbase], cnt);
+                }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
@@ -351,6 +451,7 @@ extern "C" sm_status sm_batch_create(sm_ctx* ctx, const uint8_t* d_texts, const 
     std::vector<BatchText> tx;
     std::vector<BatchPat> pats;
     std::vector<uint32_t> qc;
+    std::vector<uint32_t> masks;
     std::vector<double> entry_cost;
     size_t kk = 0;
     for (uint32_t x = 0; x < ntexts; ++x) {
@@ -360,7 +461,9 @@ extern "C" sm_status sm_batch_create(sm_ctx* ctx, const uint8_t* d_texts, const 
         for (int c = 0x80; c < 256; ++c)
             if (h[c]) text7 = false;
         const uint32_t delta = (uint32_t)((reinterpret_cast<uintptr_t>(d_texts) + (uint64_t)h_text_off[x]) & 15u);
-        BatchText cur{(uint64_t)h_text_off[x], n, 0, (uint32_t)pats.size(), (uint32_t)pats.size(), 0, 0};
+        // dense patterns first, then candidate patterns; each with its descriptors
+        std::vector<BatchPat> dense, cand;
+        std::vector<std::vector<uint32_t>> dense_qc, cand_qc;
         for (; kk < npats && (uint32_t)h_pat_text[by_text[kk]] == x; ++kk) {
             const uint32_t k = by_text[kk];
             const uint8_t* p = h_pats + h_pat_off[k];
@@ -368,47 +471,78 @@ extern "C" sm_status sm_batch_create(sm_ctx* ctx, const uint8_t* d_texts, const 
             bool absent = (uint64_t)m > n;
             for (uint32_t q = 0; q < m && !absent; ++q) absent = h[p[q]] == 0;
             if (absent) continue;   // count 0
-            if (cur.pend - cur.pbeg == kMaxSlots) {   // start another group of this text
-                tx.push_back(cur);
-                cur.pbeg = cur.pend;
-                cur.maxm = 0;
-            }
             std::vector<uint32_t> pi(m);
             std::iota(pi.begin(), pi.end(), 0u);
             std::stable_sort(pi.begin(), pi.end(), [&](uint32_t a, uint32_t b) { return h[p[a]] < h[p[b]]; });
+            std::vector<uint32_t> v(m);
+            for (uint32_t j = 0; j < m; ++j) v[j] = ((pi[j] + delta) << 8) | p[pi[j]];
+            const double f0 = (double)h[p[pi[0]]] / (double)n;
+            if (f0 < kCandidateFreq) {   // rare first symbol: candidate path, compares in order pi
+                cand.push_back(BatchPat{0, m, 1, 0, k, text7 ? 1u : 0u});
+                cand_qc.push_back(std::move(v));
+                continue;
+            }
             std::vector<uint32_t> syms(m);
             for (uint32_t j = 0; j < m; ++j) syms[j] = p[pi[j]];
             const uint32_t r = batch_peel(syms, h, n, m);
-            BatchPat bp{(uint32_t)qc.size(), m, r, 0, k, text7 ? 1u : 0u};
+            std::vector<uint32_t> w;
             uint32_t nd[4] = {0, 0, 0, 0};
             for (uint32_t d = 0; d < 4; ++d)
-                for (uint32_t j = 0; j < r; ++j) {
-                    const uint32_t v = ((pi[j] + delta) << 8) | p[pi[j]];
-                    if (((v >> 10) & 3u) == d) {
-                        qc.push_back(v);
+                for (uint32_t j = 0; j < r; ++j)
+                    if (((v[j] >> 10) & 3u) == d) {
+                        w.push_back(v[j]);
                         ++nd[d];
                     }
-                }
-            for (uint32_t j = r; j < m; ++j) qc.push_back(((pi[j] + delta) << 8) | p[pi[j]]);
-            bp.nd = nd[0] | (nd[1] << 8) | (nd[2] << 16) | (nd[3] << 24);
-            pats.push_back(bp);
-            cur.pend = (uint32_t)pats.size();
-            cur.maxm = std::max(cur.maxm, m);
+            for (uint32_t j = r; j < m; ++j) w.push_back(v[j]);
+            dense.push_back(BatchPat{0, m, r, nd[0] | (nd[1] << 8) | (nd[2] << 16) | (nd[3] << 24), k,
+                                     text7 ? 1u : 0u});
+            dense_qc.push_back(std::move(w));
         }
-        if (cur.pend > cur.pbeg) tx.push_back(cur);
+        // entries of at most kMaxSlots patterns: dense ones, then candidates
+        const size_t nall = dense.size() + cand.size();
+        for (size_t g0 = 0; g0 < nall; g0 += kMaxSlots) {
+            const size_t g1 = std::min(nall, g0 + kMaxSlots);
+            BatchText e{(uint64_t)h_text_off[x], n, 0, (uint32_t)pats.size(), 0, 0, 0, 0, 0};
+            uint32_t mask[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            bool any_cand = false;
+            for (size_t i = g0; i < g1; ++i) {
+                const bool is_c = i >= dense.size();
+                if (is_c && !any_cand) {
+                    e.pmid = (uint32_t)pats.size();
+                    any_cand = true;
+                }
+                BatchPat bp = is_c ? cand[i - dense.size()] : dense[i];
+                const std::vector<uint32_t>& w = is_c ? cand_qc[i - dense.size()] : dense_qc[i];
+                bp.qc_off = (uint32_t)qc.size();
+                qc.insert(qc.end(), w.begin(), w.end());
+                if (is_c) mask[(w[0] & 0xFFu) >> 5] |= 1u << (w[0] & 31u);
+                pats.push_back(bp);
+                e.maxm = std::max(e.maxm, bp.m);
+            }
+            e.pend = (uint32_t)pats.size();
+            if (!any_cand) e.pmid = e.pend;
+            if (any_cand) {
+                e.mask_idx = (uint32_t)(masks.size() / 8);
+                masks.insert(masks.end(), mask, mask + 8);
+            }
+            tx.push_back(e);
+        }
     }
-    // items: tiles of each entry over the starts of its shortest pattern
+    // items: tiles of each entry over the starts of its shortest pattern; cost
+    // ~ 1 per tile + 1 per dense pattern + 0.1 per candidate pattern
     uint64_t items = 0;
     uint32_t maxm_all = 1;
+    bool need_index = false;
     for (BatchText& t : tx) {
         uint32_t mn = ~0u;
         for (uint32_t p = t.pbeg; p < t.pend; ++p) mn = std::min(mn, pats[p].m);
         t.item_begin = items;
         items += (t.n - mn + 1 + kTile - 1) / kTile;
         maxm_all = std::max(maxm_all, t.maxm);
-        entry_cost.push_back(1.0 + (double)(t.pend - t.pbeg));
+        entry_cost.push_back(1.0 + (double)(t.pmid - t.pbeg) + 0.1 * (double)(t.pend - t.pmid));
+        need_index |= t.pend > t.pmid;
     }
-    BatchText sentinel{0, 0, items, 0, 0, 0, 0};
+    BatchText sentinel{0, 0, items, 0, 0, 0, 0, 0, 0};
     tx.push_back(sentinel);
 
     sm_batch* b = new sm_batch();
@@ -420,10 +554,13 @@ extern "C" sm_status sm_batch_create(sm_ctx* ctx, const uint8_t* d_texts, const 
     const uint32_t SB = stage_bytes_for(maxm_all);
     uint32_t stages = sm_ctx_stages(ctx);
     size_t smem = 0;
+    const uint32_t index_cap = need_index ? SB : 0u;
+    const size_t index_bytes = index_cap ? ((3072u + 2u * index_cap + 127u) & ~127u) : 0u;
     auto smem_for = [&](uint32_t nslots, uint32_t s) {
-        return (size_t)kScanHeader + kQueueBytes + ((nslots * 4u + 127u) & ~127u) + (size_t)SB * s;
+        return (size_t)kScanHeader + kQueueBytes + ((nslots * 4u + 127u) & ~127u) + index_bytes + (size_t)SB * s;
     };
-    while (stages > 2 && smem_for(kMaxSlots, stages) > sm_ctx_max_smem(ctx)) --stages;
+    // two resident CTAs per SM when the shared memory allows it
+    while (stages > 2 && 2 * smem_for(kMaxSlots, stages) > sm_ctx_max_smem(ctx)) --stages;
     int occ = 0;
     cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_ctx_max_smem(ctx));
     smem = smem_for(kMaxSlots, stages);
@@ -461,9 +598,9 @@ extern "C" sm_status sm_batch_create(sm_ctx* ctx, const uint8_t* d_texts, const 
     // 4. one allocation for every table
     const size_t s_tx = tx.size() * sizeof(BatchText), s_p = std::max<size_t>(pats.size(), 1) * sizeof(BatchPat);
     const size_t s_q = std::max<size_t>(qc.size(), 1) * 4, s_ci = cta_items.size() * 8,
-                 s_cp = std::max<size_t>(cta_pbase.size(), 1) * 4;
+                 s_cp = std::max<size_t>(cta_pbase.size(), 1) * 4, s_m = std::max<size_t>(masks.size(), 8) * 4;
     auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
-    const size_t total = al(s_tx) + al(s_p) + al(s_q) + al(s_ci) + al(s_cp);
+    const size_t total = al(s_tx) + al(s_p) + al(s_q) + al(s_ci) + al(s_cp) + al(s_m);
     if (cudaMalloc(&b->d_mem, total) != cudaSuccess) {
         cudaGetLastError();
         delete b;
@@ -475,11 +612,13 @@ extern "C" sm_status sm_batch_create(sm_ctx* ctx, const uint8_t* d_texts, const 
     uint32_t* d_q = reinterpret_cast<uint32_t*>(base + al(s_tx) + al(s_p));
     uint64_t* d_ci = reinterpret_cast<uint64_t*>(base + al(s_tx) + al(s_p) + al(s_q));
     uint32_t* d_cp = reinterpret_cast<uint32_t*>(base + al(s_tx) + al(s_p) + al(s_q) + al(s_ci));
+    uint32_t* d_m = reinterpret_cast<uint32_t*>(base + al(s_tx) + al(s_p) + al(s_q) + al(s_ci) + al(s_cp));
     cudaError_t e = cudaMemcpy(d_tx, tx.data(), s_tx, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !pats.empty()) e = cudaMemcpy(d_p, pats.data(), pats.size() * sizeof(BatchPat), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !qc.empty()) e = cudaMemcpy(d_q, qc.data(), qc.size() * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d_ci, cta_items.data(), s_ci, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !cta_pbase.empty()) e = cudaMemcpy(d_cp, cta_pbase.data(), cta_pbase.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !masks.empty()) e = cudaMemcpy(d_m, masks.data(), masks.size() * 4, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(b->d_mem);
         delete b;
@@ -487,6 +626,8 @@ extern "C" sm_status sm_batch_create(sm_ctx* ctx, const uint8_t* d_texts, const 
     }
     BatchArgs& a = b->args;
     a.texts = d_texts;
+    a.masks = d_m;
+    a.index_cap = index_cap;
     a.tx = d_tx;
     a.ntx = (uint32_t)tx.size() - 1;
     a.pats = d_p;

@@ -228,6 +228,37 @@ sm_status sm_count_batch(sm_ctx* ctx, const uint8_t* d_texts, const int64_t* d_t
                          uint32_t npats, int64_t* d_counts, uint64_t* d_pos, const int64_t* d_pos_off,
                          sm_stream_t stream);
 
+/* ------------------------------------------------------------- serving */
+/*
+ * Continuous batching over one device-resident text (the serving loop's
+ * core). The text is cut into chunks of chunk_bytes (a multiple of
+ * SM_TILE_STARTS); a step scans one chunk for every active query in one
+ * batched launch, so concurrent queries share each pass over the text. A
+ * query admitted before a step on chunk c and stepped on every chunk once
+ * (in any order, e.g. c, c+1, ..., c-1) has its full count in its counter.
+ *
+ *   sm_stepper_create  d_text (n bytes, device, resident for the stepper's
+ *                      life), queries up to max_m bytes, h_hist256 = the
+ *                      text's histogram (orders, Sec. 2.2)
+ *   sm_stepper_admit   describe query qid (pattern copied; m <= max_m)
+ *   sm_stepper_step    add the counts of chunk `chunk` for the queries
+ *                      h_qids[0..nq) into d_counts[qid] (int64, device;
+ *                      the caller zeroes a counter before its first step).
+ *                      Asynchronous on `stream`; allocates nothing once its
+ *                      two table buffers have grown to the batch size.
+ *   sm_stepper_retire  forget qid.
+ * One stepper is driven from one host thread and one stream.
+ */
+typedef struct sm_stepper sm_stepper;
+sm_status sm_stepper_create(sm_ctx* ctx, const uint8_t* d_text, uint64_t n, uint64_t chunk_bytes,
+                            uint32_t max_m, const uint64_t* h_hist256, sm_stepper** out);
+uint32_t sm_stepper_chunks(const sm_stepper* stepper);
+sm_status sm_stepper_admit(sm_stepper* stepper, uint32_t qid, const uint8_t* h_pat, uint32_t m);
+sm_status sm_stepper_step(sm_stepper* stepper, const uint32_t* h_qids, uint32_t nq, uint32_t chunk,
+                          int64_t* d_counts, sm_stream_t stream);
+sm_status sm_stepper_retire(sm_stepper* stepper, uint32_t qid);
+void sm_stepper_destroy(sm_stepper* stepper);
+
 /* ------------------------------------------------------- no allocation */
 /*
  * sm_report_noalloc - the report of sm_report for callers that must not

@@ -23,6 +23,7 @@
 #include <cmath>
 #include <cstring>
 #include <numeric>
+#include <unordered_map>
 #include <vector>
 
 namespace smk {
@@ -38,8 +39,9 @@ constexpr double kCandidateFreq = 0.08;
 
 struct BatchText {        // a text, or one group of <= kMaxSlots of its patterns
     uint64_t off;         // byte offset in the packed texts
-    uint64_t n;           // length
+    uint64_t n;           // length (bytes readable from off)
     uint64_t item_begin;  // first work item (tile) of this entry
+    uint64_t slimit;      // only starts below this are counted (a chunk of a longer text)
     uint32_t pbeg, pmid;  // patterns [pbeg, pmid) run the dense scan ...
     uint32_t pend;        // ... and [pmid, pend) the candidate path
     uint32_t maxm;
@@ -201,7 +203,7 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constan
             // dense patterns: every warp scans its 2048 starts
             for (uint32_t p = T.pbeg; p < T.pmid; ++p) {
                 const BatchPat P = A.pats[p];
-                const uint64_t nst = T.n - P.m + 1;   // the plan keeps only patterns with m <= n
+                const uint64_t nst = min(T.n - P.m + 1, T.slimit);   // the plan keeps only m <= n
                 if (s0 >= nst) continue;
                 const GlobalQC qc{A.qc + P.qc_off};
                 const uint32_t nd0 = P.nd & 0xFFu, nd1 = (P.nd >> 8) & 0xFFu, nd2 = (P.nd >> 16) & 0xFFu,
@@ -257,7 +259,7 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constan
                 consumers_sync();
                 for (uint32_t p = T.pmid + warp; p < T.pend; p += kConsumerWarps) {
                     const BatchPat P = A.pats[p];
-                    const uint64_t nst = T.n - P.m + 1;
+                    const uint64_t nst = min(T.n - P.m + 1, T.slimit);
                     if (s0 >= nst) continue;
                     const int32_t valid = (int32_t)min((uint64_t)kTile, nst - s0);
                     const uint32_t* pq = A.qc + P.qc_off;
@@ -330,17 +332,21 @@ __global__ void __launch_bounds__(256) batch_hist_kernel(const uint8_t* texts, c
 
 // ------------------------------------------------------------------ host
 
-struct sm_batch {
-    sm_ctx* ctx = nullptr;
-    int device = 0;
-    uint32_t npats = 0;      // caller's pattern count (size of d_counts)
-    uint32_t grid = 0;
-    size_t smem = 0;
-    smk::BatchArgs args{};
-    void* d_mem = nullptr;   // one allocation holding every table
-};
+sm_status sm_fail_internal(sm_status s, const char* msg);   // defined in sm_api.cpp
+int sm_ctx_device(const sm_ctx* c);
+int sm_ctx_num_sms(const sm_ctx* c);
+size_t sm_ctx_max_smem(const sm_ctx* c);
+uint32_t* sm_ctx_status(const sm_ctx* c);
+uint64_t sm_ctx_spin_ns(const sm_ctx* c);
+uint32_t sm_ctx_stages(const sm_ctx* c);
 
 namespace {
+
+using smk::BatchArgs;
+using smk::BatchPat;
+using smk::BatchText;
+using smk::kMaxSlots;
+using smk::kTile;
 
 struct Guard {
     int prev = -1;
@@ -354,13 +360,13 @@ struct Guard {
     }
 };
 
-// peel factor from the pattern's symbol frequencies (same cost model as the
-// single-pattern scan: dense compare ~100, compaction ~80, 32 words ~60)
-uint32_t batch_peel(const std::vector<uint32_t>& qsym_freq_order, const uint32_t* h, uint64_t n, uint32_t m) {
+// Peel factor from the pattern's symbol frequencies (the single-pattern
+// scan's cost model: dense compare ~100, compaction ~80, 32 words ~60).
+uint32_t batch_peel(const std::vector<uint32_t>& syms, const uint32_t* h, uint64_t n, uint32_t m) {
     double alive = 1.0, best = 1e300;
     uint32_t best_r = 1;
     for (uint32_t r = 1; r <= std::min<uint32_t>(m, 16); ++r) {
-        alive *= (double)h[qsym_freq_order[r - 1]] / (double)n;
+        alive *= (double)h[syms[r - 1]] / (double)n;
         double cost = 100.0 * r;
         if (r < m) {
             const double p_word = 1.0 - std::pow(1.0 - alive, 4.0);
@@ -377,16 +383,229 @@ uint32_t batch_peel(const std::vector<uint32_t>& qsym_freq_order, const uint32_t
     return best_r;
 }
 
+// One pattern described for a text with byte histogram h (n bytes): the
+// rarest-first order (Sec. 2.2), then either the dense scan (peel r, peeled
+// compares grouped by word alignment) or the candidate path (compares in
+// order pi, the first being the rarest symbol).
+struct PatDesc {
+    BatchPat pat{};
+    std::vector<uint32_t> qc;
+    bool cand = false;
+    bool zero = false;   // a symbol never occurs in the text, or m > n: count 0
+};
+
+PatDesc describe(const uint8_t* p, uint32_t m, const uint32_t* h, uint64_t n, uint32_t delta, bool text7,
+                 uint32_t out) {
+    PatDesc d;
+    d.zero = (uint64_t)m > n;
+    for (uint32_t q = 0; q < m && !d.zero; ++q) d.zero = h[p[q]] == 0;
+    if (d.zero) return d;
+    std::vector<uint32_t> pi(m);
+    std::iota(pi.begin(), pi.end(), 0u);
+    std::stable_sort(pi.begin(), pi.end(), [&](uint32_t a, uint32_t b) { return h[p[a]] < h[p[b]]; });
+    std::vector<uint32_t> v(m);
+    for (uint32_t j = 0; j < m; ++j) v[j] = ((pi[j] + delta) << 8) | p[pi[j]];
+    d.pat = BatchPat{0, m, 1, 0, out, text7 ? 1u : 0u};
+    if ((double)h[p[pi[0]]] / (double)n < smk::kCandidateFreq) {
+        d.cand = true;
+        d.qc = std::move(v);
+        return d;
+    }
+    std::vector<uint32_t> syms(m);
+    for (uint32_t j = 0; j < m; ++j) syms[j] = p[pi[j]];
+    const uint32_t r = batch_peel(syms, h, n, m);
+    uint32_t nd[4] = {0, 0, 0, 0};
+    for (uint32_t c = 0; c < 4; ++c)
+        for (uint32_t j = 0; j < r; ++j)
+            if (((v[j] >> 10) & 3u) == c) {
+                d.qc.push_back(v[j]);
+                ++nd[c];
+            }
+    for (uint32_t j = r; j < m; ++j) d.qc.push_back(v[j]);
+    d.pat.r = r;
+    d.pat.nd = nd[0] | (nd[1] << 8) | (nd[2] << 16) | (nd[3] << 24);
+    return d;
+}
+
+// Host tables of one launch.
+struct Tables {
+    std::vector<BatchText> tx;
+    std::vector<BatchPat> pats;
+    std::vector<uint32_t> qc, masks, cta_pbase;
+    std::vector<uint64_t> cta_items;
+    std::vector<double> cost;
+    uint64_t items = 0;
+    uint32_t nslots = 1, maxm = 1;
+    bool need_index = false;
+};
+
+// Entries for one text region [off, off + n) counting starts below slimit:
+// groups of at most kMaxSlots patterns, dense ones first.
+void add_text(Tables& T, uint64_t off, uint64_t n, uint64_t slimit, const std::vector<const PatDesc*>& ds) {
+    std::vector<const PatDesc*> order;
+    for (const PatDesc* d : ds)
+        if (!d->zero && !d->cand) order.push_back(d);
+    const size_t ndense = order.size();
+    for (const PatDesc* d : ds)
+        if (!d->zero && d->cand) order.push_back(d);
+    for (size_t g0 = 0; g0 < order.size(); g0 += kMaxSlots) {
+        const size_t g1 = std::min(order.size(), g0 + kMaxSlots);
+        BatchText e{off, n, 0, slimit, (uint32_t)T.pats.size(), 0, 0, 0, 0, 0};
+        uint32_t mask[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        bool any_cand = false;
+        uint32_t mn = ~0u;
+        for (size_t i = g0; i < g1; ++i) {
+            const PatDesc* d = order[i];
+            if (i >= ndense && !any_cand) {
+                e.pmid = (uint32_t)T.pats.size();
+                any_cand = true;
+            }
+            BatchPat bp = d->pat;
+            bp.qc_off = (uint32_t)T.qc.size();
+            T.qc.insert(T.qc.end(), d->qc.begin(), d->qc.end());
+            if (d->cand) mask[(d->qc[0] & 0xFFu) >> 5] |= 1u << (d->qc[0] & 31u);
+            T.pats.push_back(bp);
+            e.maxm = std::max(e.maxm, bp.m);
+            mn = std::min(mn, bp.m);
+        }
+        e.pend = (uint32_t)T.pats.size();
+        if (!any_cand) e.pmid = e.pend;
+        if (any_cand) {
+            e.mask_idx = (uint32_t)(T.masks.size() / 8);
+            T.masks.insert(T.masks.end(), mask, mask + 8);
+        }
+        e.item_begin = T.items;
+        T.items += (std::min<uint64_t>(n - mn + 1, slimit) + kTile - 1) / kTile;
+        T.maxm = std::max(T.maxm, e.maxm);
+        T.need_index |= any_cand;
+        T.cost.push_back(1.0 + (double)(e.pmid - e.pbeg) + 0.1 * (double)(e.pend - e.pmid));
+        T.tx.push_back(e);
+    }
+}
+
+// Sentinel entry and CTA ranges of about equal cost (tiles x patterns), each
+// counting at most kMaxSlots patterns in shared memory.
+void finish(Tables& T, uint64_t want_ctas) {
+    T.tx.push_back(BatchText{0, 0, T.items, 0, 0, 0, 0, 0, 0, 0});
+    double total = 0;
+    for (size_t e = 0; e + 1 < T.tx.size(); ++e)
+        total += T.cost[e] * (double)(T.tx[e + 1].item_begin - T.tx[e].item_begin);
+    const double per_cta = std::max(1.0, total / (double)std::max<uint64_t>(want_ctas, 1));
+    T.cta_items.assign(1, 0);
+    T.cta_pbase.clear();
+    T.nslots = 1;
+    for (uint64_t item = 0, e = 0; item < T.items;) {
+        while (T.tx[e + 1].item_begin <= item) ++e;   // entry of the CTA's first item
+        const uint32_t pb = T.tx[e].pbeg;
+        double acc = 0;
+        uint64_t it = item, ee = e;
+        while (it < T.items) {
+            while (T.tx[ee + 1].item_begin <= it) ++ee;
+            if (T.tx[ee].pend - pb > kMaxSlots) break;   // pattern window full: next CTA
+            acc += T.cost[ee];
+            ++it;
+            if (acc >= per_cta) break;
+        }
+        uint64_t el = e;                                // entry of the CTA's last item
+        while (T.tx[el + 1].item_begin < it) ++el;
+        T.cta_items.push_back(it);
+        T.cta_pbase.push_back(pb);
+        T.nslots = std::max(T.nslots, T.tx[el].pend - pb);
+        item = it;
+    }
+}
+
+struct Geometry {
+    uint32_t SB = 0, stages = 2, index_cap = 0;
+    int occ = 1;
+    size_t smem(uint32_t nslots) const {
+        const size_t ib = index_cap ? ((3072u + 2u * index_cap + 127u) & ~127u) : 0u;
+        return (size_t)smk::kScanHeader + smk::kQueueBytes + ((nslots * 4u + 127u) & ~127u) + ib + (size_t)SB * stages;
+    }
+};
+
+Geometry geometry(sm_ctx* ctx, uint32_t maxm, bool need_index) {
+    Geometry g;
+    g.SB = smk::stage_bytes_for(maxm);
+    g.index_cap = need_index ? g.SB : 0u;
+    g.stages = sm_ctx_stages(ctx);
+    // two resident CTAs per SM when the shared memory allows it
+    while (g.stages > 2 && 2 * g.smem(kMaxSlots) > sm_ctx_max_smem(ctx)) --g.stages;
+    cudaFuncSetAttribute(smk::batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_ctx_max_smem(ctx));
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, smk::batch_kernel, smk::kThreads, g.smem(kMaxSlots));
+    g.occ = std::max(occ, 1);
+    return g;
+}
+
+// Byte layout of the tables in one buffer (host staging and device copy).
+struct Layout {
+    size_t tx = 0, pats = 0, qc = 0, ci = 0, cp = 0, masks = 0, total = 0;
+};
+
+Layout layout_of(const Tables& T) {
+    auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    Layout L;
+    size_t o = 0;
+    L.tx = o; o += al(T.tx.size() * sizeof(BatchText));
+    L.pats = o; o += al(std::max<size_t>(T.pats.size(), 1) * sizeof(BatchPat));
+    L.qc = o; o += al(std::max<size_t>(T.qc.size(), 1) * 4);
+    L.ci = o; o += al(T.cta_items.size() * 8);
+    L.cp = o; o += al(std::max<size_t>(T.cta_pbase.size(), 1) * 4);
+    L.masks = o; o += al(std::max<size_t>(T.masks.size(), 8) * 4);
+    L.total = o;
+    return L;
+}
+
+void pack(const Tables& T, const Layout& L, char* h) {
+    std::memcpy(h + L.tx, T.tx.data(), T.tx.size() * sizeof(BatchText));
+    if (!T.pats.empty()) std::memcpy(h + L.pats, T.pats.data(), T.pats.size() * sizeof(BatchPat));
+    if (!T.qc.empty()) std::memcpy(h + L.qc, T.qc.data(), T.qc.size() * 4);
+    std::memcpy(h + L.ci, T.cta_items.data(), T.cta_items.size() * 8);
+    if (!T.cta_pbase.empty()) std::memcpy(h + L.cp, T.cta_pbase.data(), T.cta_pbase.size() * 4);
+    if (!T.masks.empty()) std::memcpy(h + L.masks, T.masks.data(), T.masks.size() * 4);
+}
+
+BatchArgs args_for(sm_ctx* ctx, const uint8_t* d_texts, const Tables& T, const Layout& L, char* d,
+                   const Geometry& g) {
+    BatchArgs a{};
+    a.texts = d_texts;
+    a.masks = reinterpret_cast<const uint32_t*>(d + L.masks);
+    a.tx = reinterpret_cast<const BatchText*>(d + L.tx);
+    a.ntx = (uint32_t)T.tx.size() - 1;
+    a.pats = reinterpret_cast<const BatchPat*>(d + L.pats);
+    a.qc = reinterpret_cast<const uint32_t*>(d + L.qc);
+    a.cta_items = reinterpret_cast<const uint64_t*>(d + L.ci);
+    a.cta_pbase = reinterpret_cast<const uint32_t*>(d + L.cp);
+    a.stage_bytes = g.SB;
+    a.stages = g.stages;
+    a.one = 1;
+    a.nslots = T.nslots;
+    a.index_cap = g.index_cap;
+    a.status = sm_ctx_status(ctx);
+    a.spin_ns = sm_ctx_spin_ns(ctx);
+    return a;
+}
+
+bool text_is_7bit(const uint32_t* h) {
+    for (int c = 0x80; c < 256; ++c)
+        if (h[c]) return false;
+    return true;
+}
+
 }  // namespace
 
-extern "C" const char* sm_last_error(void);
-sm_status sm_fail_internal(sm_status s, const char* msg);   // defined in sm_api.cpp
-int sm_ctx_device(const sm_ctx* c);
-int sm_ctx_num_sms(const sm_ctx* c);
-size_t sm_ctx_max_smem(const sm_ctx* c);
-uint32_t* sm_ctx_status(const sm_ctx* c);
-uint64_t sm_ctx_spin_ns(const sm_ctx* c);
-uint32_t sm_ctx_stages(const sm_ctx* c);
+// ------------------------------------------------------------------ batch
+
+struct sm_batch {
+    sm_ctx* ctx = nullptr;
+    int device = 0;
+    uint32_t npats = 0;      // caller's pattern count (size of d_counts)
+    uint32_t grid = 0;
+    size_t smem = 0;
+    BatchArgs args{};
+    void* d_mem = nullptr;   // one allocation holding every table
+};
 
 extern "C" sm_status sm_batch_create(sm_ctx* ctx, const uint8_t* d_texts, const int64_t* h_text_off, uint32_t ntexts,
                                      const uint8_t* h_pats, const int64_t* h_pat_off, const int32_t* h_pat_text,
@@ -397,18 +616,17 @@ extern "C" sm_status sm_batch_create(sm_ctx* ctx, const uint8_t* d_texts, const 
     if (!ctx || !h_text_off || (npats && (!h_pats || !h_pat_off || !h_pat_text)))
         return sm_fail_internal(SM_EINVAL, "NULL argument");
     if (ntexts == 0) return sm_fail_internal(SM_EINVAL, "no texts");
-    const uint64_t total_bytes = (uint64_t)h_text_off[ntexts];
     if (h_text_off[0] != 0) return sm_fail_internal(SM_EINVAL, "h_text_off[0] must be 0");
     for (uint32_t x = 0; x < ntexts; ++x)
         if (h_text_off[x + 1] < h_text_off[x]) return sm_fail_internal(SM_EINVAL, "text offsets must not decrease");
-    if (total_bytes && !d_texts) return sm_fail_internal(SM_EINVAL, "d_texts is NULL");
+    if (h_text_off[ntexts] && !d_texts) return sm_fail_internal(SM_EINVAL, "d_texts is NULL");
     for (uint32_t k = 0; k < npats; ++k) {
         const int64_t m = h_pat_off[k + 1] - h_pat_off[k];
         if (m < 1 || m > (int64_t)SM_MAX_M) return sm_fail_internal(SM_EINVAL, "pattern length out of range");
         if (h_pat_text[k] < 0 || (uint32_t)h_pat_text[k] >= ntexts)
             return sm_fail_internal(SM_EINVAL, "pattern refers to a missing text");
     }
-    Guard g(sm_ctx_device(ctx));
+    Guard guard(sm_ctx_device(ctx));
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
 
     // 1. per-text histograms on the device
@@ -443,203 +661,53 @@ extern "C" sm_status sm_batch_create(sm_ctx* ctx, const uint8_t* d_texts, const 
         if (e != cudaSuccess) return sm_fail_internal(SM_ECUDA, cudaGetErrorString(e));
     }
 
-    // 2. patterns grouped by text; orders, peels, compare descriptors
+    // 2. patterns grouped by text, described under their text's frequencies
     std::vector<uint32_t> by_text(npats);
     std::iota(by_text.begin(), by_text.end(), 0u);
     std::stable_sort(by_text.begin(), by_text.end(),
                      [&](uint32_t a, uint32_t b) { return h_pat_text[a] < h_pat_text[b]; });
-    std::vector<BatchText> tx;
-    std::vector<BatchPat> pats;
-    std::vector<uint32_t> qc;
-    std::vector<uint32_t> masks;
-    std::vector<double> entry_cost;
+    Tables T;
     size_t kk = 0;
     for (uint32_t x = 0; x < ntexts; ++x) {
         const uint64_t n = (uint64_t)(h_text_off[x + 1] - h_text_off[x]);
         const uint32_t* h = &hist[(size_t)x * 256];
-        bool text7 = true;
-        for (int c = 0x80; c < 256; ++c)
-            if (h[c]) text7 = false;
+        const bool text7 = text_is_7bit(h);
         const uint32_t delta = (uint32_t)((reinterpret_cast<uintptr_t>(d_texts) + (uint64_t)h_text_off[x]) & 15u);
-        // dense patterns first, then candidate patterns; each with its descriptors
-        std::vector<BatchPat> dense, cand;
-        std::vector<std::vector<uint32_t>> dense_qc, cand_qc;
+        std::vector<PatDesc> descs;
         for (; kk < npats && (uint32_t)h_pat_text[by_text[kk]] == x; ++kk) {
             const uint32_t k = by_text[kk];
-            const uint8_t* p = h_pats + h_pat_off[k];
-            const uint32_t m = (uint32_t)(h_pat_off[k + 1] - h_pat_off[k]);
-            bool absent = (uint64_t)m > n;
-            for (uint32_t q = 0; q < m && !absent; ++q) absent = h[p[q]] == 0;
-            if (absent) continue;   // count 0
-            std::vector<uint32_t> pi(m);
-            std::iota(pi.begin(), pi.end(), 0u);
-            std::stable_sort(pi.begin(), pi.end(), [&](uint32_t a, uint32_t b) { return h[p[a]] < h[p[b]]; });
-            std::vector<uint32_t> v(m);
-            for (uint32_t j = 0; j < m; ++j) v[j] = ((pi[j] + delta) << 8) | p[pi[j]];
-            const double f0 = (double)h[p[pi[0]]] / (double)n;
-            if (f0 < kCandidateFreq) {   // rare first symbol: candidate path, compares in order pi
-                cand.push_back(BatchPat{0, m, 1, 0, k, text7 ? 1u : 0u});
-                cand_qc.push_back(std::move(v));
-                continue;
-            }
-            std::vector<uint32_t> syms(m);
-            for (uint32_t j = 0; j < m; ++j) syms[j] = p[pi[j]];
-            const uint32_t r = batch_peel(syms, h, n, m);
-            std::vector<uint32_t> w;
-            uint32_t nd[4] = {0, 0, 0, 0};
-            for (uint32_t d = 0; d < 4; ++d)
-                for (uint32_t j = 0; j < r; ++j)
-                    if (((v[j] >> 10) & 3u) == d) {
-                        w.push_back(v[j]);
-                        ++nd[d];
-                    }
-            for (uint32_t j = r; j < m; ++j) w.push_back(v[j]);
-            dense.push_back(BatchPat{0, m, r, nd[0] | (nd[1] << 8) | (nd[2] << 16) | (nd[3] << 24), k,
-                                     text7 ? 1u : 0u});
-            dense_qc.push_back(std::move(w));
+            descs.push_back(describe(h_pats + h_pat_off[k], (uint32_t)(h_pat_off[k + 1] - h_pat_off[k]), h, n, delta,
+                                     text7, k));
         }
-        // entries of at most kMaxSlots patterns: dense ones, then candidates
-        const size_t nall = dense.size() + cand.size();
-        for (size_t g0 = 0; g0 < nall; g0 += kMaxSlots) {
-            const size_t g1 = std::min(nall, g0 + kMaxSlots);
-            BatchText e{(uint64_t)h_text_off[x], n, 0, (uint32_t)pats.size(), 0, 0, 0, 0, 0};
-            uint32_t mask[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            bool any_cand = false;
-            for (size_t i = g0; i < g1; ++i) {
-                const bool is_c = i >= dense.size();
-                if (is_c && !any_cand) {
-                    e.pmid = (uint32_t)pats.size();
-                    any_cand = true;
-                }
-                BatchPat bp = is_c ? cand[i - dense.size()] : dense[i];
-                const std::vector<uint32_t>& w = is_c ? cand_qc[i - dense.size()] : dense_qc[i];
-                bp.qc_off = (uint32_t)qc.size();
-                qc.insert(qc.end(), w.begin(), w.end());
-                if (is_c) mask[(w[0] & 0xFFu) >> 5] |= 1u << (w[0] & 31u);
-                pats.push_back(bp);
-                e.maxm = std::max(e.maxm, bp.m);
-            }
-            e.pend = (uint32_t)pats.size();
-            if (!any_cand) e.pmid = e.pend;
-            if (any_cand) {
-                e.mask_idx = (uint32_t)(masks.size() / 8);
-                masks.insert(masks.end(), mask, mask + 8);
-            }
-            tx.push_back(e);
-        }
+        std::vector<const PatDesc*> ptrs;
+        for (const PatDesc& d : descs) ptrs.push_back(&d);
+        add_text(T, (uint64_t)h_text_off[x], n, ~0ull, ptrs);
     }
-    // items: tiles of each entry over the starts of its shortest pattern; cost
-    // ~ 1 per tile + 1 per dense pattern + 0.1 per candidate pattern
-    uint64_t items = 0;
-    uint32_t maxm_all = 1;
-    bool need_index = false;
-    for (BatchText& t : tx) {
-        uint32_t mn = ~0u;
-        for (uint32_t p = t.pbeg; p < t.pend; ++p) mn = std::min(mn, pats[p].m);
-        t.item_begin = items;
-        items += (t.n - mn + 1 + kTile - 1) / kTile;
-        maxm_all = std::max(maxm_all, t.maxm);
-        entry_cost.push_back(1.0 + (double)(t.pmid - t.pbeg) + 0.1 * (double)(t.pend - t.pmid));
-        need_index |= t.pend > t.pmid;
-    }
-    BatchText sentinel{0, 0, items, 0, 0, 0, 0, 0, 0};
-    tx.push_back(sentinel);
+    const Geometry g = geometry(ctx, T.maxm, T.need_index);
+    finish(T, (uint64_t)sm_ctx_num_sms(ctx) * g.occ);
 
+    // 3. one allocation for every table
+    const Layout L = layout_of(T);
+    std::vector<char> host(L.total);
+    pack(T, L, host.data());
     sm_batch* b = new sm_batch();
     b->ctx = ctx;
     b->device = sm_ctx_device(ctx);
     b->npats = npats;
-
-    // 3. CTA ranges: equal cost (tiles x patterns), each within kMaxSlots patterns
-    const uint32_t SB = stage_bytes_for(maxm_all);
-    uint32_t stages = sm_ctx_stages(ctx);
-    size_t smem = 0;
-    const uint32_t index_cap = need_index ? SB : 0u;
-    const size_t index_bytes = index_cap ? ((3072u + 2u * index_cap + 127u) & ~127u) : 0u;
-    auto smem_for = [&](uint32_t nslots, uint32_t s) {
-        return (size_t)kScanHeader + kQueueBytes + ((nslots * 4u + 127u) & ~127u) + index_bytes + (size_t)SB * s;
-    };
-    // two resident CTAs per SM when the shared memory allows it
-    while (stages > 2 && 2 * smem_for(kMaxSlots, stages) > sm_ctx_max_smem(ctx)) --stages;
-    int occ = 0;
-    cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_ctx_max_smem(ctx));
-    smem = smem_for(kMaxSlots, stages);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel, kThreads, smem);
-    const uint64_t want = std::max<uint64_t>(1, (uint64_t)sm_ctx_num_sms(ctx) * std::max(occ, 1));
-    double total_cost = 0;
-    for (size_t e = 0; e + 1 < tx.size(); ++e)
-        total_cost += entry_cost[e] * (double)(tx[e + 1].item_begin - tx[e].item_begin);
-    const double per_cta = std::max(1.0, total_cost / (double)want);
-    std::vector<uint64_t> cta_items{0};
-    std::vector<uint32_t> cta_pbase;
-    uint32_t nslots = 1;
-    for (uint64_t item = 0, e = 0; item < items;) {
-        while (tx[e + 1].item_begin <= item) ++e;   // entry of the CTA's first item
-        const uint32_t pb = tx[e].pbeg;
-        double acc = 0;
-        uint64_t it = item, ee = e;
-        while (it < items) {
-            while (tx[ee + 1].item_begin <= it) ++ee;
-            if (tx[ee].pend - pb > kMaxSlots) break;   // pattern window full: next CTA
-            acc += entry_cost[ee];
-            ++it;
-            if (acc >= per_cta) break;
-        }
-        uint64_t el = e;                            // entry of the CTA's last item
-        while (tx[el + 1].item_begin < it) ++el;
-        cta_items.push_back(it);
-        cta_pbase.push_back(pb);
-        nslots = std::max(nslots, tx[el].pend - pb);
-        item = it;
-    }
-    b->grid = (uint32_t)cta_pbase.size();
-    b->smem = smem_for(nslots, stages);
-
-    // 4. one allocation for every table
-    const size_t s_tx = tx.size() * sizeof(BatchText), s_p = std::max<size_t>(pats.size(), 1) * sizeof(BatchPat);
-    const size_t s_q = std::max<size_t>(qc.size(), 1) * 4, s_ci = cta_items.size() * 8,
-                 s_cp = std::max<size_t>(cta_pbase.size(), 1) * 4, s_m = std::max<size_t>(masks.size(), 8) * 4;
-    auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
-    const size_t total = al(s_tx) + al(s_p) + al(s_q) + al(s_ci) + al(s_cp) + al(s_m);
-    if (cudaMalloc(&b->d_mem, total) != cudaSuccess) {
+    if (cudaMalloc(&b->d_mem, L.total) != cudaSuccess) {
         cudaGetLastError();
         delete b;
         return sm_fail_internal(SM_ENOMEM, "batch plan tables");
     }
-    char* base = static_cast<char*>(b->d_mem);
-    BatchText* d_tx = reinterpret_cast<BatchText*>(base);
-    BatchPat* d_p = reinterpret_cast<BatchPat*>(base + al(s_tx));
-    uint32_t* d_q = reinterpret_cast<uint32_t*>(base + al(s_tx) + al(s_p));
-    uint64_t* d_ci = reinterpret_cast<uint64_t*>(base + al(s_tx) + al(s_p) + al(s_q));
-    uint32_t* d_cp = reinterpret_cast<uint32_t*>(base + al(s_tx) + al(s_p) + al(s_q) + al(s_ci));
-    uint32_t* d_m = reinterpret_cast<uint32_t*>(base + al(s_tx) + al(s_p) + al(s_q) + al(s_ci) + al(s_cp));
-    cudaError_t e = cudaMemcpy(d_tx, tx.data(), s_tx, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !pats.empty()) e = cudaMemcpy(d_p, pats.data(), pats.size() * sizeof(BatchPat), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !qc.empty()) e = cudaMemcpy(d_q, qc.data(), qc.size() * 4, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(d_ci, cta_items.data(), s_ci, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !cta_pbase.empty()) e = cudaMemcpy(d_cp, cta_pbase.data(), cta_pbase.size() * 4, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !masks.empty()) e = cudaMemcpy(d_m, masks.data(), masks.size() * 4, cudaMemcpyHostToDevice);
+    const cudaError_t e = cudaMemcpy(b->d_mem, host.data(), L.total, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(b->d_mem);
         delete b;
         return sm_fail_internal(SM_ECUDA, cudaGetErrorString(e));
     }
-    BatchArgs& a = b->args;
-    a.texts = d_texts;
-    a.masks = d_m;
-    a.index_cap = index_cap;
-    a.tx = d_tx;
-    a.ntx = (uint32_t)tx.size() - 1;
-    a.pats = d_p;
-    a.qc = d_q;
-    a.cta_items = d_ci;
-    a.cta_pbase = d_cp;
-    a.stage_bytes = SB;
-    a.stages = stages;
-    a.one = 1;
-    a.nslots = nslots;
-    a.status = sm_ctx_status(ctx);
-    a.spin_ns = sm_ctx_spin_ns(ctx);
+    b->args = args_for(ctx, d_texts, T, L, static_cast<char*>(b->d_mem), g);
+    b->grid = (uint32_t)T.cta_pbase.size();
+    b->smem = g.smem(T.nslots);
     *out = b;
     return SM_OK;
 }
@@ -652,7 +720,7 @@ extern "C" sm_status sm_batch_count(sm_batch* b, int64_t* d_counts, sm_stream_t 
     cudaError_t e = cudaSuccess;
     if (b->npats) e = cudaMemsetAsync(d_counts, 0, (size_t)b->npats * sizeof(int64_t), st);
     if (e == cudaSuccess && b->grid) {
-        smk::BatchArgs a = b->args;
+        BatchArgs a = b->args;
         a.d_counts = d_counts;
         smk::batch_kernel<<<b->grid, smk::kThreads, b->smem, st>>>(a);
         e = cudaGetLastError();
@@ -719,4 +787,145 @@ extern "C" sm_status sm_count_batch(sm_ctx* ctx, const uint8_t* d_texts, const i
     cudaStreamSynchronize(st);
     sm_batch_destroy(b);
     return s;
+}
+
+// ------------------------------------------------------------------ stepper
+//
+// Continuous batching over a device-resident text cut into chunks. Each step
+// scans one chunk for every active query in one batch launch (the queries
+// share the chunk's pass over HBM); a query that joins at chunk c is complete
+// after one step on every chunk. Counts accumulate into the caller's
+// per-query int64 counters. A step allocates nothing: its tables are built in
+// one of two pinned host buffers and copied asynchronously to one of two
+// device buffers, alternating, so that building step k+1 overlaps step k.
+
+struct sm_stepper {
+    sm_ctx* ctx = nullptr;
+    int device = 0;
+    const uint8_t* d_text = nullptr;
+    uint64_t n = 0, chunk = 0;
+    uint32_t nchunks = 0, max_m = 0, delta = 0;
+    bool text7 = true;
+    uint32_t hist[256] = {};
+    Geometry geo;
+    std::unordered_map<uint32_t, PatDesc> queries;
+    struct Buf {
+        char* d = nullptr;
+        char* h = nullptr;
+        size_t cap = 0;
+        cudaEvent_t ev = nullptr;
+        bool used = false;
+    } buf[2];
+    int cur = 0;
+};
+
+extern "C" sm_status sm_stepper_create(sm_ctx* ctx, const uint8_t* d_text, uint64_t n, uint64_t chunk_bytes,
+                                       uint32_t max_m, const uint64_t* h_hist256, sm_stepper** out) {
+    if (!out) return sm_fail_internal(SM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!ctx || !h_hist256 || (!d_text && n)) return sm_fail_internal(SM_EINVAL, "NULL argument");
+    if (max_m < 1 || max_m > SM_MAX_M) return sm_fail_internal(SM_EINVAL, "max_m out of range");
+    if (chunk_bytes < smk::kTile || chunk_bytes % smk::kTile)
+        return sm_fail_internal(SM_EINVAL, "chunk_bytes must be a positive multiple of SM_TILE_STARTS");
+    Guard g(sm_ctx_device(ctx));
+    sm_stepper* s = new sm_stepper();
+    s->ctx = ctx;
+    s->device = sm_ctx_device(ctx);
+    s->d_text = d_text;
+    s->n = n;
+    s->chunk = chunk_bytes;
+    s->nchunks = (uint32_t)((n + chunk_bytes - 1) / chunk_bytes);
+    s->max_m = max_m;
+    s->delta = (uint32_t)(reinterpret_cast<uintptr_t>(d_text) & 15u);
+    for (int c = 0; c < 256; ++c) s->hist[c] = (uint32_t)std::min<uint64_t>(h_hist256[c], 0xFFFFFFFFull);
+    s->text7 = text_is_7bit(s->hist);
+    s->geo = geometry(ctx, max_m, true);
+    for (auto& b : s->buf)
+        if (cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            sm_stepper_destroy(s);
+            return sm_fail_internal(SM_ECUDA, "event");
+        }
+    *out = s;
+    return SM_OK;
+}
+
+extern "C" uint32_t sm_stepper_chunks(const sm_stepper* s) { return s ? s->nchunks : 0; }
+
+extern "C" sm_status sm_stepper_admit(sm_stepper* s, uint32_t qid, const uint8_t* h_pat, uint32_t m) {
+    if (!s || !h_pat) return sm_fail_internal(SM_EINVAL, "NULL argument");
+    if (m < 1 || m > s->max_m) return sm_fail_internal(SM_EINVAL, "pattern length out of range for this stepper");
+    // orders from the whole resident text's frequencies (counts never depend on them)
+    s->queries[qid] = describe(h_pat, m, s->hist, s->n, s->delta, s->text7, qid);
+    return SM_OK;
+}
+
+extern "C" sm_status sm_stepper_retire(sm_stepper* s, uint32_t qid) {
+    if (!s) return sm_fail_internal(SM_EINVAL, "stepper is NULL");
+    s->queries.erase(qid);
+    return SM_OK;
+}
+
+extern "C" sm_status sm_stepper_step(sm_stepper* s, const uint32_t* h_qids, uint32_t nq, uint32_t chunk,
+                                     int64_t* d_counts, sm_stream_t stream) {
+    if (!s || (nq && (!h_qids || !d_counts))) return sm_fail_internal(SM_EINVAL, "NULL argument");
+    if (chunk >= s->nchunks) return sm_fail_internal(SM_EINVAL, "chunk out of range");
+    Guard g(s->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const uint64_t off = (uint64_t)chunk * s->chunk;
+    const uint64_t avail = s->n - off;                          // bytes from the chunk start
+    const uint64_t nbytes = std::min<uint64_t>(avail, s->chunk + s->max_m - 1);
+    const uint64_t slimit = std::min<uint64_t>(avail, s->chunk);
+    std::vector<const PatDesc*> ds;
+    ds.reserve(nq);
+    for (uint32_t i = 0; i < nq; ++i) {
+        auto it = s->queries.find(h_qids[i]);
+        if (it == s->queries.end()) return sm_fail_internal(SM_EINVAL, "query not admitted");
+        if (it->second.zero || it->second.pat.m > nbytes) continue;   // no start in this chunk
+        ds.push_back(&it->second);
+    }
+    if (ds.empty()) return SM_OK;
+    Tables T;
+    add_text(T, off, nbytes, slimit, ds);
+    finish(T, (uint64_t)sm_ctx_num_sms(s->ctx) * s->geo.occ);
+    const Layout L = layout_of(T);
+    sm_stepper::Buf& b = s->buf[s->cur];
+    s->cur ^= 1;
+    if (b.used && cudaEventSynchronize(b.ev) != cudaSuccess) return sm_fail_internal(SM_ECUDA, "event wait");
+    if (b.cap < L.total) {
+        const size_t cap = std::max(L.total, 2 * b.cap);
+        if (b.h) cudaFreeHost(b.h);
+        if (b.d) cudaFree(b.d);
+        b.h = nullptr;
+        b.d = nullptr;
+        b.cap = 0;
+        if (cudaMallocHost(&b.h, cap) != cudaSuccess || cudaMalloc(&b.d, cap) != cudaSuccess) {
+            cudaGetLastError();
+            return sm_fail_internal(SM_ENOMEM, "stepper tables");
+        }
+        b.cap = cap;
+    }
+    pack(T, L, b.h);
+    cudaError_t e = cudaMemcpyAsync(b.d, b.h, L.total, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        BatchArgs a = args_for(s->ctx, s->d_text, T, L, b.d, s->geo);
+        a.d_counts = d_counts;
+        smk::batch_kernel<<<(uint32_t)T.cta_pbase.size(), smk::kThreads, s->geo.smem(T.nslots), st>>>(a);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(b.ev, st);
+    b.used = true;
+    return e == cudaSuccess ? SM_OK : sm_fail_internal(SM_ECUDA, cudaGetErrorString(e));
+}
+
+extern "C" void sm_stepper_destroy(sm_stepper* s) {
+    if (!s) return;
+    Guard g(s->device);
+    cudaDeviceSynchronize();
+    for (auto& b : s->buf) {
+        if (b.h) cudaFreeHost(b.h);
+        if (b.d) cudaFree(b.d);
+        if (b.ev) cudaEventDestroy(b.ev);
+    }
+    delete s;
 }

@@ -1,0 +1,257 @@
+"""Serving loop: count and report queries against one device-resident text.
+
+Continuous batching: the text stays in HBM, cut into chunks. Every step scans
+the next chunk for all active queries in one batched launch
+(``sm_stepper_step``), so queries in flight share each pass over the text.
+A query is admitted whenever a counter slot is free -- it joins at whatever
+chunk comes next -- and its count is complete after one step on every chunk.
+A report query then needs a position buffer of exactly count x 8 bytes; it is
+admitted when the report memory budget has room, and its positions are
+written by ``sm_report`` on a second stream while the next steps run.
+
+Every query's result is the same as when it runs alone (the tests check
+this against single calls and the CPU oracle).
+"""
+from __future__ import annotations
+
+import collections
+import ctypes as C
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import sm
+
+
+@dataclass
+class Query:
+    pattern: bytes
+    kind: str = "count"            # "count" or "report"
+    arrival: float = 0.0           # seconds on the server's clock
+    count: int | None = None
+    positions: object = None       # device tensor (int64) for reports
+    done: float | None = None
+    qid: int = -1
+
+    @property
+    def latency(self) -> float:
+        return (self.done or 0.0) - self.arrival
+
+
+def _bind_stepper():
+    lib = sm.load()
+    if getattr(lib, "_stepper_bound", False):
+        return lib
+    vp, u8p, u32p = C.c_void_p, C.POINTER(C.c_uint8), C.POINTER(C.c_uint32)
+    st = C.c_int
+    lib.sm_stepper_create.argtypes = [vp, vp, C.c_uint64, C.c_uint64, C.c_uint32, C.POINTER(C.c_uint64),
+                                      C.POINTER(vp)]
+    lib.sm_stepper_create.restype = st
+    lib.sm_stepper_chunks.argtypes = [vp]
+    lib.sm_stepper_chunks.restype = C.c_uint32
+    lib.sm_stepper_admit.argtypes = [vp, C.c_uint32, u8p, C.c_uint32]
+    lib.sm_stepper_admit.restype = st
+    lib.sm_stepper_step.argtypes = [vp, u32p, C.c_uint32, C.c_uint32, vp, vp]
+    lib.sm_stepper_step.restype = st
+    lib.sm_stepper_retire.argtypes = [vp, C.c_uint32]
+    lib.sm_stepper_retire.restype = st
+    lib.sm_stepper_destroy.argtypes = [vp]
+    lib.sm_stepper_destroy.restype = None
+    lib._stepper_bound = True
+    return lib
+
+
+class Server:
+    """Continuous-batching server over the resident uint8 CUDA tensor `text`."""
+
+    def __init__(self, text, chunk_bytes: int = 256 << 20, max_m: int = 2048, max_active: int = 1024,
+                 report_budget: int = 8 << 30):
+        import torch
+        self.torch = torch
+        self.text = text
+        self.dev = text.device
+        self.lib = _bind_stepper()
+        self.ctx = sm.sm_create(self.dev.index or 0)           # steps, on self.stream
+        self.rctx = sm.sm_create(self.dev.index or 0)          # reports, on self.rstream
+        self.stream = torch.cuda.Stream(device=self.dev)
+        self.rstream = torch.cuda.Stream(device=self.dev)
+        self.hist = sm.sm_histogram(self.ctx, text, stream=self.stream)
+        self.stream.synchronize()
+        self.hist = self.hist.cpu().numpy().view(np.uint64).copy()
+        self.max_m = max_m
+        chunk = max(sm.SM_TILE_STARTS, (chunk_bytes // sm.SM_TILE_STARTS) * sm.SM_TILE_STARTS)
+        h = C.c_void_p()
+        sm._check(self.lib.sm_stepper_create(self.ctx.handle, text.data_ptr(), text.numel(), chunk, max_m,
+                                              self.hist.ctypes.data_as(C.POINTER(C.c_uint64)), C.byref(h)))
+        self.stepper = h.value
+        self.nchunks = int(self.lib.sm_stepper_chunks(self.stepper))
+        self.max_active = max_active
+        self.counters = torch.zeros(max_active, dtype=torch.int64, device=self.dev)
+        self.host_counters = torch.zeros(max_active, dtype=torch.int64).pin_memory()
+        self.free_slots = list(range(max_active - 1, -1, -1))
+        self.pending: collections.deque[Query] = collections.deque()
+        self.active: dict[int, list] = {}         # slot -> [query, chunks left]
+        self.finishing: list = []                 # (event, [queries]) whose counts are final
+        self.report_wait: collections.deque[Query] = collections.deque()
+        self.reporting: list = []                 # (event, query, bytes)
+        self.report_budget = report_budget
+        self.report_reserved = 0
+        self.next_chunk = 0
+        self.done: list[Query] = []
+        self.steps = 0
+        self.t0 = time.perf_counter()
+
+    def __del__(self):
+        h, self.stepper = getattr(self, "stepper", None), None
+        if h:
+            self.lib.sm_stepper_destroy(h)
+
+    def now(self) -> float:
+        return time.perf_counter() - self.t0
+
+    def submit(self, q: Query):
+        if len(q.pattern) < 1 or len(q.pattern) > self.max_m:
+            raise ValueError("pattern length out of range")
+        self.pending.append(q)
+
+    @property
+    def busy(self) -> bool:
+        return bool(self.pending or self.active or self.finishing or self.report_wait or self.reporting)
+
+    # ------------------------------------------------------------ one step
+    def step(self):
+        torch = self.torch
+        # admission: a free counter slot per query
+        while self.pending and self.free_slots:
+            q = self.pending.popleft()
+            slot = self.free_slots.pop()
+            q.qid = slot
+            p = np.frombuffer(q.pattern, np.uint8)
+            sm._check(self.lib.sm_stepper_admit(self.stepper, slot, p.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                                p.size))
+            with torch.cuda.stream(self.stream):
+                self.counters[slot].zero_()
+            self.active[slot] = [q, self.nchunks]
+        if self.active:
+            slots = np.fromiter(self.active.keys(), dtype=np.uint32, count=len(self.active))
+            sm._check(self.lib.sm_stepper_step(self.stepper, slots.ctypes.data_as(C.POINTER(C.c_uint32)),
+                                               slots.size, self.next_chunk, self.counters.data_ptr(),
+                                               self.stream.cuda_stream))
+            finished = []
+            for slot in list(self.active):
+                ent = self.active[slot]
+                ent[1] -= 1
+                if ent[1] == 0:
+                    finished.append(ent[0])
+                    del self.active[slot]
+            if finished:
+                with torch.cuda.stream(self.stream):
+                    idx = torch.tensor([q.qid for q in finished], dtype=torch.int64, device=self.dev)
+                    vals = self.counters.index_select(0, idx)
+                    host = torch.empty(len(finished), dtype=torch.int64).pin_memory()
+                    host.copy_(vals, non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(self.stream)
+                self.finishing.append((ev, finished, host))
+            self.next_chunk = (self.next_chunk + 1) % self.nchunks
+            self.steps += 1
+        self._poll()
+
+    def _poll(self):
+        torch = self.torch
+        keep = []
+        for ev, qs, host in self.finishing:
+            if not ev.query():
+                keep.append((ev, qs, host))
+                continue
+            now = self.now()
+            for q, c in zip(qs, host.tolist()):
+                q.count = int(c)
+                self.lib.sm_stepper_retire(self.stepper, q.qid)
+                self.free_slots.append(q.qid)
+                if q.kind == "report":
+                    self.report_wait.append(q)
+                else:
+                    q.done = now
+                    self.done.append(q)
+        self.finishing = keep
+        # reports: admitted by the memory their position buffers need
+        while self.report_wait:
+            q = self.report_wait[0]
+            need = max(q.count, 1) * 8
+            if self.report_reserved and self.report_reserved + need > self.report_budget:
+                break
+            self.report_wait.popleft()
+            self.report_reserved += need
+            with torch.cuda.stream(self.rstream):
+                pos = torch.empty(max(q.count, 1), dtype=torch.int64, device=self.dev)
+                cnt = torch.empty(1, dtype=torch.int64, device=self.dev)
+            sm.sm_report(self.rctx, self.text, q.pattern, q.count, pi=sm.sm_order(q.pattern, self.hist),
+                         out_pos=pos, out_count=cnt, stream=self.rstream, hist=self.hist)
+            ev = torch.cuda.Event()
+            ev.record(self.rstream)
+            q.positions = pos[: q.count]
+            self.reporting.append((ev, q, need))
+        keep = []
+        for ev, q, need in self.reporting:
+            if ev.query():
+                q.done = self.now()
+                self.report_reserved -= need
+                self.done.append(q)
+            else:
+                keep.append((ev, q, need))
+        self.reporting = keep
+
+    # ------------------------------------------------------------ drivers
+    def run(self, queries: list[Query], time_scale: float = 1.0, max_steps: int | None = None) -> list[Query]:
+        """Submit queries at their arrival times (seconds x time_scale) and
+        step until every one is done."""
+        order = sorted(queries, key=lambda q: q.arrival)
+        i = 0
+        self.t0 = time.perf_counter()
+        for q in order:
+            q.arrival *= time_scale
+        while i < len(order) or self.busy:
+            now = self.now()
+            while i < len(order) and order[i].arrival <= now:
+                self.submit(order[i])
+                i += 1
+            if not self.busy and i < len(order):
+                time.sleep(max(0.0, min(order[i].arrival - now, 0.001)))
+                continue
+            self.step()
+            if max_steps is not None and self.steps >= max_steps:
+                break
+        self.torch.cuda.synchronize()
+        return order
+
+
+def one_at_a_time(text, queries: list[Query], hist=None) -> list[Query]:
+    """Baseline: each query alone, in arrival order, waiting for the previous."""
+    import torch
+    ctx = sm.sm_create(text.device.index or 0)
+    if hist is None:
+        hist = sm.sm_histogram(ctx, text).cpu().numpy().view(np.uint64).copy()
+    order = sorted(queries, key=lambda q: q.arrival)
+    t0 = time.perf_counter()
+    for q in order:
+        now = time.perf_counter() - t0
+        if q.arrival > now:
+            time.sleep(q.arrival - now)
+        pi = sm.sm_order(q.pattern, hist)
+        c = sm.sm_count(ctx, text, q.pattern, pi=pi, hist=hist)
+        q.count = int(c.item())
+        if q.kind == "report":
+            pos, _ = sm.sm_report(ctx, text, q.pattern, max(q.count, 1), pi=pi, hist=hist)
+            q.positions = pos[: q.count]
+            torch.cuda.synchronize()
+        q.done = time.perf_counter() - t0
+    return order
+
+
+def latency_stats(qs: list[Query]) -> dict:
+    lat = np.array([q.latency for q in qs]) * 1e3
+    span = max(q.done for q in qs) - min(q.arrival for q in qs)
+    return {"queries": len(qs), "p50_ms": round(float(np.percentile(lat, 50)), 3),
+            "p99_ms": round(float(np.percentile(lat, 99)), 3), "qps": round(len(qs) / span, 1)}

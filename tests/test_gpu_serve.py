@@ -1,0 +1,78 @@
+"""Serving: every query's result is the same alone and in the mix."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1612_01506_gb300 import sm, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    return t
+
+
+def make_text(n_half):
+    return np.concatenate([synth.uniform(n_half, 4, seed=0, stream=71), synth.markov95(n_half, seed=0, stream=72)])
+
+
+def make_queries(t, k, seed, report_frac=0.2, mmax=2048):
+    from paper_1612_01506_gb300.serve import Query
+    r = np.random.default_rng(seed)
+    qs = []
+    for i in range(k):
+        m = int(np.exp(r.uniform(np.log(2), np.log(mmax))))
+        if r.random() < 0.8:
+            s = int(r.integers(0, t.size - m + 1))
+            p = t[s:s + m].tobytes()
+        else:
+            p = bytes(r.choice(np.frombuffer(b"ACGT e", np.uint8), m))
+        qs.append(Query(pattern=p, kind="report" if r.random() < report_frac else "count", arrival=i * 0.0004))
+    return qs
+
+
+def test_serving_results_equal_alone(torch):
+    from paper_1612_01506_gb300.serve import Server
+    t = make_text(3 << 20)
+    text = torch.from_numpy(t).cuda()
+    server = Server(text, chunk_bytes=1 << 20, max_m=2048, max_active=16, report_budget=1 << 20)
+    assert server.nchunks == 6
+    qs = make_queries(t, 60, seed=1)
+    done = server.run(qs)
+    assert len(server.done) == len(qs)
+    ctx = sm.sm_create(0)
+    for q in done:
+        alone = int(sm.sm_count(ctx, text, q.pattern).item())
+        assert q.count == alone == oracle.count_threads(q.pattern, t), q.pattern[:20]
+        if q.kind == "report":
+            pos, c = oracle.report_threads(q.pattern, t, q.count)
+            assert np.array_equal(q.positions.cpu().numpy().view(np.uint64), pos)
+    # the mix really overlapped: more queries than slots, several steps
+    assert server.steps > server.nchunks
+
+
+def test_stepper_joins_at_any_chunk(torch):
+    # queries joining at different chunks and wrapping around give full counts
+    from paper_1612_01506_gb300.serve import Server
+    t = make_text(1 << 20)
+    text = torch.from_numpy(t).cuda()
+    server = Server(text, chunk_bytes=1 << 18, max_m=512, max_active=8)
+    qs = make_queries(t, 24, seed=2, report_frac=0.0, mmax=512)
+    for k, q in enumerate(qs):
+        q.arrival = 0.0
+    # submit in waves between steps so that joins happen at many chunks
+    pending = list(qs)
+    while pending or server.busy:
+        for _ in range(3):
+            if pending:
+                server.submit(pending.pop())
+        server.step()
+    torch.cuda.synchronize()
+    for q in qs:
+        assert q.count == oracle.count_threads(q.pattern, t)

@@ -63,6 +63,11 @@ def parse():
     ap.add_argument("--batch", action="store_true",
                     help="also measure batched counting (256 MiB Markov text, 4096 patterns)")
     ap.add_argument("--batch-only", action="store_true", help="measure only the batched counting")
+    ap.add_argument("--serve", action="store_true",
+                    help="also measure the serving loop (4 GiB resident text, Poisson arrivals)")
+    ap.add_argument("--serve-only", action="store_true", help="measure only the serving loop")
+    ap.add_argument("--serve-rates", default="200,1000,4000")
+    ap.add_argument("--serve-seconds", type=float, default=1.0)
     return ap.parse_args()
 
 
@@ -413,6 +418,55 @@ def run_batch(args, local, steps=3, warmup=2):
             "counts_agree": agree}
 
 
+# ---------------------------------------------------------------- serving
+
+def run_serve(args, local):
+    """Serving loop on a 4 GiB resident text (2 GiB uniform ACGT + 2 GiB
+    Markov-95). Poisson arrivals at each rate for --serve-seconds; m
+    log-uniform in [2, 2048]; 80% counts, 20% reports; 80% of patterns copied
+    from the text. p50/p99 latency and queries/s of the continuous-batching
+    server and of one query at a time on the same arrival trace."""
+    import torch
+    from paper_1612_01506_gb300 import synth
+    from paper_1612_01506_gb300.serve import Query, Server, latency_stats, one_at_a_time
+    half = 2 << 30
+    t = np.empty(2 * half, dtype=np.uint8)
+    synth.uniform(half, 4, seed=0, stream=synth.stream_id("serve", 4), out=t[:half])
+    synth.markov95(half, seed=0, stream=synth.stream_id("serve", "markov95"), out=t[half:])
+    text = torch.from_numpy(t).to(torch.device("cuda", local))
+    out = {"workload": "serving: 4 GiB resident text (2 GiB ACGT + 2 GiB Markov-95), Poisson arrivals, "
+                       "m log-uniform [2,2048], 80/20 count/report", "chunk_bytes": 256 << 20, "rates": {}}
+    server = Server(text, chunk_bytes=256 << 20, max_m=2048, max_active=4096, report_budget=24 << 30)
+    server.warm_up([t[1000:1000 + m].tobytes() for m in (3, 40, 700, 2048)])
+    one_at_a_time(text, [Query(pattern=t[5:12].tobytes(), kind="report"), Query(pattern=t[9:30].tobytes())],
+                  hist=server.hist)
+    for rate in [float(x) for x in args.serve_rates.split(",") if x]:
+        r = np.random.default_rng(int(rate))
+        k = max(1, int(rate * args.serve_seconds))
+        arr = np.cumsum(r.exponential(1.0 / rate, k))
+        def trace():
+            qs = []
+            rr = np.random.default_rng(int(rate) + 1)
+            for i in range(k):
+                m = int(np.exp(rr.uniform(np.log(2), np.log(2048))))
+                if rr.random() < 0.8:
+                    s = int(rr.integers(0, t.size - m + 1))
+                    p = t[s:s + m].tobytes()
+                else:
+                    p = bytes(rr.choice(np.frombuffer(b"ACGT etaoin", np.uint8), m))
+                qs.append(Query(pattern=p, kind="report" if rr.random() < 0.2 else "count", arrival=float(arr[i])))
+            return qs
+        qs = trace()
+        server.done = []
+        t0 = time.perf_counter()
+        server.run(qs)
+        wall = time.perf_counter() - t0
+        srv = latency_stats(qs)
+        base = latency_stats(one_at_a_time(text, trace(), hist=server.hist))
+        out["rates"][str(int(rate))] = {"server": srv, "one_at_a_time": base, "server_wall_s": round(wall, 2)}
+    return out
+
+
 # ---------------------------------------------------------------- CPU oracle
 
 def run_cpu_baseline(args, budget_s: float):
@@ -483,6 +537,10 @@ def main():
         if rank == 0:
             print(json.dumps({"batch": run_batch(args, local)}), flush=True)
         return
+    if args.serve_only:
+        if rank == 0:
+            print(json.dumps({"serving": run_serve(args, local)}), flush=True)
+        return
     res = run_gpu(args, world, rank, local)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -496,6 +554,8 @@ def main():
                 "e2e": res["e2e"], "gpu_launches": res["launches"], "clocks": res["clocks"]}
         if args.batch and world == 1:
             line["batch"] = run_batch(args, local)
+        if args.serve and world == 1:
+            line["serving"] = run_serve(args, local)
         print(json.dumps(line), flush=True)
         if args.json_detail:
             with open(args.json_detail, "w") as f:

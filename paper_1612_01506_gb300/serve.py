@@ -66,7 +66,7 @@ class Server:
     """Continuous-batching server over the resident uint8 CUDA tensor `text`."""
 
     def __init__(self, text, chunk_bytes: int = 256 << 20, max_m: int = 2048, max_active: int = 1024,
-                 report_budget: int = 8 << 30):
+                 report_budget: int = 8 << 30, burst_below: int = 4):
         import torch
         self.torch = torch
         self.text = text
@@ -87,6 +87,10 @@ class Server:
         self.stepper = h.value
         self.nchunks = int(self.lib.sm_stepper_chunks(self.stepper))
         self.max_active = max_active
+        # with at most this many queries in flight and none waiting, a step
+        # scans every chunk back to back; otherwise one chunk per step, so that
+        # arrivals join at the next chunk
+        self.burst_below = burst_below
         self.counters = torch.zeros(max_active, dtype=torch.int64, device=self.dev)
         self.host_counters = torch.zeros(max_active, dtype=torch.int64).pin_memory()
         self.free_slots = list(range(max_active - 1, -1, -1))
@@ -133,30 +137,48 @@ class Server:
             with torch.cuda.stream(self.stream):
                 self.counters[slot].zero_()
             self.active[slot] = [q, self.nchunks]
-        if self.active:
-            slots = np.fromiter(self.active.keys(), dtype=np.uint32, count=len(self.active))
-            sm._check(self.lib.sm_stepper_step(self.stepper, slots.ctypes.data_as(C.POINTER(C.c_uint32)),
-                                               slots.size, self.next_chunk, self.counters.data_ptr(),
-                                               self.stream.cuda_stream))
-            finished = []
-            for slot in list(self.active):
-                ent = self.active[slot]
-                ent[1] -= 1
-                if ent[1] == 0:
-                    finished.append(ent[0])
-                    del self.active[slot]
-            if finished:
-                with torch.cuda.stream(self.stream):
-                    idx = torch.tensor([q.qid for q in finished], dtype=torch.int64, device=self.dev)
-                    vals = self.counters.index_select(0, idx)
-                    host = torch.empty(len(finished), dtype=torch.int64).pin_memory()
-                    host.copy_(vals, non_blocking=True)
-                ev = torch.cuda.Event()
-                ev.record(self.stream)
-                self.finishing.append((ev, finished, host))
-            self.next_chunk = (self.next_chunk + 1) % self.nchunks
-            self.steps += 1
+        burst = self.nchunks if len(self.active) <= self.burst_below and not self.pending else 1
+        for _ in range(burst):
+            if not self.active:
+                break
+            self._step_chunk()
         self._poll()
+
+    def _step_chunk(self):
+        torch = self.torch
+        slots = np.fromiter(self.active.keys(), dtype=np.uint32, count=len(self.active))
+        sm._check(self.lib.sm_stepper_step(self.stepper, slots.ctypes.data_as(C.POINTER(C.c_uint32)),
+                                           slots.size, self.next_chunk, self.counters.data_ptr(),
+                                           self.stream.cuda_stream))
+        finished = []
+        for slot in list(self.active):
+            ent = self.active[slot]
+            ent[1] -= 1
+            if ent[1] == 0:
+                finished.append(ent[0])
+                del self.active[slot]
+        if finished:
+            with torch.cuda.stream(self.stream):
+                idx = torch.tensor([q.qid for q in finished], dtype=torch.int64).pin_memory().to(
+                    self.dev, non_blocking=True)
+                vals = self.counters.index_select(0, idx)
+                host = torch.empty(len(finished), dtype=torch.int64).pin_memory()
+                host.copy_(vals, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(self.stream)
+            self.finishing.append((ev, finished, host))
+        self.next_chunk = (self.next_chunk + 1) % self.nchunks
+        self.steps += 1
+
+    def warm_up(self, patterns: list[bytes]):
+        """Run a few queries through every path once (loads kernels, sizes buffers)."""
+        qs = [Query(pattern=p, kind=("report" if i % 2 else "count")) for i, p in enumerate(patterns)]
+        for q in qs:
+            self.submit(q)
+        while self.busy:
+            self.step()
+        self.torch.cuda.synchronize()
+        self.done = []
 
     def _poll(self):
         torch = self.torch

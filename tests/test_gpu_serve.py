@@ -41,7 +41,7 @@ def test_serving_results_equal_alone(torch):
     from paper_1612_01506_gb300.serve import Server
     t = make_text(3 << 20)
     text = torch.from_numpy(t).cuda()
-    server = Server(text, chunk_bytes=1 << 20, max_m=2048, max_active=16, report_budget=1 << 20)
+    server = Server(text, chunk_bytes=1 << 20, max_m=2048, max_active=16, report_budget=1 << 20, burst_below=4)
     assert server.nchunks == 6
     qs = make_queries(t, 60, seed=1)
     done = server.run(qs)
@@ -62,7 +62,7 @@ def test_stepper_joins_at_any_chunk(torch):
     from paper_1612_01506_gb300.serve import Server
     t = make_text(1 << 20)
     text = torch.from_numpy(t).cuda()
-    server = Server(text, chunk_bytes=1 << 18, max_m=512, max_active=8)
+    server = Server(text, chunk_bytes=1 << 18, max_m=512, max_active=8, burst_below=0)   # one chunk per step
     qs = make_queries(t, 24, seed=2, report_frac=0.0, mmax=512)
     for k, q in enumerate(qs):
         q.arrival = 0.0

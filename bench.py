@@ -513,7 +513,7 @@ def run_cpu_baseline(args, budget_s: float):
             searches += 1
         rep += 1
     return {"value": round(scanned / spent / 1e9, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
-            "sample": f"{searches} counts over 64 MiB prefixes of the sweep texts "
+            "sample": f"{searches} counts over {sample_n >> 20} MiB prefixes of the sweep texts "
                       f"(sigma {args.kinds}; m {args.ms}), {spent:.1f} s"}
 
 

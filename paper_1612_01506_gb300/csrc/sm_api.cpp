@@ -17,6 +17,7 @@
 #include <cstring>
 #include <numeric>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 struct sm_ctx {
@@ -26,15 +27,17 @@ struct sm_ctx {
     uint32_t* d_status = nullptr;
     uint32_t* h_status = nullptr;     // pinned mirror for sm_sync
     uint32_t* d_ticket = nullptr;
+    unsigned long long* d_tiles = nullptr;   // tile counter of the counting modes
     uint64_t* d_partials = nullptr;
     size_t partials_cap = 0;          // entries
     uint32_t* d_warp_counts = nullptr;
     size_t warp_counts_cap = 0;       // entries
     uint32_t stages = 4;
+    bool stages_fixed = false;        // set by SM_KNOB_STAGES; otherwise fewer stages may raise occupancy
     uint32_t grid_override = 0;
     uint64_t spin_ns = 1000000000ull;
     uint32_t test_skip_copy = 0;
-    int occ_cache[3][2][2] = {};      // [mode][seven][large m] CTAs per SM at default smem
+    std::unordered_map<uint64_t, int> occ;   // (mode, seven, large m, smem) -> resident CTAs per SM
 };
 
 namespace {
@@ -173,6 +176,16 @@ struct Grid {
     size_t smem = 0;
 };
 
+int occupancy(sm_ctx* c, int mode, bool seven, uint32_t m, size_t smem) {
+    const uint64_t key = ((uint64_t)smem << 8) | ((uint64_t)mode << 2) | (seven ? 2u : 0u) |
+                         (m > (uint32_t)smk::kSmallM ? 1u : 0u);
+    auto it = c->occ.find(key);
+    if (it != c->occ.end()) return it->second;
+    const int o = smk::scan_occupancy(mode, seven, m, smem);
+    c->occ.emplace(key, o);
+    return o;
+}
+
 sm_status plan_grid(sm_ctx* c, int mode, bool seven, uint32_t m, uint64_t nstarts, Grid* g) {
     g->ntiles = (nstarts + smk::kTile - 1) / smk::kTile;
     g->stage_bytes = smk::stage_bytes_for(m);
@@ -180,12 +193,19 @@ sm_status plan_grid(sm_ctx* c, int mode, bool seven, uint32_t m, uint64_t nstart
     while (g->stages > 2 && smk::scan_smem_bytes(g->stage_bytes, g->stages) > c->max_smem) --g->stages;
     g->smem = smk::scan_smem_bytes(g->stage_bytes, g->stages);
     if (g->smem > c->max_smem) return fail(SM_ENOTSUP, "pattern too long for shared memory");
-    uint64_t want = c->grid_override;
-    if (!want) {
-        int occ = smk::scan_occupancy(mode, seven, m, g->smem);
-        if (occ <= 0) return fail(SM_ECUDA, "scan kernel cannot be resident (smem %zu)", g->smem);
-        want = (uint64_t)c->num_sms * (uint64_t)occ;
+    int occ = occupancy(c, mode, seven, m, g->smem);
+    if (occ <= 0) return fail(SM_ECUDA, "scan kernel cannot be resident (smem %zu)", g->smem);
+    // one stage fewer is worth it when it lets another CTA reside on each SM
+    while (!c->stages_fixed && g->stages > 2) {
+        const size_t sm2 = smk::scan_smem_bytes(g->stage_bytes, g->stages - 1);
+        const int o2 = occupancy(c, mode, seven, m, sm2);
+        if (o2 <= occ) break;
+        --g->stages;
+        g->smem = sm2;
+        occ = o2;
     }
+    uint64_t want = c->grid_override;
+    if (!want) want = (uint64_t)c->num_sms * (uint64_t)occ;
     want = std::max<uint64_t>(1, std::min<uint64_t>(want, g->ntiles));
     g->per_cta = (g->ntiles + want - 1) / want;
     g->grid = (uint32_t)((g->ntiles + g->per_cta - 1) / g->per_cta);
@@ -207,6 +227,7 @@ smk::ScanArgs scan_args(sm_ctx* c, const uint8_t* d_text, uint64_t n, uint32_t m
     a.status = c->d_status;
     a.partials = c->d_partials;
     a.ticket = c->d_ticket;
+    a.tile_next = c->d_tiles;
     a.d_count = d_count;
     a.warp_counts = c->d_warp_counts;
     a.one = 1;
@@ -271,6 +292,7 @@ sm_status sm_create(sm_ctx** out, int device) {
         return cuda_fail(e, "context allocation");
     }
     c->d_ticket = c->d_status + 8;   // second 32-byte sector of the same allocation
+    c->d_tiles = reinterpret_cast<unsigned long long*>(c->d_status + 12);
     if ((e = smk::scan_prepare(c->max_smem)) != cudaSuccess) {
         sm_destroy(c);
         return cuda_fail(e, "cudaFuncSetAttribute");
@@ -301,6 +323,7 @@ sm_status sm_set_knob(sm_ctx* c, sm_knob knob, int64_t value) {
         case SM_KNOB_STAGES:
             if (value < 2 || value > smk::kMaxStages) return fail(SM_EINVAL, "stages must be 2..%d", smk::kMaxStages);
             c->stages = (uint32_t)value;
+            c->stages_fixed = true;
             return SM_OK;
         case SM_KNOB_GRID:
             if (value < 0 || value > (1 << 24)) return fail(SM_EINVAL, "grid out of range");
@@ -414,7 +437,10 @@ static sm_status search(sm_ctx* c, const uint8_t* d_text, uint64_t n, const uint
         if (st != SM_OK) return st;
     }
     smk::ScanArgs a = scan_args(c, d_text, n, m, pl, gr, d_count);
-    cudaError_t e = smk::launch_scan(mode1, pl.seven, gr.grid, gr.smem, s, a, pl.qc.data());
+    cudaError_t e;
+    if (report && (e = cudaMemsetAsync(c->d_partials, 0, sizeof(uint64_t) * gr.grid, s)) != cudaSuccess)
+        return cuda_fail(e, "clearing the range counts");
+    e = smk::launch_scan(mode1, pl.seven, gr.grid, gr.smem, s, a, pl.qc.data());
     if (e != cudaSuccess) return cuda_fail(e, "scan launch");
     if (report) {
         a.d_pos = d_pos;

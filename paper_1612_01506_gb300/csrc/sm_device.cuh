@@ -141,44 +141,41 @@ __device__ __forceinline__ TileCopy stage_ragged(uint8_t* buf, const uint8_t* te
 
 // ------------------------------------------------------------ compare core
 
-// found &= [byte of w == byte of P], flags in the high bit of each byte.
-// General bytes: exact zero-byte test of x = w ^ P: the high bit of
-// ((x & 0x7F..) + 0x7F..) | x is set iff the byte is nonzero.
-// SEVEN: every byte of w and P is below 0x80, so x + 0x7F.. cannot carry
-// between bytes and its high bit alone marks a nonzero byte.
-// With SMK_MADD_ADD the add is a multiply-add by `one` (== 1) so that it
-// issues on the multiply-add pipe instead of the integer pipe.
+// A byte of x = w ^ (c..c) is zero iff that byte of w equals c. Several
+// compares fold into one zero-byte test: a byte of the OR of their XORs is
+// zero iff every one of them matched, so the found flags after the test are
+// the AND of the flags of the separate compares.
+//
+// keep_zero(f, y): f & [byte of y == 0], flags in the high bit of each byte.
+// General bytes: the high bit of ((y & 0x7F..) + 0x7F..) | y is set iff the
+// byte is nonzero. SEVEN: every byte of y is below 0x80 (text and pattern
+// are 7-bit), so y + 0x7F.. cannot carry between bytes and its high bit
+// alone marks a nonzero byte. With SMK_MADD_ADD the add is a multiply-add by
+// `one` (== 1) so that it issues on the multiply-add pipe instead of the
+// integer pipe.
 #ifndef SMK_MADD_ADD
 #define SMK_MADD_ADD 1
 #endif
 template <bool SEVEN>
-__device__ __forceinline__ uint32_t keep_equal(uint32_t f, uint32_t w, uint32_t P, uint32_t one) {
-    const uint32_t x = w ^ P;
+__device__ __forceinline__ uint32_t keep_zero(uint32_t f, uint32_t y, uint32_t one) {
 #if SMK_MADD_ADD
-    if (SEVEN) return f & ~(x * one + 0x7F7F7F7Fu);
-    return f & ~(((x & 0x7F7F7F7Fu) * one + 0x7F7F7F7Fu) | x);
+    if (SEVEN) return f & ~(y * one + 0x7F7F7F7Fu);
+    return f & ~(((y & 0x7F7F7F7Fu) * one + 0x7F7F7F7Fu) | y);
 #else
     (void)one;
-    if (SEVEN) return f & ~(x + 0x7F7F7F7Fu);
-    return f & ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x);
+    if (SEVEN) return f & ~(y + 0x7F7F7F7Fu);
+    return f & ~(((y & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | y);
 #endif
 }
 
-template <bool SEVEN, int D>
-__device__ __forceinline__ void cmp_chunk(const uint4& a, const uint4& b, uint32_t sh, uint32_t P, uint32_t one,
-                                          uint32_t (&f)[4]) {
-    const uint32_t X[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) f[i] = keep_equal<SEVEN>(f[i], __funnelshift_r(X[D + i], X[D + i + 1], sh), P, one);
-}
-
-// One SIMDcompare for the lane's NC 16-start chunks (chunk c at index
-// c0 + 32c). v = (e << 8) | symbol with e = text misalignment + pattern
-// position; the caller guarantees D == (e >> 2) & 3, so the word selection is
-// static. All 2*NC loads issue before the compares.
-template <bool SEVEN, int D, int NC>
-__device__ __forceinline__ void compare_chunks(const uint4* __restrict__ b4, uint32_t c0, uint32_t v, uint32_t one,
-                                               uint32_t (&f)[NC][4]) {
+// One compare, accumulated for the lane's NC 16-start chunks (chunk c at
+// index c0 + 32c): y |= window ^ (c..c), where the window of a start is
+// text bytes s+q .. s+q+3. v = (e << 8) | symbol with e = text misalignment
+// + pattern position q; the caller guarantees D == (e >> 2) & 3, so the
+// word selection is static. All 2*NC loads issue before the XORs.
+template <int D, int NC>
+__device__ __forceinline__ void acc_chunks(const uint4* __restrict__ b4, uint32_t c0, uint32_t v,
+                                           uint32_t (&y)[NC][4]) {
     const uint32_t e = v >> 8;
     const uint32_t P = (v & 0xFFu) * 0x01010101u;
     const uint32_t ci = c0 + (e >> 4);
@@ -190,19 +187,26 @@ __device__ __forceinline__ void compare_chunks(const uint4* __restrict__ b4, uin
         b[c] = b4[ci + 32 * c + 1];
     }
 #pragma unroll
-    for (int c = 0; c < NC; ++c) cmp_chunk<SEVEN, D>(a[c], b[c], sh, P, one, f[c]);
+    for (int c = 0; c < NC; ++c) {
+        const uint32_t X[8] = {a[c].x, a[c].y, a[c].z, a[c].w, b[c].x, b[c].y, b[c].z, b[c].w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) y[c][i] |= __funnelshift_r(X[D + i], X[D + i + 1], sh) ^ P;
+    }
 }
 
-// One SIMDcompare for a single 4-start word whose first start is at word
-// index `wbase` of the stage buffer.
-template <bool SEVEN>
-__device__ __forceinline__ uint32_t compare_word(const uint32_t* __restrict__ b32, uint32_t wbase, uint32_t v,
-                                                 uint32_t one, uint32_t f) {
+// One compare, accumulated for a single 16-start chunk whose first start is
+// at word index W of the stage buffer (any alignment class).
+__device__ __forceinline__ void acc_window(const uint32_t* __restrict__ b32, uint32_t W, uint32_t v,
+                                           uint32_t (&y)[4]) {
     const uint32_t e = v >> 8;
     const uint32_t P = (v & 0xFFu) * 0x01010101u;
-    const uint32_t W = wbase + (e >> 2);
-    const uint32_t w = __funnelshift_r(b32[W], b32[W + 1], (e & 3u) << 3);
-    return keep_equal<SEVEN>(f, w, P, one);
+    const uint32_t w0 = W + (e >> 2);
+    const uint32_t sh = (e & 3u) << 3;
+    uint32_t t[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) t[i] = b32[w0 + i];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) y[i] |= __funnelshift_r(t[i], t[i + 1], sh) ^ P;
 }
 
 // Sum of the found flags (bit 7 of each byte) of NC x 4 words: eight words
@@ -269,32 +273,41 @@ struct GlobalQC {
 };
 
 // One consumer warp's 2048 starts of a staged tile against one pattern:
-// Algorithms 2-4 (dense peeled compares, compaction of surviving words,
-// per-word early exit). Starts at or beyond nstarts (relative to the tile's
-// first start s0) are out of range. Returns this lane's number of
-// matches; with WRITE, also
-// writes the positions in ascending order from rank `out` (first `cap` only).
-// DIRECT: a count may skip the compaction when r >= m.
+// Algorithms 2-4. Starts at or beyond nstarts (relative to the tile's first
+// start s0) are out of range. Returns this lane's number of matches; with
+// WRITE, also writes the positions in ascending order from rank `out`
+// (first `cap` only). DIRECT: a count may skip the compaction when r >= m.
+//
+// Dense phase: the r peeled compares (arriving grouped by word alignment in
+// nd0..nd3) for all 2048 starts, folded into one zero-byte test.
+// Sparse phase: the 16-start chunks with a surviving start are compacted, in
+// position order, into the warp's queue q (at most 128 entries: the found
+// words, the chunk index in the low bits of the first); each lane then takes
+// one chunk and continues with compares r .. m-1, two per zero-byte test,
+// leaving as soon as the chunk's found flags are all zero - the early exit
+// of Algorithm 2, taken per 16-start chunk.
 template <bool SEVEN, bool WRITE, bool DIRECT, class QC>
 __device__ __forceinline__ uint32_t warp_tile(const uint4* __restrict__ b4, const uint32_t* __restrict__ b32,
                                               uint32_t c0, uint32_t wq, uint32_t warp, uint32_t lane, QC qc,
                                               uint32_t m, uint32_t r, uint32_t nd0, uint32_t nd1, uint32_t nd2,
-                                              uint32_t nd3, uint32_t one, uint64_t nstarts, uint64_t s0, uint2* q,
+                                              uint32_t nd3, uint32_t one, uint64_t nstarts, uint64_t s0, uint4* q,
                                               uint64_t out, uint64_t* __restrict__ d_pos, uint64_t cap) {
-    // dense phase: r compares for all starts of the warp; the peeled
-    // compares arrive grouped by word alignment (A.nd)
     uint32_t f[kChunks][4];
 #pragma unroll
     for (int c = 0; c < kChunks; ++c)
 #pragma unroll
-        for (int i = 0; i < 4; ++i) f[c][i] = 0x80808080u;
+        for (int i = 0; i < 4; ++i) f[c][i] = 0u;
     {
         uint32_t j = 0;
-        for (uint32_t k = 0; k < nd0; ++k, ++j) compare_chunks<SEVEN, 0>(b4, c0, qc(j), one, f);
-        for (uint32_t k = 0; k < nd1; ++k, ++j) compare_chunks<SEVEN, 1>(b4, c0, qc(j), one, f);
-        for (uint32_t k = 0; k < nd2; ++k, ++j) compare_chunks<SEVEN, 2>(b4, c0, qc(j), one, f);
-        for (uint32_t k = 0; k < nd3; ++k, ++j) compare_chunks<SEVEN, 3>(b4, c0, qc(j), one, f);
+        for (uint32_t k = 0; k < nd0; ++k, ++j) acc_chunks<0>(b4, c0, qc(j), f);
+        for (uint32_t k = 0; k < nd1; ++k, ++j) acc_chunks<1>(b4, c0, qc(j), f);
+        for (uint32_t k = 0; k < nd2; ++k, ++j) acc_chunks<2>(b4, c0, qc(j), f);
+        for (uint32_t k = 0; k < nd3; ++k, ++j) acc_chunks<3>(b4, c0, qc(j), f);
     }
+#pragma unroll
+    for (int c = 0; c < kChunks; ++c)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) f[c][i] = keep_zero<SEVEN>(0x80808080u, f[c][i], one);
 
     if (s0 + kTile > nstarts) {   // last tile: clear starts beyond n - m
         const int64_t lim = (int64_t)(nstarts - s0) - (int64_t)(warp * kWarpStarts + lane * 16u);
@@ -304,116 +317,69 @@ __device__ __forceinline__ uint32_t warp_tile(const uint4* __restrict__ b4, cons
             for (int i = 0; i < 4; ++i) f[c][i] &= valid_mask(lim - (512 * c + 4 * i));
     }
 
-    uint32_t any = 0;
+    if (DIRECT && r >= m) return count_flags<kChunks>(f);
+
+    // byte c: 1 if chunk c of this lane has a surviving start
+    uint32_t alive = 0;
 #pragma unroll
-    for (int c = 0; c < kChunks; ++c) any |= (f[c][0] | f[c][1]) | (f[c][2] | f[c][3]);
+    for (int c = 0; c < kChunks; ++c)
+        alive |= (uint32_t)(((f[c][0] | f[c][1]) | (f[c][2] | f[c][3])) != 0u) << (8 * c);
+    if (!__any_sync(kFull, alive != 0u)) return 0;
+
+    // queue in position order: chunk 0 of all lanes, then chunk 1, ...
+    const uint32_t incl = warp_incl_scan(alive, lane);
+    const uint32_t tot = __shfl_sync(kFull, incl, 31);
+    uint32_t qn = 0;
+#pragma unroll
+    for (int c = 0; c < kChunks; ++c) {
+        if ((alive >> (8 * c)) & 1u)
+            q[qn + ((incl >> (8 * c)) & 0xFFu) - 1u] =
+                make_uint4(f[c][0] | (32u * c + lane), f[c][1], f[c][2], f[c][3]);
+        qn += (tot >> (8 * c)) & 0xFFu;
+    }
+    __syncwarp();
 
     uint32_t tile_count = 0;   // this lane's share of the warp's matches in the tile
-    if (DIRECT && r >= m) {
-        tile_count = count_flags<kChunks>(f);
-    } else if (__any_sync(kFull, any != 0u)) {
-        // compact surviving words in position order: chunk 0 of all
-        // lanes, then chunk 1, ... (4 bits per chunk, counts in bytes)
-        uint32_t a[kChunks], packed = 0;
-#pragma unroll
-        for (int c = 0; c < kChunks; ++c) {
-            a[c] = 0;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) a[c] |= (f[c][i] != 0u) << i;
-            packed |= (uint32_t)__popc(a[c]) << (8 * c);
+    for (uint32_t qb = 0; qb < qn; qb += 32) {
+        const uint32_t e = qb + lane;
+        uint32_t g[4] = {0u, 0u, 0u, 0u}, k = 0;
+        if (e < qn) {
+            const uint4 x = q[e];
+            k = x.x & 0x7Fu;
+            g[0] = x.x & ~0x7Fu;
+            g[1] = x.y;
+            g[2] = x.z;
+            g[3] = x.w;
         }
-        const uint32_t incl = warp_incl_scan(packed, lane);
-        const uint32_t tot = __shfl_sync(kFull, incl, 31);
-        const uint32_t qn = (tot & 0xFFu) + ((tot >> 8) & 0xFFu) + ((tot >> 16) & 0xFFu) + (tot >> 24);
-
-        if (qn <= kQueueCap) {
-            uint32_t base = 0;
+        const uint32_t W = wq + 4u * k;   // word index of the chunk's first start
+        for (uint32_t j = r; j < m && ((g[0] | g[1]) | (g[2] | g[3])); j += 2) {
+            uint32_t y[4] = {0u, 0u, 0u, 0u};
+            acc_window(b32, W, qc(j), y);
+            acc_window(b32, W, qc(min(j + 1, m - 1)), y);   // an odd tail repeats compare j
 #pragma unroll
-            for (int c = 0; c < kChunks; ++c) {
-                uint32_t p = base + ((incl >> (8 * c)) & 0xFFu) - ((packed >> (8 * c)) & 0xFFu);
+            for (int i = 0; i < 4; ++i) g[i] = keep_zero<SEVEN>(g[i], y[i], one);
+        }
+        const uint32_t n = (__popc(g[0]) + __popc(g[1])) + (__popc(g[2]) + __popc(g[3]));
+        if (WRITE) {
+            const uint32_t inc = warp_incl_scan(n, lane);
+            uint64_t rk = out + inc - n;
+            const uint64_t pos0 = s0 + warp * kWarpStarts + 16u * k;
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    if (a[c] & (1u << i)) q[p++] = make_uint2(128u * c + lane * 4u + i, f[c][i]);
-                base += (tot >> (8 * c)) & 0xFFu;
-            }
-            __syncwarp();
-            // sparse phase: each lane continues one word with its own early exit
-            for (uint32_t qb = 0; qb < qn; qb += 32) {
-                const uint32_t e = qb + lane;
-                uint32_t wi = 0, fw = 0;
-                if (e < qn) {
-                    const uint2 x = q[e];
-                    wi = x.x;
-                    fw = x.y;
-                }
-                for (uint32_t j = r; j < m && fw; ++j) fw = compare_word<SEVEN>(b32, wq + wi, qc(j), one, fw);
-                const uint32_t k = __popc(fw);
-                if (WRITE) {
-                    const uint32_t inc = warp_incl_scan(k, lane);
-                    uint64_t rk = out + inc - k;
-                    const uint64_t pos0 = s0 + warp * kWarpStarts + 4u * wi;
-                    while (fw) {
-                        const uint32_t b = (uint32_t)(__ffs(fw) - 1) >> 3;
-                        if (rk < cap) d_pos[rk] = pos0 + b;
-                        ++rk;
-                        fw &= fw - 1;
-                    }
-                    out += __shfl_sync(kFull, inc, 31);
-                } else {
-                    tile_count += k;
+            for (int i = 0; i < 4; ++i) {
+                uint32_t fw = g[i];
+                while (fw) {
+                    const uint32_t b = (uint32_t)(__ffs(fw) - 1) >> 3;
+                    if (rk < cap) d_pos[rk] = pos0 + 4u * i + b;
+                    ++rk;
+                    fw &= fw - 1;
                 }
             }
-            __syncwarp();   // the queue is reused by the next tile
+            out += __shfl_sync(kFull, inc, 31);
         } else {
-            // more survivors than the queue holds: continue the remaining
-            // compares for all of the warp's starts, leaving when all are dead
-            for (uint32_t j = r; j < m; ++j) {
-                uint32_t an = 0;
-#pragma unroll
-                for (int c = 0; c < kChunks; ++c) an |= (f[c][0] | f[c][1]) | (f[c][2] | f[c][3]);
-                if (!__any_sync(kFull, an != 0u)) break;
-                const uint32_t v = qc(j);
-                switch ((v >> 10) & 3u) {
-                    case 0: compare_chunks<SEVEN, 0>(b4, c0, v, one, f); break;
-                    case 1: compare_chunks<SEVEN, 1>(b4, c0, v, one, f); break;
-                    case 2: compare_chunks<SEVEN, 2>(b4, c0, v, one, f); break;
-                    default: compare_chunks<SEVEN, 3>(b4, c0, v, one, f); break;
-                }
-            }
-            if (WRITE) {
-                // positions in order: chunk c of all lanes, words, bytes
-                uint32_t kc[kChunks];
-#pragma unroll
-                for (int c = 0; c < kChunks; ++c)
-                    kc[c] = __popc(f[c][0]) + __popc(f[c][1]) + __popc(f[c][2]) + __popc(f[c][3]);
-                const uint32_t i01 = warp_incl_scan(kc[0] | (kc[1] << 16), lane);
-                const uint32_t i23 = warp_incl_scan(kc[2] | (kc[3] << 16), lane);
-                const uint32_t t01 = __shfl_sync(kFull, i01, 31), t23 = __shfl_sync(kFull, i23, 31);
-                const uint32_t incs[4] = {i01 & 0xFFFFu, i01 >> 16, i23 & 0xFFFFu, i23 >> 16};
-                const uint32_t tots[4] = {t01 & 0xFFFFu, t01 >> 16, t23 & 0xFFFFu, t23 >> 16};
-                uint64_t cb = out;
-#pragma unroll
-                for (int c = 0; c < kChunks; ++c) {
-                    uint64_t rk = cb + incs[c] - kc[c];
-                    const uint64_t pos0 = s0 + warp * kWarpStarts + 512u * c + 16u * lane;
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        uint32_t fw = f[c][i];
-                        while (fw) {
-                            const uint32_t b = (uint32_t)(__ffs(fw) - 1) >> 3;
-                            if (rk < cap) d_pos[rk] = pos0 + 4u * i + b;
-                            ++rk;
-                            fw &= fw - 1;
-                        }
-                    }
-                    cb += tots[c];
-                }
-            } else {
-                tile_count += count_flags<kChunks>(f);
-            }
+            tile_count += n;
         }
     }
-
+    __syncwarp();   // the queue is reused by the next tile
     return tile_count;
 }
 

@@ -23,8 +23,10 @@ constexpr uint32_t kStatusTimeout = 2u;
 
 enum ScanMode : int {
     kModeCount = 0,      // count only: per-CTA partial counts, last CTA writes *d_count
-    kModeTileCount = 1,  // as kModeCount, and per-(tile, warp) counts for a report
-    kModeWrite = 2       // report: write ascending positions of tiles with matches
+    kModeTileCount = 1,  // as kModeCount, and per-(tile, warp) counts for a report; the partials
+                         // are per range of tiles_per_cta tiles (zeroed by the caller)
+    kModeWrite = 2       // report: write ascending positions of tiles with matches; CTA b owns
+                         // tile range b
 };
 
 struct ScanArgs {
@@ -41,8 +43,9 @@ struct ScanArgs {
     uint32_t nd[4];          // dense compares per word-alignment class (set by launch_scan)
     uint32_t test_skip_copy; // test hook: 1 = never issue the first tile's copy
     uint32_t* status;        // deferred status word
-    uint64_t* partials;      // per-CTA counts (scratch, grid entries)
+    uint64_t* partials;      // counting: per-CTA counts; tile-count/write: per tile-range counts (grid entries)
     uint32_t* ticket;        // last-CTA ticket (scratch, zero between launches)
+    unsigned long long* tile_next;  // next unclaimed tile of the counting modes (scratch, zero between launches)
     uint64_t* d_count;       // result count
     uint32_t* warp_counts;   // per-(tile, warp) counts (scratch, ntiles x 8; report only)
     uint64_t* d_pos;         // report output
@@ -67,11 +70,11 @@ inline uint32_t stage_bytes_for(uint32_t m) {
 }
 
 // Header (barriers, stage descriptors, reduction slots), the per-warp queues
-// of surviving 4-start words (kQueueCap each; a warp-tile with more survivors
-// continues densely instead), then the stage ring.
+// of 16-start chunks with surviving starts (one 16-byte entry for each of
+// the warp's 128 chunks), then the stage ring.
 constexpr uint32_t kScanHeader = 512;
-constexpr uint32_t kQueueCap = 128;                                      // entries per warp
-constexpr uint32_t kQueueBytes = kConsumerWarps * kQueueCap * 8;           // 8 KiB
+constexpr uint32_t kQueueCap = kWarpStarts / 16;                           // entries per warp
+constexpr uint32_t kQueueBytes = kConsumerWarps * kQueueCap * 16;          // 16 KiB
 
 inline size_t scan_smem_bytes(uint32_t stage_bytes, uint32_t stages) {
     return kScanHeader + kQueueBytes + (size_t)stage_bytes * stages;

@@ -1,8 +1,11 @@
 // Kernels of the SIMD-naive search (Tarhio, Holub, Giaquinta, Sec. 2), for sm_103a.
 //
-// scan_kernel  - Algorithms 2-4 on the GPU. A CTA owns a contiguous range of
-//                tiles of kTile = 16384 start positions and runs nine warps:
-//                one producer and eight consumers.
+// scan_kernel  - Algorithms 2-4 on the GPU. A CTA runs nine warps: one
+//                producer and eight consumers, over tiles of kTile = 16384
+//                start positions. In the counting modes CTAs claim tiles one
+//                at a time from a global counter, so that the CTAs that run
+//                faster take more tiles and all finish together; in the
+//                write mode CTA b owns the contiguous tile range b.
 //
 //   Producer (warp 8): for each tile, waits until the consumers have
 //   released a ring slot (mbarrier `empty`), loads the at most 30 bytes of
@@ -15,18 +18,19 @@
 //   16-byte shared-memory load of a warp covers 512 consecutive bytes. The
 //   paper's SIMDcompare for pattern position q and symbol c is computed for
 //   16 starts s at a time: two 16-byte loads cover bytes s+q .. s+q+19,
-//   funnel shifts align them, and an exact SWAR zero-byte test of w ^ c..c
-//   leaves the result in the high bit of each byte ("found", four starts
-//   per 32-bit word).
+//   funnel shifts align them, and w ^ c..c is zero in exactly the bytes that
+//   match. Compares are ANDed by OR-ing these XORs: one exact SWAR zero-byte
+//   test of the OR leaves the AND of their results in the high bit of each
+//   byte ("found", four starts per 32-bit word).
 //
 //   Dense phase: the first r compares (in the order pi) run for every start
 //   with no zero test - the loop peeling of Sec. 2.3.
-//   Sparse phase: the 4-start words whose found bits survived are compacted,
+//   Sparse phase: the 16-start chunks with a surviving start are compacted,
 //   in position order, into a per-warp queue in shared memory; each lane
-//   then continues one word through compares r .. m-1 and leaves as soon as
-//   the word's found bits are zero - the early exit of Algorithm 2, taken per
-//   4-start word instead of per SIMD register. popcount(found) is the count
-//   (Algorithm 2); the reporting modes write the set bits' positions.
+//   then continues one chunk through compares r .. m-1 and leaves as soon as
+//   the chunk's found bits are zero - the early exit of Algorithm 2, taken
+//   per 16-start chunk instead of per SIMD register. popcount(found) is the
+//   count (Algorithm 2); the reporting modes write the set bits' positions.
 //
 // hist_kernel  - byte histogram of the text (the frequencies of Sec. 2.2).
 //
@@ -60,7 +64,7 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
     StageDesc* desc = reinterpret_cast<StageDesc*>(smem + 128);          // [kMaxStages]
     uint64_t* red = reinterpret_cast<uint64_t*>(smem + 256);             // [kConsumerWarps + 1]
     uint32_t* flag = reinterpret_cast<uint32_t*>(smem + 336);
-    uint2* queues = reinterpret_cast<uint2*>(smem + kScanHeader);        // [kConsumerWarps][kQueueCap]
+    uint4* queues = reinterpret_cast<uint4*>(smem + kScanHeader);        // [kConsumerWarps][kQueueCap]
     uint8_t* bufs = smem + kScanHeader + kQueueBytes;
 
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -94,6 +98,10 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
             }
         }
         uint32_t issued = 0;
+        // counting modes: the claim of the next tile is in flight while the
+        // producer waits for a free slot
+        unsigned long long claim = 0;
+        if (MODE != kModeWrite && lane == 0) claim = atomicAdd(A.tile_next, 1ull);
         // stage s and use count u of the ring for iteration it, kept without division
         for (uint32_t it = 0, s = 0, u = 0;; ++it) {
             if (u > 0) {
@@ -106,7 +114,11 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
             uint64_t tile = kEnd;
             uint32_t tcount = 0;
             if (MODE != kModeWrite) {
-                if (cursor < t_end) tile = cursor++;
+                const uint64_t t = __shfl_sync(kFull, claim, 0);
+                if (t < A.ntiles) {
+                    tile = t;
+                    if (lane == 0) claim = atomicAdd(A.tile_next, 1ull);
+                }
             } else {
                 // next tile with matches; lanes look at 4 tiles x 8 warp counts per step
                 while (cursor < t_end) {
@@ -158,7 +170,7 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
         __syncwarp();
     } else {
         // ---------------------------------------------------------- consumers
-        uint2* q = queues + warp * kQueueCap;
+        uint4* q = queues + warp * kQueueCap;
         const uint32_t c0 = warp * (kWarpStarts / 16) + lane;   // lane's first 16-byte chunk in the tile
         const uint32_t wq = warp * (kWarpStarts / 4);           // warp's first word in the tile
         for (uint32_t s = 0, phase = 0;; ) {
@@ -185,7 +197,11 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
 
             if (MODE == kModeTileCount) {
                 const uint32_t wsum = warp_sum_u32(tile_count);
-                if (lane == 0) A.warp_counts[d.tile * kConsumerWarps + warp] = wsum;
+                if (lane == 0) {
+                    A.warp_counts[d.tile * kConsumerWarps + warp] = wsum;
+                    if (wsum) atomicAdd(reinterpret_cast<unsigned long long*>(A.partials) + d.tile / A.tiles_per_cta,
+                                        (unsigned long long)wsum);
+                }
             }
             my_count += tile_count;
             __syncwarp();
@@ -199,14 +215,17 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
 
     if (MODE == kModeWrite) return;
 
-    // CTA total -> partials; the last CTA to finish writes the sum.
+    // count: CTA total -> partials; tile-count: the consumers added each
+    // tile's count to its range's partial. The last CTA to finish writes the
+    // sum and clears the ticket and the tile counter for the next launch.
     const uint64_t ws = warp_sum_u64((uint64_t)my_count);
     if (lane == 0) red[warp] = ws;
+    __threadfence();
     __syncthreads();
     if (tid == 0) {
         uint64_t tot = 0;
         for (int w = 0; w < kConsumerWarps + 1; ++w) tot += red[w];
-        A.partials[blockIdx.x] = tot;
+        if (MODE == kModeCount) A.partials[blockIdx.x] = tot;
         __threadfence();
         const uint32_t t = atomicAdd(A.ticket, 1u);
         *flag = (t == gridDim.x - 1) ? 1u : 0u;
@@ -225,6 +244,7 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
             for (int w = 0; w < kConsumerWarps + 1; ++w) tot += red[w];
             *A.d_count = tot;
             *A.ticket = 0u;
+            *A.tile_next = 0ull;
         }
     }
 }

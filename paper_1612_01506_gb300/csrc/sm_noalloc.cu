@@ -11,7 +11,8 @@
 // Scratch layout (bytes of g_noalloc_scratch):
 //   [0, 4)        deferred status bits (written by kernels, not read back)
 //   [4, 8)        last-CTA ticket (must be 0 when a call starts)
-//   [256, ..)     partial counts, kMaxCtas x uint64
+//   [8, 16)       tile counter of the tile-count pass (must be 0 when a call starts)
+//   [256, ..)     partial counts per tile range, kMaxCtas x uint64 (cleared by each call)
 //   [.., end)     per-(tile, warp) match counts, kMaxTiles x 8 x uint32
 // kMaxTiles bounds the text: at most kMaxTiles * 16384 start positions.
 #include "sm.h"
@@ -114,14 +115,16 @@ extern "C" sm_status sm_report_noalloc(const uint8_t* d_text, uint64_t n, const 
     const uint32_t grid = (uint32_t)((a.ntiles + a.tiles_per_cta - 1) / a.tiles_per_cta);
     a.status = reinterpret_cast<uint32_t*>(su.scratch);
     a.ticket = reinterpret_cast<uint32_t*>(su.scratch + 4);
+    a.tile_next = reinterpret_cast<unsigned long long*>(su.scratch + 8);
     a.partials = reinterpret_cast<uint64_t*>(su.scratch + kPartialsOff);
     a.warp_counts = reinterpret_cast<uint32_t*>(su.scratch + kWarpCountsOff);
     a.one = 1;
     a.d_count = d_count;
     a.spin_ns = 1000000000ull;
 
-    // the array keeps the previous call's contents: clear status and ticket
-    if (cudaMemsetAsync(su.scratch, 0, 8, s) != cudaSuccess) return SM_ECUDA;
+    // the array keeps the previous call's contents: clear status, ticket,
+    // tile counter and the range counts
+    if (cudaMemsetAsync(su.scratch, 0, kPartialsOff + sizeof(uint64_t) * grid, s) != cudaSuccess) return SM_ECUDA;
     if (smk::launch_scan(smk::kModeTileCount, false, grid, smem, s, a, qc) != cudaSuccess) return SM_ECUDA;
     a.d_pos = d_pos;
     a.cap = cap;

@@ -8,6 +8,7 @@
 // which the paper also builds on the host before searching.
 #include "sm.h"
 #include "sm_internal.h"
+#include "sm_plan.h"
 
 #include <algorithm>
 #include <cmath>
@@ -108,66 +109,47 @@ sm_status check_pattern(const uint8_t* h_pat, uint32_t m, const uint32_t* h_pi) 
     return SM_OK;
 }
 
-// Peeling factor r when the caller gives none. Sec. 2.3 leaves r to tuning
-// (2 for English with frequency order, 3 to 5 for DNA). Costs, in
-// instructions per warp of 2048 starts, measured on GB300: a peeled compare
-// of all starts ~100; compacting the surviving 4-start words ~80 when any
-// survives; each round of 32 surviving words continued by one lane each ~60;
-// more than the queue holds (~96 expected) falls back to dense compares. With
-// the text histogram the fraction of starts alive after r compares is the
-// product of the compared symbols' frequencies, and r minimizes the sum.
-// Without it r = 2, the paper's choice for the frequency-ordered search.
-uint32_t auto_peel(const uint8_t* p, uint32_t m, const uint32_t* pi, const uint64_t* hist, uint64_t n) {
-    if (!hist || n == 0) return std::min<uint32_t>(m, 2);
-    double alive = 1.0, best = 1e300;
-    uint32_t best_r = 1;
-    const uint32_t top = std::min<uint32_t>(m, 16);
-    for (uint32_t r = 1; r <= top; ++r) {
-        const uint32_t q = pi ? pi[r - 1] : r - 1;
-        alive *= (double)hist[p[q]] / (double)n;
-        double cost = 100.0 * r;
-        if (r < m) {
-            const double p_word = 1.0 - std::pow(1.0 - alive, 4.0);
-            const double p_warp = 1.0 - std::pow(1.0 - alive, 2048.0);
-            const double entries = 512.0 * p_word;
-            cost += 80.0 * p_warp + 60.0 * (p_warp + std::max(0.0, entries - 32.0) / 32.0);
-            if (entries > 96.0) cost += 200.0;
-        }
-        if (cost < best) {
-            best = cost;
-            best_r = r;
-        }
-    }
-    return best_r;
-}
-
 struct Plan {
-    std::vector<uint32_t> qc;
+    std::vector<uint32_t> qc;       // compare descriptors in scan order (plan_dense)
+    std::vector<uint32_t> groups;   // window groups of the peeled compares
     uint32_t r = 1;
     bool seven = false;
     bool zero = false;   // a pattern symbol never occurs in the text
 };
 
-Plan make_plan(const uint8_t* p, uint32_t m, const uint32_t* pi, const sm_search_opts* o, uint64_t n) {
-    Plan pl;
-    pl.qc.resize(m);
+// Compare descriptors (e << 8) | p[q], e = (text address mod 16) + q, in the
+// order pi; the text's symbol frequencies (when the caller passes its
+// histogram) pick the peeled compares.
+sm_status make_plan(const uint8_t* d_text, const uint8_t* p, uint32_t m, const uint32_t* pi,
+                    const sm_search_opts* o, uint64_t n, Plan* pl) {
+    const uint32_t delta = (uint32_t)(reinterpret_cast<uintptr_t>(d_text) & 15u);
+    std::vector<uint32_t> v(m);
     for (uint32_t j = 0; j < m; ++j) {
         const uint32_t q = pi ? pi[j] : j;
-        pl.qc[j] = (q << 8) | p[q];
+        v[j] = ((q + delta) << 8) | p[q];
     }
     const uint64_t* h = o ? o->h_hist256 : nullptr;
+    std::vector<double> freq;
     if (h) {
         uint64_t high = 0;
         for (int c = 0x80; c < 256; ++c) high += h[c];
         bool pat7 = true;
         for (uint32_t q = 0; q < m; ++q) {
             if (p[q] >= 0x80) pat7 = false;
-            if (h[p[q]] == 0) pl.zero = true;
+            if (h[p[q]] == 0) pl->zero = true;
         }
-        pl.seven = (high == 0) && pat7;
+        pl->seven = (high == 0) && pat7;
+        freq.resize(m);
+        for (uint32_t j = 0; j < m; ++j) freq[j] = n ? (double)h[v[j] & 0xFFu] / (double)n : 1.0;
     }
-    pl.r = (o && o->peel) ? std::min(o->peel, m) : auto_peel(p, m, pi, h, n);
-    return pl;
+    pl->qc.resize(m);
+    pl->groups.resize(smk::max_groups_for(m));
+    uint32_t ng = 0;
+    pl->r = smk::plan_dense(v.data(), m, h ? freq.data() : nullptr, o ? o->peel : 0u, pl->qc.data(),
+                            pl->groups.data(), (uint32_t)pl->groups.size(), &ng);
+    if (pl->r == 0) return fail(SM_EINVAL, "internal: dense plan exceeds its group capacity");
+    pl->groups.resize(ng);
+    return SM_OK;
 }
 
 struct Grid {
@@ -221,7 +203,8 @@ smk::ScanArgs scan_args(sm_ctx* c, const uint8_t* d_text, uint64_t n, uint32_t m
     a.ntiles = g.ntiles;
     a.tiles_per_cta = g.per_cta;
     a.m = m;
-    a.r = std::max<uint32_t>(1, std::min(pl.r, m));
+    a.r = pl.r;
+    a.ng = (uint32_t)pl.groups.size();
     a.stage_bytes = g.stage_bytes;
     a.stages = g.stages;
     a.status = c->d_status;
@@ -423,7 +406,9 @@ static sm_status search(sm_ctx* c, const uint8_t* d_text, uint64_t n, const uint
     if (!g.ok) return fail(SM_ECUDA, "cudaSetDevice(%d) failed", c->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if ((uint64_t)m > n) return zero_count(d_count, s);
-    Plan pl = make_plan(h_pat, m, h_pi, opts, n);
+    Plan pl;
+    st = make_plan(d_text, h_pat, m, h_pi, opts, n, &pl);
+    if (st != SM_OK) return st;
     if (pl.zero) return zero_count(d_count, s);
 
     const uint64_t nstarts = n - m + 1;
@@ -440,12 +425,12 @@ static sm_status search(sm_ctx* c, const uint8_t* d_text, uint64_t n, const uint
     cudaError_t e;
     if (report && (e = cudaMemsetAsync(c->d_partials, 0, sizeof(uint64_t) * gr.grid, s)) != cudaSuccess)
         return cuda_fail(e, "clearing the range counts");
-    e = smk::launch_scan(mode1, pl.seven, gr.grid, gr.smem, s, a, pl.qc.data());
+    e = smk::launch_scan(mode1, pl.seven, gr.grid, gr.smem, s, a, pl.qc.data(), pl.groups.data());
     if (e != cudaSuccess) return cuda_fail(e, "scan launch");
     if (report) {
         a.d_pos = d_pos;
         a.cap = cap;
-        e = smk::launch_scan(smk::kModeWrite, pl.seven, gr.grid, gr.smem, s, a, pl.qc.data());
+        e = smk::launch_scan(smk::kModeWrite, pl.seven, gr.grid, gr.smem, s, a, pl.qc.data(), pl.groups.data());
         if (e != cudaSuccess) return cuda_fail(e, "report launch");
     }
     return SM_OK;

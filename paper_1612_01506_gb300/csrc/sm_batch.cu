@@ -18,6 +18,7 @@
 // launch, and can be captured in a CUDA graph.
 #include "sm.h"
 #include "sm_device.cuh"
+#include "sm_plan.h"
 
 #include <algorithm>
 #include <cmath>
@@ -52,7 +53,7 @@ struct BatchText {        // a text, or one group of <= kMaxSlots of its pattern
 struct BatchPat {
     uint32_t qc_off;      // first compare descriptor in the qc table
     uint32_t m, r;
-    uint32_t nd;          // peeled compares per alignment class, 8 bits each
+    uint32_t ng;          // window groups of the peeled compares (after the m compares in the qc table)
     uint32_t out;         // index of the pattern in the caller's arrays
     uint32_t seven;       // 1: text and pattern are 7-bit
 };
@@ -205,16 +206,14 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constan
                 const BatchPat P = A.pats[p];
                 const uint64_t nst = min(T.n - P.m + 1, T.slimit);   // the plan keeps only m <= n
                 if (s0 >= nst) continue;
-                const GlobalQC qc{A.qc + P.qc_off};
-                const uint32_t nd0 = P.nd & 0xFFu, nd1 = (P.nd >> 8) & 0xFFu, nd2 = (P.nd >> 16) & 0xFFu,
-                               nd3 = P.nd >> 24;
+                const GlobalQC qc{A.qc + P.qc_off, P.m};
                 uint32_t c;
                 if (P.seven)
-                    c = warp_tile<true, false, true>(b4, b32, c0, wq, warp, lane, qc, P.m, P.r, nd0, nd1, nd2, nd3,
-                                                     one, nst, s0, q, 0, nullptr, 0);
+                    c = warp_tile<true, false, true>(b4, b32, c0, wq, warp, lane, qc, P.m, P.r, P.ng, one, nst, s0, q,
+                                                     0, nullptr, 0);
                 else
-                    c = warp_tile<false, false, true>(b4, b32, c0, wq, warp, lane, qc, P.m, P.r, nd0, nd1, nd2, nd3,
-                                                      one, nst, s0, q, 0, nullptr, 0);
+                    c = warp_tile<false, false, true>(b4, b32, c0, wq, warp, lane, qc, P.m, P.r, P.ng, one, nst, s0,
+                                                      q, 0, nullptr, 0);
                 c = warp_sum_u32(c);
                 if (lane == 0 && c) atomicAdd(&slots[p - pbase], c);
             }
@@ -362,31 +361,10 @@ struct Guard {
 
 // Peel factor from the pattern's symbol frequencies (the single-pattern
 // scan's cost model: dense compare ~100, compaction ~80, 32 words ~60).
-uint32_t batch_peel(const std::vector<uint32_t>& syms, const uint32_t* h, uint64_t n, uint32_t m) {
-    double alive = 1.0, best = 1e300;
-    uint32_t best_r = 1;
-    for (uint32_t r = 1; r <= std::min<uint32_t>(m, 16); ++r) {
-        alive *= (double)h[syms[r - 1]] / (double)n;
-        double cost = 100.0 * r;
-        if (r < m) {
-            const double p_word = 1.0 - std::pow(1.0 - alive, 4.0);
-            const double p_warp = 1.0 - std::pow(1.0 - alive, 2048.0);
-            const double entries = 512.0 * p_word;
-            cost += 80.0 * p_warp + 60.0 * (p_warp + std::max(0.0, entries - 32.0) / 32.0);
-            if (entries > 96.0) cost += 200.0;
-        }
-        if (cost < best) {
-            best = cost;
-            best_r = r;
-        }
-    }
-    return best_r;
-}
-
 // One pattern described for a text with byte histogram h (n bytes): the
-// rarest-first order (Sec. 2.2), then either the dense scan (peel r, peeled
-// compares grouped by word alignment) or the candidate path (compares in
-// order pi, the first being the rarest symbol).
+// rarest-first order (Sec. 2.2), then either the dense scan (peeled compares
+// and their window groups from plan_dense) or the candidate path (compares
+// in order pi, the first being the rarest symbol).
 struct PatDesc {
     BatchPat pat{};
     std::vector<uint32_t> qc;
@@ -405,25 +383,20 @@ PatDesc describe(const uint8_t* p, uint32_t m, const uint32_t* h, uint64_t n, ui
     std::stable_sort(pi.begin(), pi.end(), [&](uint32_t a, uint32_t b) { return h[p[a]] < h[p[b]]; });
     std::vector<uint32_t> v(m);
     for (uint32_t j = 0; j < m; ++j) v[j] = ((pi[j] + delta) << 8) | p[pi[j]];
-    d.pat = BatchPat{0, m, 1, 0, out, text7 ? 1u : 0u};
+    d.pat = BatchPat{0, m, 1, 0, out, text7 ? 1u : 0u};   // ng = 0: no peeled compares (candidate path)
     if ((double)h[p[pi[0]]] / (double)n < smk::kCandidateFreq) {
         d.cand = true;
         d.qc = std::move(v);
         return d;
     }
-    std::vector<uint32_t> syms(m);
-    for (uint32_t j = 0; j < m; ++j) syms[j] = p[pi[j]];
-    const uint32_t r = batch_peel(syms, h, n, m);
-    uint32_t nd[4] = {0, 0, 0, 0};
-    for (uint32_t c = 0; c < 4; ++c)
-        for (uint32_t j = 0; j < r; ++j)
-            if (((v[j] >> 10) & 3u) == c) {
-                d.qc.push_back(v[j]);
-                ++nd[c];
-            }
-    for (uint32_t j = r; j < m; ++j) d.qc.push_back(v[j]);
-    d.pat.r = r;
-    d.pat.nd = nd[0] | (nd[1] << 8) | (nd[2] << 16) | (nd[3] << 24);
+    std::vector<double> freq(m);
+    for (uint32_t j = 0; j < m; ++j) freq[j] = (double)h[p[pi[j]]] / (double)n;
+    // the m compares in scan order, then the window groups of the peeled ones
+    d.qc.resize(m + smk::max_groups_for(m));
+    uint32_t ng = 0;
+    d.pat.r = smk::plan_dense(v.data(), m, freq.data(), 0, d.qc.data(), d.qc.data() + m, smk::max_groups_for(m), &ng);
+    d.qc.resize(m + ng);
+    d.pat.ng = ng;
     return d;
 }
 

@@ -168,29 +168,35 @@ __device__ __forceinline__ uint32_t keep_zero(uint32_t f, uint32_t y, uint32_t o
 #endif
 }
 
-// One compare, accumulated for the lane's NC 16-start chunks (chunk c at
-// index c0 + 32c): y |= window ^ (c..c), where the window of a start is
-// text bytes s+q .. s+q+3. v = (e << 8) | symbol with e = text misalignment
-// + pattern position q; the caller guarantees D == (e >> 2) & 3, so the
-// word selection is static. All 2*NC loads issue before the XORs.
+// One compare, accumulated for the lane's NC 16-start chunks: y |= window ^
+// (c..c), where the window of a start s is text bytes s+q .. s+q+3 and a, b
+// hold the 16-byte units E and E + 1 of each chunk. v = (e << 8) | symbol
+// with e = text misalignment + pattern position q; the caller guarantees
+// E == e >> 4 and D == (e >> 2) & 3, so the word selection is static.
 template <int D, int NC>
-__device__ __forceinline__ void acc_chunks(const uint4* __restrict__ b4, uint32_t c0, uint32_t v,
+__device__ __forceinline__ void acc_loaded(const uint4 (&a)[NC], const uint4 (&b)[NC], uint32_t v,
                                            uint32_t (&y)[NC][4]) {
-    const uint32_t e = v >> 8;
     const uint32_t P = (v & 0xFFu) * 0x01010101u;
-    const uint32_t ci = c0 + (e >> 4);
-    const uint32_t sh = (e & 3u) << 3;
-    uint4 a[NC], b[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        a[c] = b4[ci + 32 * c];
-        b[c] = b4[ci + 32 * c + 1];
-    }
+    const uint32_t sh = ((v >> 8) & 3u) << 3;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
         const uint32_t X[8] = {a[c].x, a[c].y, a[c].z, a[c].w, b[c].x, b[c].y, b[c].z, b[c].w};
 #pragma unroll
         for (int i = 0; i < 4; ++i) y[c][i] |= __funnelshift_r(X[D + i], X[D + i + 1], sh) ^ P;
+    }
+}
+
+// As acc_loaded for a compare whose window is 4-byte aligned (e mod 4 == 0):
+// the words need no shift.
+template <int D, int NC>
+__device__ __forceinline__ void acc_aligned(const uint4 (&a)[NC], const uint4 (&b)[NC], uint32_t v,
+                                            uint32_t (&y)[NC][4]) {
+    const uint32_t P = (v & 0xFFu) * 0x01010101u;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const uint32_t X[8] = {a[c].x, a[c].y, a[c].z, a[c].w, b[c].x, b[c].y, b[c].z, b[c].w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) y[c][i] |= X[D + i] ^ P;
     }
 }
 
@@ -254,22 +260,28 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, uint32_t lane) {
 
 template <int MAXM>
 struct PatArg {
-    uint32_t qc[MAXM];   // compare j: (e_j << 8) | p[pi(j)], e_j = (text address mod 16) + pi(j)
+    static constexpr int kGroups = (14 + MAXM) / 16 + 1;
+    uint32_t qc[MAXM];        // compare j: (e_j << 8) | p[pi(j)], e_j = (text address mod 16) + pi(j)
+    uint32_t grp[kGroups];    // window groups of the peeled compares
 };
 
 // ------------------------------------------------------------ one warp-tile
 
-// Compare descriptors held in the kernel's parameter block.
+// Compare descriptors and window groups held in the kernel's parameter block.
 template <int MAXM>
 struct ParamQC {
     const PatArg<MAXM>* p;
     __device__ __forceinline__ uint32_t operator()(uint32_t j) const { return p->qc[j]; }
+    __device__ __forceinline__ uint32_t group(uint32_t g) const { return p->grp[g]; }
 };
 
-// Compare descriptors in global memory (read-only, uniform across the warp).
+// Compare descriptors in global memory (read-only, uniform across the warp),
+// the window groups after the m compares.
 struct GlobalQC {
     const uint32_t* __restrict__ p;
+    uint32_t m;
     __device__ __forceinline__ uint32_t operator()(uint32_t j) const { return __ldg(p + j); }
+    __device__ __forceinline__ uint32_t group(uint32_t g) const { return __ldg(p + m + g); }
 };
 
 // One consumer warp's 2048 starts of a staged tile against one pattern:
@@ -278,8 +290,10 @@ struct GlobalQC {
 // WRITE, also writes the positions in ascending order from rank `out`
 // (first `cap` only). DIRECT: a count may skip the compaction when r >= m.
 //
-// Dense phase: the r peeled compares (arriving grouped by word alignment in
-// nd0..nd3) for all 2048 starts, folded into one zero-byte test.
+// Dense phase: the r peeled compares for all 2048 starts, folded into one
+// zero-byte test. They arrive in ng window groups: the two 16-byte units of
+// every chunk are loaded once per group and serve all its compares, the
+// 4-byte-aligned ones (no shift) first.
 // Sparse phase: the 16-start chunks with a surviving start are compacted, in
 // position order, into the warp's queue q (at most 128 entries: the found
 // words, the chunk index in the low bits of the first); each lane then takes
@@ -289,20 +303,32 @@ struct GlobalQC {
 template <bool SEVEN, bool WRITE, bool DIRECT, class QC>
 __device__ __forceinline__ uint32_t warp_tile(const uint4* __restrict__ b4, const uint32_t* __restrict__ b32,
                                               uint32_t c0, uint32_t wq, uint32_t warp, uint32_t lane, QC qc,
-                                              uint32_t m, uint32_t r, uint32_t nd0, uint32_t nd1, uint32_t nd2,
-                                              uint32_t nd3, uint32_t one, uint64_t nstarts, uint64_t s0, uint4* q,
+                                              uint32_t m, uint32_t r, uint32_t ng, uint32_t one,
+                                              uint64_t nstarts, uint64_t s0, uint4* q,
                                               uint64_t out, uint64_t* __restrict__ d_pos, uint64_t cap) {
     uint32_t f[kChunks][4];
 #pragma unroll
     for (int c = 0; c < kChunks; ++c)
 #pragma unroll
         for (int i = 0; i < 4; ++i) f[c][i] = 0u;
-    {
-        uint32_t j = 0;
-        for (uint32_t k = 0; k < nd0; ++k, ++j) acc_chunks<0>(b4, c0, qc(j), f);
-        for (uint32_t k = 0; k < nd1; ++k, ++j) acc_chunks<1>(b4, c0, qc(j), f);
-        for (uint32_t k = 0; k < nd2; ++k, ++j) acc_chunks<2>(b4, c0, qc(j), f);
-        for (uint32_t k = 0; k < nd3; ++k, ++j) acc_chunks<3>(b4, c0, qc(j), f);
+    for (uint32_t g = 0, j = 0; g < ng; ++g) {
+        const uint32_t gd = qc.group(g);
+        const uint32_t ci = c0 + (gd & 0x1FFu);
+        uint4 a[kChunks], b[kChunks];
+#pragma unroll
+        for (int c = 0; c < kChunks; ++c) {
+            a[c] = b4[ci + 32 * c];
+            b[c] = b4[ci + 32 * c + 1];
+        }
+        // aligned compares (at most one per word class), then the others
+        if (gd & (1u << 9)) acc_aligned<0>(a, b, qc(j++), f);
+        if (gd & (1u << 10)) acc_aligned<1>(a, b, qc(j++), f);
+        if (gd & (1u << 11)) acc_aligned<2>(a, b, qc(j++), f);
+        if (gd & (1u << 12)) acc_aligned<3>(a, b, qc(j++), f);
+        for (uint32_t k = (gd >> 13) & 3u; k; --k) acc_loaded<0>(a, b, qc(j++), f);
+        for (uint32_t k = (gd >> 15) & 3u; k; --k) acc_loaded<1>(a, b, qc(j++), f);
+        for (uint32_t k = (gd >> 17) & 3u; k; --k) acc_loaded<2>(a, b, qc(j++), f);
+        for (uint32_t k = (gd >> 19) & 3u; k; --k) acc_loaded<3>(a, b, qc(j++), f);
     }
 #pragma unroll
     for (int c = 0; c < kChunks; ++c)

@@ -40,7 +40,7 @@ struct ScanArgs {
     uint32_t stage_bytes;    // shared-memory bytes per pipeline stage (multiple of 128)
     uint32_t stages;         // pipeline depth, 2..kMaxStages
     uint32_t one;            // the value 1 (keeps an add on the multiply-add pipe)
-    uint32_t nd[4];          // dense compares per word-alignment class (set by launch_scan)
+    uint32_t ng;             // window groups of the peeled compares
     uint32_t test_skip_copy; // test hook: 1 = never issue the first tile's copy
     uint32_t* status;        // deferred status word
     uint64_t* partials;      // counting: per-CTA counts; tile-count/write: per tile-range counts (grid entries)
@@ -80,11 +80,11 @@ inline size_t scan_smem_bytes(uint32_t stage_bytes, uint32_t stages) {
     return kScanHeader + kQueueBytes + (size_t)stage_bytes * stages;
 }
 
-// Launch a scan kernel. `qc` holds m words (q << 8) | p[q] in compare order.
-// The first a.r of them (the peeled compares, whose order is free) are
-// regrouped by the 4-byte alignment of their text offset.
+// Launch a scan kernel. `qc` holds the m compare descriptors (e << 8) | p[q],
+// e = (text address mod 16) + q, in scan order and `groups` the a.ng window
+// groups of the first a.r (both as planned by plan_dense).
 cudaError_t launch_scan(int mode, bool seven, uint32_t grid, size_t smem, cudaStream_t s,
-                        const ScanArgs& a, const uint32_t* qc);
+                        const ScanArgs& a, const uint32_t* qc, const uint32_t* groups);
 // Resident CTAs per SM of the scan kernel used for (m, mode, seven) with this smem.
 int scan_occupancy(int mode, bool seven, uint32_t m, size_t smem);
 // Raise the dynamic shared-memory limit of every scan kernel.

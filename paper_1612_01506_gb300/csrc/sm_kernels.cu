@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
                 out = d.offset + warp_sum_u32(cw);
             }
             const uint32_t tile_count = warp_tile<SEVEN, MODE == kModeWrite, MODE == kModeCount>(
-                b4, b32, c0, wq, warp, lane, ParamQC<MAXM>{&P}, m, r, A.nd[0], A.nd[1], A.nd[2], A.nd[3], one,
+                b4, b32, c0, wq, warp, lane, ParamQC<MAXM>{&P}, m, r, A.ng, one,
                 A.nstarts, s0, q, out, A.d_pos, A.cap);
 
             if (MODE == kModeTileCount) {
@@ -309,25 +309,15 @@ __global__ void __launch_bounds__(kHistThreads) hist_kernel(const HistArgs A) {
 // ------------------------------------------------------------ dispatch
 
 template <int MAXM, int MODE, bool SEVEN>
-cudaError_t launch_one(uint32_t grid, size_t smem, cudaStream_t st, const ScanArgs& a0, const uint32_t* qc) {
+cudaError_t launch_one(uint32_t grid, size_t smem, cudaStream_t st, const ScanArgs& a, const uint32_t* qc,
+                       const uint32_t* groups) {
+    if (a.ng > (uint32_t)PatArg<MAXM>::kGroups) return cudaErrorInvalidValue;
     PatArg<MAXM> p;
-    ScanArgs a = a0;
-    // add the text's misalignment to every position; stable-sort the peeled
-    // compares by word alignment class d = (e >> 2) & 3
-    const uint32_t delta = (uint32_t)(reinterpret_cast<uintptr_t>(a.text) & 15u);
     uint32_t j = 0;
-    for (uint32_t d = 0; d < 4; ++d) {
-        a.nd[d] = 0;
-        for (uint32_t k = 0; k < a.r; ++k) {
-            const uint32_t v = qc[k] + (delta << 8);
-            if (((v >> 10) & 3u) == d) {
-                p.qc[j++] = v;
-                ++a.nd[d];
-            }
-        }
-    }
-    for (; j < a.m; ++j) p.qc[j] = qc[j] + (delta << 8);
+    for (; j < a.m; ++j) p.qc[j] = qc[j];
     for (; j < (uint32_t)MAXM; ++j) p.qc[j] = 0;
+    for (j = 0; j < a.ng; ++j) p.grp[j] = groups[j];
+    for (; j < (uint32_t)PatArg<MAXM>::kGroups; ++j) p.grp[j] = 0;
     scan_kernel<MAXM, MODE, SEVEN><<<grid, kThreads, smem, st>>>(a, p);
     return cudaGetLastError();
 }
@@ -350,13 +340,13 @@ const void* pick(int mode, bool seven, uint32_t m) {
 }  // namespace
 
 cudaError_t launch_scan(int mode, bool seven, uint32_t grid, size_t smem, cudaStream_t s, const ScanArgs& a,
-                        const uint32_t* qc) {
+                        const uint32_t* qc, const uint32_t* groups) {
     const bool small = a.m <= (uint32_t)kSmallM;
 #define SMK_LAUNCH(MODE)                                                                            \
-    if (small) return seven ? launch_one<kSmallM, MODE, true>(grid, smem, s, a, qc)                 \
-                            : launch_one<kSmallM, MODE, false>(grid, smem, s, a, qc);              \
-    return seven ? launch_one<kLargeM, MODE, true>(grid, smem, s, a, qc)                            \
-                 : launch_one<kLargeM, MODE, false>(grid, smem, s, a, qc);
+    if (small) return seven ? launch_one<kSmallM, MODE, true>(grid, smem, s, a, qc, groups)                 \
+                            : launch_one<kSmallM, MODE, false>(grid, smem, s, a, qc, groups);              \
+    return seven ? launch_one<kLargeM, MODE, true>(grid, smem, s, a, qc, groups)                            \
+                 : launch_one<kLargeM, MODE, false>(grid, smem, s, a, qc, groups);
     switch (mode) {
         case kModeCount: SMK_LAUNCH(kModeCount)
         case kModeTileCount: SMK_LAUNCH(kModeTileCount)

@@ -17,6 +17,7 @@
 // kMaxTiles bounds the text: at most kMaxTiles * 16384 start positions.
 #include "sm.h"
 #include "sm_internal.h"
+#include "sm_plan.h"
 
 #include <cstring>
 #include <functional>
@@ -89,18 +90,24 @@ extern "C" sm_status sm_report_noalloc(const uint8_t* d_text, uint64_t n, const 
     const uint64_t nstarts = n - m + 1;
     if (nstarts > SM_NOALLOC_MAX_STARTS) return SM_EINVAL;   // text longer than the scratch covers
 
-    uint32_t qc[SM_MAX_M];
+    // compare descriptors in the order pi, the first two peeled (no histogram)
+    const uint32_t delta = (uint32_t)(reinterpret_cast<uintptr_t>(d_text) & 15u);
+    uint32_t v[SM_MAX_M], qc[SM_MAX_M], groups[smk::max_groups_for(SM_MAX_M)];
     for (uint32_t j = 0; j < m; ++j) {
         const uint32_t q = h_pi ? h_pi[j] : j;
-        qc[j] = (q << 8) | h_pat[q];
+        v[j] = ((q + delta) << 8) | h_pat[q];
     }
+    uint32_t ng = 0;
+    const uint32_t r = smk::plan_dense(v, m, nullptr, 0, qc, groups, smk::max_groups_for(SM_MAX_M), &ng);
+    if (r == 0) return SM_EINVAL;
     smk::ScanArgs a{};
     a.text = d_text;
     a.n = n;
     a.nstarts = nstarts;
     a.ntiles = (nstarts + smk::kTile - 1) / smk::kTile;
     a.m = m;
-    a.r = m < 2 ? m : 2;
+    a.r = r;
+    a.ng = ng;
     a.stage_bytes = smk::stage_bytes_for(m);
     a.stages = 4;
     while (a.stages > 2 && smk::scan_smem_bytes(a.stage_bytes, a.stages) > su.max_smem) --a.stages;
@@ -125,9 +132,9 @@ extern "C" sm_status sm_report_noalloc(const uint8_t* d_text, uint64_t n, const 
     // the array keeps the previous call's contents: clear status, ticket,
     // tile counter and the range counts
     if (cudaMemsetAsync(su.scratch, 0, kPartialsOff + sizeof(uint64_t) * grid, s) != cudaSuccess) return SM_ECUDA;
-    if (smk::launch_scan(smk::kModeTileCount, false, grid, smem, s, a, qc) != cudaSuccess) return SM_ECUDA;
+    if (smk::launch_scan(smk::kModeTileCount, false, grid, smem, s, a, qc, groups) != cudaSuccess) return SM_ECUDA;
     a.d_pos = d_pos;
     a.cap = cap;
-    if (smk::launch_scan(smk::kModeWrite, false, grid, smem, s, a, qc) != cudaSuccess) return SM_ECUDA;
+    if (smk::launch_scan(smk::kModeWrite, false, grid, smem, s, a, qc, groups) != cudaSuccess) return SM_ECUDA;
     return SM_OK;
 }

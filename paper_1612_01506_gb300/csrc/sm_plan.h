@@ -1,0 +1,190 @@
+// Host planning of the dense phase of the scan (loop peeling, Sec. 2.3 of
+// Tarhio, Holub, Giaquinta), shared by the single-pattern and batched
+// launches. Internal to the library; uses no heap memory.
+//
+// A compare descriptor is (e << 8) | symbol, where e = (text address mod 16)
+// + pattern position is the byte offset of the compare's 4-byte window from
+// the first start of a 16-start chunk. A consumer lane reads that window
+// from the 16-byte units E = e >> 4 and E + 1 of each of its chunks. The
+// dense phase loads those two units once per group of peeled compares that
+// share E, and a compare whose window is 4-byte aligned (e mod 4 == 0) needs
+// no funnel shift, so it costs half the integer instructions of the others.
+//
+// Which compares to peel: Sec. 2.3 peels the first r compares of the order
+// pi and leaves r to tuning. With the text's symbol frequencies the planner
+// also builds a second order that takes, step by step, the compare with the
+// most selectivity (-log frequency) per modelled cost (aligned or not, in a
+// window already loaded or not), and peels the prefix of either order with
+// the lowest modelled cost. The count does not depend on which compares are
+// peeled or on their order: every start is still tested at every pattern
+// position until its found bit is zero.
+#pragma once
+
+#include <cmath>
+#include <cstdint>
+
+namespace smk {
+
+// Group descriptor: window unit E in bits 0-8; bit 9 + D set when the group
+// has the aligned compare of word class D = (e >> 2) & 3 (e = 16E + 4D);
+// bits 13 + 2D .. 14 + 2D the number (0..3) of its other compares of class D.
+constexpr uint32_t kPlanMaxPeel = 16;   // largest r the cost model chooses
+constexpr uint32_t kPlanCandidates = 64;
+
+// Window groups a pattern of length m can have: e < 16 + m, so E <= (14 + m) / 16.
+constexpr uint32_t max_groups_for(uint32_t m) { return (14 + m) / 16 + 1; }
+
+inline uint32_t group_e(uint32_t v) { return v >> 12; }
+inline uint32_t word_class(uint32_t v) { return (v >> 10) & 3u; }
+inline bool aligned(uint32_t v) { return ((v >> 8) & 3u) == 0; }
+
+// Modelled time of one 2048-start warp-tile, in consumer-warp cycles measured
+// per phase on GB300 (3 CTAs of 8 consumer warps per SM).
+struct PlanCosts {
+    double base = 550, window = 550, cmp_aligned = 190, cmp_shifted = 375;
+    double zero_test = 380, compact = 480, compact_per_chunk = 10;
+    double round = 350, iter = 450, iter_per_lane = 15;
+};
+
+inline double plan_cost(const uint32_t* v, uint32_t m, const double* freq, const uint32_t* sel, uint32_t k) {
+    const PlanCosts C;
+    double cost = C.base, alive = 1.0;
+    for (uint32_t a = 0; a < k; ++a) {
+        bool seen = false;
+        for (uint32_t b = 0; b < a; ++b) seen = seen || group_e(v[sel[b]]) == group_e(v[sel[a]]);
+        cost += (seen ? 0.0 : C.window) + (aligned(v[sel[a]]) ? C.cmp_aligned : C.cmp_shifted);
+        alive *= freq[sel[a]];
+    }
+    if (k >= m) return cost;
+    cost += C.zero_test;
+    const double p_any = 1.0 - std::pow(1.0 - alive, 2048.0);
+    const double qn = 128.0 * (1.0 - std::pow(1.0 - alive, 16.0));
+    cost += p_any * (C.compact + C.compact_per_chunk * qn);
+    // sparse rounds: two compares per zero test, the rest in the order pi
+    const double rounds = std::fmax(1.0, qn / 32.0);
+    double a = alive;
+    uint32_t iters = 0, i = 0;
+    auto next = [&]() -> int64_t {
+        for (; i < m; ++i) {
+            bool in = false;
+            for (uint32_t b = 0; b < k; ++b) in = in || sel[b] == i;
+            if (!in) return i++;
+        }
+        return -1;
+    };
+    while (iters < 64) {
+        const int64_t j1 = next();
+        if (j1 < 0) break;
+        const int64_t j2 = next();
+        ++iters;
+        a *= freq[j1] * (j2 >= 0 ? freq[j2] : 1.0);
+        if (j2 < 0 || 128.0 * (1.0 - std::pow(1.0 - a, 16.0)) < 0.5) break;
+    }
+    cost += p_any * rounds * (C.round + iters * (C.iter + C.iter_per_lane * std::fmin(32.0, qn / rounds)));
+    return cost;
+}
+
+// Plans the dense phase of a pattern with compare descriptors v[0..m) in
+// the order pi. freq[j] is the text frequency of v[j]'s symbol (nullptr:
+// unknown; then r = min(m, 2), the paper's choice for English). r_fixed > 0
+// peels the first r_fixed compares of pi. Writes the m descriptors in scan
+// order to qc (the r peeled ones by window, in each window the aligned ones
+// by word class and then the others by word class; then the rest in the
+// order pi) and the window groups to groups (one per distinct window, at
+// most max_groups_for(m)). Returns r, or 0 when the groups exceed
+// max_groups; *ng = number of groups.
+inline uint32_t plan_dense(const uint32_t* v, uint32_t m, const double* freq, uint32_t r_fixed, uint32_t* qc,
+                           uint32_t* groups, uint32_t max_groups, uint32_t* ng) {
+    uint32_t sel[kPlanCandidates];
+    uint32_t k = 0;
+    bool implicit = false;   // a long forced peel: the first r compares of pi
+    if (r_fixed || !freq) {
+        const uint32_t r = r_fixed ? (r_fixed < m ? r_fixed : m) : (m < 2 ? m : 2);
+        implicit = r > kPlanCandidates;
+        if (implicit)
+            k = r;
+        else
+            for (k = 0; k < r; ++k) sel[k] = k;
+    } else {
+        const PlanCosts C;
+        const uint32_t top = m < kPlanMaxPeel ? m : kPlanMaxPeel;
+        double best = 1e300;
+        uint32_t cand[kPlanMaxPeel];
+        // prefixes of pi
+        for (uint32_t j = 0; j < top; ++j) cand[j] = j;
+        for (uint32_t r = 1; r <= top; ++r) {
+            const double c = plan_cost(v, m, freq, cand, r);
+            if (c < best) {
+                best = c;
+                k = r;
+                for (uint32_t a = 0; a < r; ++a) sel[a] = cand[a];
+            }
+        }
+        // prefixes of the greedy order over the kPlanCandidates rarest
+        const uint32_t pool = m < kPlanCandidates ? m : kPlanCandidates;
+        for (uint32_t r = 1; r <= top; ++r) {
+            double best_gain = -1.0;
+            uint32_t pick = 0;
+            for (uint32_t j = 0; j < pool; ++j) {
+                bool in = false, loaded = false;
+                for (uint32_t a = 0; a + 1 < r; ++a) {
+                    in = in || cand[a] == j;
+                    loaded = loaded || group_e(v[cand[a]]) == group_e(v[j]);
+                }
+                if (in) continue;
+                const double cost = (loaded ? 0.0 : C.window) + (aligned(v[j]) ? C.cmp_aligned : C.cmp_shifted);
+                const double gain = -std::log(std::fmax(freq[j], 1e-300)) / cost;
+                if (gain > best_gain) {
+                    best_gain = gain;
+                    pick = j;
+                }
+            }
+            cand[r - 1] = pick;
+            const double c = plan_cost(v, m, freq, cand, r);
+            if (c < best) {
+                best = c;
+                k = r;
+                for (uint32_t a = 0; a < r; ++a) sel[a] = cand[a];
+            }
+        }
+    }
+    const uint32_t r = k;
+    auto sel_at = [&](uint32_t a) { return implicit ? a : sel[a]; };
+    // the peeled compares by window, in ascending order; in a window the
+    // aligned ones by word class, then the others by word class
+    uint32_t o = 0, g = 0;
+    int64_t prev = -1;
+    while (o < r) {
+        uint32_t E = ~0u;
+        for (uint32_t a = 0; a < r; ++a) {
+            const uint32_t e = group_e(v[sel_at(a)]);
+            if ((int64_t)e > prev && e < E) E = e;
+        }
+        prev = E;
+        uint32_t desc = E;
+        for (uint32_t pass = 0; pass < 2; ++pass)
+            for (uint32_t d = 0; d < 4; ++d) {
+                uint32_t cnt = 0;
+                for (uint32_t a = 0; a < r; ++a) {
+                    const uint32_t x = v[sel_at(a)];
+                    if (group_e(x) == E && word_class(x) == d && aligned(x) == (pass == 0)) {
+                        qc[o++] = x;
+                        ++cnt;
+                    }
+                }
+                desc |= pass == 0 ? (cnt << (9 + d)) : (cnt << (13 + 2 * d));
+            }
+        if (g >= max_groups) return 0;
+        groups[g++] = desc;
+    }
+    // the rest in the order pi
+    for (uint32_t j = 0; j < m; ++j) {
+        bool in = implicit && j < r;
+        for (uint32_t a = 0; a < r && !implicit; ++a) in = in || sel[a] == j;
+        if (!in) qc[o++] = v[j];
+    }
+    *ng = g;
+    return r;
+}
+
+}  // namespace smk

@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constan
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     uint64_t* empty = reinterpret_cast<uint64_t*>(smem + 64);
     BatchDesc* desc = reinterpret_cast<BatchDesc*>(smem + 128);
-    uint4* queues = reinterpret_cast<uint4*>(smem + kScanHeader);
+    uint32_t* queues = reinterpret_cast<uint32_t*>(smem + kScanHeader);
     uint32_t* slots = reinterpret_cast<uint32_t*>(smem + kScanHeader + kQueueBytes);
     uint8_t* after_slots = smem + kScanHeader + kQueueBytes + ((A.nslots * 4u + 127u) & ~127u);
     // per-tile position index of selected symbols: count, start, cursor, positions
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constan
         __syncwarp();
     } else {
         // ---------------------------------------------------------- consumers
-        uint4* q = queues + warp * kQueueCap;
+        uint32_t* q = queues + warp * kQueueCap;
         const uint32_t c0 = warp * (kWarpStarts / 16) + lane;
         const uint32_t wq = warp * (kWarpStarts / 4);
         for (uint32_t s = 0, phase = 0;;) {

@@ -295,8 +295,8 @@ struct GlobalQC {
 // every chunk are loaded once per group and serve all its compares, the
 // 4-byte-aligned ones (no shift) first.
 // Sparse phase: the 16-start chunks with a surviving start are compacted, in
-// position order, into the warp's queue q (at most 128 entries: the found
-// words, the chunk index in the low bits of the first); each lane then takes
+// position order, into the warp's queue q (at most 128 entries of one word:
+// the chunk's found bits and index); each lane then takes
 // one chunk and continues with compares r .. m-1, two per zero-byte test,
 // leaving as soon as the chunk's found flags are all zero - the early exit
 // of Algorithm 2, taken per 16-start chunk.
@@ -304,7 +304,7 @@ template <bool SEVEN, bool WRITE, bool DIRECT, class QC>
 __device__ __forceinline__ uint32_t warp_tile(const uint4* __restrict__ b4, const uint32_t* __restrict__ b32,
                                               uint32_t c0, uint32_t wq, uint32_t warp, uint32_t lane, QC qc,
                                               uint32_t m, uint32_t r, uint32_t ng, uint32_t one,
-                                              uint64_t nstarts, uint64_t s0, uint4* q,
+                                              uint64_t nstarts, uint64_t s0, uint32_t* q,
                                               uint64_t out, uint64_t* __restrict__ d_pos, uint64_t cap) {
     uint32_t f[kChunks][4];
 #pragma unroll
@@ -352,15 +352,19 @@ __device__ __forceinline__ uint32_t warp_tile(const uint4* __restrict__ b4, cons
         alive |= (uint32_t)(((f[c][0] | f[c][1]) | (f[c][2] | f[c][3])) != 0u) << (8 * c);
     if (!__any_sync(kFull, alive != 0u)) return 0;
 
-    // queue in position order: chunk 0 of all lanes, then chunk 1, ...
+    // queue in position order: chunk 0 of all lanes, then chunk 1, ...; an
+    // entry packs the chunk's 16 found bits (word i's bit 7 + 8b at bit
+    // i + 8b) and its index k (bits 4-7: k mod 16, bits 12-14: k / 16)
     const uint32_t incl = warp_incl_scan(alive, lane);
     const uint32_t tot = __shfl_sync(kFull, incl, 31);
     uint32_t qn = 0;
 #pragma unroll
     for (int c = 0; c < kChunks; ++c) {
-        if ((alive >> (8 * c)) & 1u)
-            q[qn + ((incl >> (8 * c)) & 0xFFu) - 1u] =
-                make_uint4(f[c][0] | (32u * c + lane), f[c][1], f[c][2], f[c][3]);
+        if ((alive >> (8 * c)) & 1u) {
+            const uint32_t k = 32u * c + lane;
+            q[qn + ((incl >> (8 * c)) & 0xFFu) - 1u] = ((f[c][0] >> 7) | (f[c][1] >> 6)) | ((f[c][2] >> 5) |
+                                                       (f[c][3] >> 4)) | ((k & 15u) << 4) | ((k >> 4) << 12);
+        }
         qn += (tot >> (8 * c)) & 0xFFu;
     }
     __syncwarp();
@@ -370,12 +374,10 @@ __device__ __forceinline__ uint32_t warp_tile(const uint4* __restrict__ b4, cons
         const uint32_t e = qb + lane;
         uint32_t g[4] = {0u, 0u, 0u, 0u}, k = 0;
         if (e < qn) {
-            const uint4 x = q[e];
-            k = x.x & 0x7Fu;
-            g[0] = x.x & ~0x7Fu;
-            g[1] = x.y;
-            g[2] = x.z;
-            g[3] = x.w;
+            const uint32_t x = q[e];
+            k = ((x >> 4) & 15u) | ((x >> 8) & 0x70u);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) g[i] = (x << (7 - i)) & 0x80808080u;
         }
         const uint32_t W = wq + 4u * k;   // word index of the chunk's first start
         for (uint32_t j = r; j < m && ((g[0] | g[1]) | (g[2] | g[3])); j += 2) {

@@ -70,11 +70,11 @@ inline uint32_t stage_bytes_for(uint32_t m) {
 }
 
 // Header (barriers, stage descriptors, reduction slots), the per-warp queues
-// of 16-start chunks with surviving starts (one 16-byte entry for each of
-// the warp's 128 chunks), then the stage ring.
+// of 16-start chunks with surviving starts (one 4-byte entry for each of the
+// warp's 128 chunks), then the stage ring.
 constexpr uint32_t kScanHeader = 512;
 constexpr uint32_t kQueueCap = kWarpStarts / 16;                           // entries per warp
-constexpr uint32_t kQueueBytes = kConsumerWarps * kQueueCap * 16;          // 16 KiB
+constexpr uint32_t kQueueBytes = kConsumerWarps * kQueueCap * 4;           // 4 KiB
 
 inline size_t scan_smem_bytes(uint32_t stage_bytes, uint32_t stages) {
     return kScanHeader + kQueueBytes + (size_t)stage_bytes * stages;

@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
     StageDesc* desc = reinterpret_cast<StageDesc*>(smem + 128);          // [kMaxStages]
     uint64_t* red = reinterpret_cast<uint64_t*>(smem + 256);             // [kConsumerWarps + 1]
     uint32_t* flag = reinterpret_cast<uint32_t*>(smem + 336);
-    uint4* queues = reinterpret_cast<uint4*>(smem + kScanHeader);        // [kConsumerWarps][kQueueCap]
+    uint32_t* queues = reinterpret_cast<uint32_t*>(smem + kScanHeader);        // [kConsumerWarps][kQueueCap]
     uint8_t* bufs = smem + kScanHeader + kQueueBytes;
 
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
         __syncwarp();
     } else {
         // ---------------------------------------------------------- consumers
-        uint4* q = queues + warp * kQueueCap;
+        uint32_t* q = queues + warp * kQueueCap;
         const uint32_t c0 = warp * (kWarpStarts / 16) + lane;   // lane's first 16-byte chunk in the tile
         const uint32_t wq = warp * (kWarpStarts / 4);           // warp's first word in the tile
         for (uint32_t s = 0, phase = 0;; ) {

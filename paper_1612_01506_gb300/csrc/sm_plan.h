@@ -46,7 +46,11 @@ struct PlanCosts {
     double round = 350, iter = 450, iter_per_lane = 15;
 };
 
-inline double plan_cost(const uint32_t* v, uint32_t m, const double* freq, const uint32_t* sel, uint32_t k) {
+// Modelled cost of peeling the set sel[0..k) (indices below 64; inmask has
+// their bits): the dense phase, then the zero test, the compaction and the
+// sparse rounds, which continue with the other compares in the order pi.
+inline double plan_cost(const uint32_t* v, uint32_t m, const double* freq, const uint32_t* sel, uint32_t k,
+                        uint64_t inmask) {
     const PlanCosts C;
     double cost = C.base, alive = 1.0;
     for (uint32_t a = 0; a < k; ++a) {
@@ -57,20 +61,19 @@ inline double plan_cost(const uint32_t* v, uint32_t m, const double* freq, const
     }
     if (k >= m) return cost;
     cost += C.zero_test;
-    const double p_any = 1.0 - std::pow(1.0 - alive, 2048.0);
-    const double qn = 128.0 * (1.0 - std::pow(1.0 - alive, 16.0));
+    // 1 - (1 - a)^n ~ 1 - exp(-n a): a warp-tile (2048 starts) with any
+    // survivor, and the expected number of its 16-start chunks with one
+    const double p_any = -std::expm1(-2048.0 * alive);
+    const double qn = -128.0 * std::expm1(-16.0 * alive);
+    if (p_any < 1e-6) return cost;
     cost += p_any * (C.compact + C.compact_per_chunk * qn);
     // sparse rounds: two compares per zero test, the rest in the order pi
     const double rounds = std::fmax(1.0, qn / 32.0);
     double a = alive;
     uint32_t iters = 0, i = 0;
     auto next = [&]() -> int64_t {
-        for (; i < m; ++i) {
-            bool in = false;
-            for (uint32_t b = 0; b < k; ++b) in = in || sel[b] == i;
-            if (!in) return i++;
-        }
-        return -1;
+        while (i < m && i < 64 && ((inmask >> i) & 1u)) ++i;
+        return i < m ? (int64_t)i++ : -1;
     };
     while (iters < 64) {
         const int64_t j1 = next();
@@ -78,7 +81,7 @@ inline double plan_cost(const uint32_t* v, uint32_t m, const double* freq, const
         const int64_t j2 = next();
         ++iters;
         a *= freq[j1] * (j2 >= 0 ? freq[j2] : 1.0);
-        if (j2 < 0 || 128.0 * (1.0 - std::pow(1.0 - a, 16.0)) < 0.5) break;
+        if (j2 < 0 || a < 2.44e-4) break;   // fewer than 0.5 of the 128 chunks still alive
     }
     cost += p_any * rounds * (C.round + iters * (C.iter + C.iter_per_lane * std::fmin(32.0, qn / rounds)));
     return cost;
@@ -113,7 +116,7 @@ inline uint32_t plan_dense(const uint32_t* v, uint32_t m, const double* freq, ui
         // prefixes of pi
         for (uint32_t j = 0; j < top; ++j) cand[j] = j;
         for (uint32_t r = 1; r <= top; ++r) {
-            const double c = plan_cost(v, m, freq, cand, r);
+            const double c = plan_cost(v, m, freq, cand, r, (r < 64 ? (1ull << r) : 0ull) - 1ull);
             if (c < best) {
                 best = c;
                 k = r;
@@ -122,25 +125,30 @@ inline uint32_t plan_dense(const uint32_t* v, uint32_t m, const double* freq, ui
         }
         // prefixes of the greedy order over the kPlanCandidates rarest
         const uint32_t pool = m < kPlanCandidates ? m : kPlanCandidates;
+        uint64_t inmask = 0;
+        uint32_t wins[kPlanMaxPeel], nw = 0;   // windows of the compares taken so far
+        double info[kPlanCandidates];
+        for (uint32_t j = 0; j < pool; ++j) info[j] = -std::log(std::fmax(freq[j], 1e-300));
         for (uint32_t r = 1; r <= top; ++r) {
             double best_gain = -1.0;
             uint32_t pick = 0;
             for (uint32_t j = 0; j < pool; ++j) {
-                bool in = false, loaded = false;
-                for (uint32_t a = 0; a + 1 < r; ++a) {
-                    in = in || cand[a] == j;
-                    loaded = loaded || group_e(v[cand[a]]) == group_e(v[j]);
-                }
-                if (in) continue;
+                if ((inmask >> j) & 1u) continue;
+                bool loaded = false;
+                for (uint32_t w = 0; w < nw; ++w) loaded = loaded || wins[w] == group_e(v[j]);
                 const double cost = (loaded ? 0.0 : C.window) + (aligned(v[j]) ? C.cmp_aligned : C.cmp_shifted);
-                const double gain = -std::log(std::fmax(freq[j], 1e-300)) / cost;
+                const double gain = info[j] / cost;
                 if (gain > best_gain) {
                     best_gain = gain;
                     pick = j;
                 }
             }
             cand[r - 1] = pick;
-            const double c = plan_cost(v, m, freq, cand, r);
+            inmask |= 1ull << pick;
+            bool known = false;
+            for (uint32_t w = 0; w < nw; ++w) known = known || wins[w] == group_e(v[pick]);
+            if (!known) wins[nw++] = group_e(v[pick]);
+            const double c = plan_cost(v, m, freq, cand, r, inmask);
             if (c < best) {
                 best = c;
                 k = r;
@@ -177,10 +185,11 @@ inline uint32_t plan_dense(const uint32_t* v, uint32_t m, const double* freq, ui
         if (g >= max_groups) return 0;
         groups[g++] = desc;
     }
-    // the rest in the order pi
+    // the rest in the order pi (sel holds indices below kPlanCandidates = 64)
+    uint64_t taken = 0;
+    for (uint32_t a = 0; a < r && !implicit; ++a) taken |= 1ull << sel[a];
     for (uint32_t j = 0; j < m; ++j) {
-        bool in = implicit && j < r;
-        for (uint32_t a = 0; a < r && !implicit; ++a) in = in || sel[a] == j;
+        const bool in = implicit ? j < r : (j < 64 && ((taken >> j) & 1u));
         if (!in) qc[o++] = v[j];
     }
     *ng = g;

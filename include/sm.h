@@ -134,18 +134,24 @@ sm_status sm_order_fixed(const uint8_t* h_pat, uint32_t m, int mode, uint32_t* h
  * Options for one search; NULL selects the defaults.
  *   peel       peeling factor r of Sec. 2.3 (Algorithm 4): the first r
  *              compares of every group of starts run without the zero test.
- *              0 = choose automatically. Clamped to m. Does not change the
+ *              0 = choose automatically (then the peeled compares are chosen
+ *              by a cost model, see below). Clamped to m. Does not change the
  *              result.
+ *   flags      SM_SEARCH_BYTES: compare bytes even when 2-bit codes apply.
+ *              Other bits must be 0.
  *   h_hist256  optional host histogram of THIS text (from sm_histogram). When
- *              given, it selects the automatic peel, allows a faster compare
- *              when the text has no byte >= 0x80, and returns a zero count
+ *              given, it selects the automatic peel and the peeled compares,
+ *              allows a faster compare when the text has no byte >= 0x80,
+ *              compares 2-bit codes (16 starts per 32-bit word) when the text
+ *              has at most four distinct symbols, and returns a zero count
  *              without scanning when some pattern symbol never occurs in the
  *              text. A histogram that does not belong to the text gives
  *              undefined results.
  */
+#define SM_SEARCH_BYTES 1u
 typedef struct sm_search_opts {
     uint32_t peel;
-    uint32_t reserved;
+    uint32_t flags;
     const uint64_t* h_hist256;
 } sm_search_opts;
 

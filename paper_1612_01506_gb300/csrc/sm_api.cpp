@@ -38,7 +38,7 @@ struct sm_ctx {
     uint32_t grid_override = 0;
     uint64_t spin_ns = 1000000000ull;
     uint32_t test_skip_copy = 0;
-    std::unordered_map<uint64_t, int> occ;   // (mode, seven, large m, smem) -> resident CTAs per SM
+    std::unordered_map<uint64_t, int> occ;   // (mode, kind, large m, smem) -> resident CTAs per SM
 };
 
 namespace {
@@ -110,18 +110,22 @@ sm_status check_pattern(const uint8_t* h_pat, uint32_t m, const uint32_t* h_pi) 
 }
 
 struct Plan {
-    std::vector<uint32_t> qc;       // compare descriptors in scan order (plan_dense)
+    std::vector<uint32_t> qc;       // compare descriptors in scan order (plan_dense / plan_packed)
     std::vector<uint32_t> groups;   // window groups of the peeled compares
     uint32_t r = 1;
-    bool seven = false;
+    int kind = smk::kKindBytes;
+    uint32_t b1 = 0, b2 = 0;        // packed kinds: the code bits
     bool zero = false;   // a pattern symbol never occurs in the text
 };
 
 // Compare descriptors (e << 8) | p[q], e = (text address mod 16) + q, in the
 // order pi; the text's symbol frequencies (when the caller passes its
-// histogram) pick the peeled compares.
+// histogram) pick the peeled compares and the compare kind: 2-bit codes for
+// texts of at most four symbols, the 7-bit test for texts without bytes
+// >= 0x80, else the general byte test.
 sm_status make_plan(const uint8_t* d_text, const uint8_t* p, uint32_t m, const uint32_t* pi,
                     const sm_search_opts* o, uint64_t n, Plan* pl) {
+    if (o && (o->flags & ~SM_SEARCH_BYTES)) return fail(SM_EINVAL, "unknown search flags");
     const uint32_t delta = (uint32_t)(reinterpret_cast<uintptr_t>(d_text) & 15u);
     std::vector<uint32_t> v(m);
     for (uint32_t j = 0; j < m; ++j) {
@@ -130,6 +134,7 @@ sm_status make_plan(const uint8_t* d_text, const uint8_t* p, uint32_t m, const u
     }
     const uint64_t* h = o ? o->h_hist256 : nullptr;
     std::vector<double> freq;
+    bool packed = false;
     if (h) {
         uint64_t high = 0;
         for (int c = 0x80; c < 256; ++c) high += h[c];
@@ -138,15 +143,28 @@ sm_status make_plan(const uint8_t* d_text, const uint8_t* p, uint32_t m, const u
             if (p[q] >= 0x80) pat7 = false;
             if (h[p[q]] == 0) pl->zero = true;
         }
-        pl->seven = (high == 0) && pat7;
+        pl->kind = (high == 0) && pat7 ? smk::kKindSeven : smk::kKindBytes;
         freq.resize(m);
         for (uint32_t j = 0; j < m; ++j) freq[j] = n ? (double)h[v[j] & 0xFFu] / (double)n : 1.0;
+        packed = !pl->zero && !(o->flags & SM_SEARCH_BYTES) && smk::packed_code_bits(h, &pl->b1, &pl->b2);
     }
     pl->qc.resize(m);
-    pl->groups.resize(smk::max_groups_for(m));
     uint32_t ng = 0;
-    pl->r = smk::plan_dense(v.data(), m, h ? freq.data() : nullptr, o ? o->peel : 0u, pl->qc.data(),
-                            pl->groups.data(), (uint32_t)pl->groups.size(), &ng);
+    if (packed) {
+        // every pattern symbol occurs in the text, so its code is defined
+        for (uint32_t j = 0; j < m; ++j) {
+            const uint32_t c = v[j] & 0xFFu;
+            v[j] = (v[j] & ~0xFFu) | ((c >> pl->b1) & 1u) | (((c >> pl->b2) & 1u) << 1);
+        }
+        pl->kind = pl->b2 == pl->b1 + 1 ? smk::kKindPackedAdj : smk::kKindPacked;
+        pl->groups.resize(smk::max_packed_groups_for(m));
+        pl->r = smk::plan_packed(v.data(), m, freq.data(), o->peel, pl->qc.data(), pl->groups.data(),
+                                 (uint32_t)pl->groups.size(), &ng);
+    } else {
+        pl->groups.resize(smk::max_groups_for(m));
+        pl->r = smk::plan_dense(v.data(), m, h ? freq.data() : nullptr, o ? o->peel : 0u, pl->qc.data(),
+                                pl->groups.data(), (uint32_t)pl->groups.size(), &ng);
+    }
     if (pl->r == 0) return fail(SM_EINVAL, "internal: dense plan exceeds its group capacity");
     pl->groups.resize(ng);
     return SM_OK;
@@ -158,29 +176,29 @@ struct Grid {
     size_t smem = 0;
 };
 
-int occupancy(sm_ctx* c, int mode, bool seven, uint32_t m, size_t smem) {
-    const uint64_t key = ((uint64_t)smem << 8) | ((uint64_t)mode << 2) | (seven ? 2u : 0u) |
+int occupancy(sm_ctx* c, int mode, int kind, uint32_t m, size_t smem) {
+    const uint64_t key = ((uint64_t)smem << 8) | ((uint64_t)mode << 4) | ((uint64_t)kind << 1) |
                          (m > (uint32_t)smk::kSmallM ? 1u : 0u);
     auto it = c->occ.find(key);
     if (it != c->occ.end()) return it->second;
-    const int o = smk::scan_occupancy(mode, seven, m, smem);
+    const int o = smk::scan_occupancy(mode, kind, m, smem);
     c->occ.emplace(key, o);
     return o;
 }
 
-sm_status plan_grid(sm_ctx* c, int mode, bool seven, uint32_t m, uint64_t nstarts, Grid* g) {
+sm_status plan_grid(sm_ctx* c, int mode, int kind, uint32_t m, uint64_t nstarts, Grid* g) {
     g->ntiles = (nstarts + smk::kTile - 1) / smk::kTile;
     g->stage_bytes = smk::stage_bytes_for(m);
     g->stages = c->stages;
-    while (g->stages > 2 && smk::scan_smem_bytes(g->stage_bytes, g->stages) > c->max_smem) --g->stages;
-    g->smem = smk::scan_smem_bytes(g->stage_bytes, g->stages);
+    while (g->stages > 2 && smk::scan_smem_bytes(g->stage_bytes, g->stages, kind) > c->max_smem) --g->stages;
+    g->smem = smk::scan_smem_bytes(g->stage_bytes, g->stages, kind);
     if (g->smem > c->max_smem) return fail(SM_ENOTSUP, "pattern too long for shared memory");
-    int occ = occupancy(c, mode, seven, m, g->smem);
+    int occ = occupancy(c, mode, kind, m, g->smem);
     if (occ <= 0) return fail(SM_ECUDA, "scan kernel cannot be resident (smem %zu)", g->smem);
     // one stage fewer is worth it when it lets another CTA reside on each SM
     while (!c->stages_fixed && g->stages > 2) {
-        const size_t sm2 = smk::scan_smem_bytes(g->stage_bytes, g->stages - 1);
-        const int o2 = occupancy(c, mode, seven, m, sm2);
+        const size_t sm2 = smk::scan_smem_bytes(g->stage_bytes, g->stages - 1, kind);
+        const int o2 = occupancy(c, mode, kind, m, sm2);
         if (o2 <= occ) break;
         --g->stages;
         g->smem = sm2;
@@ -205,6 +223,10 @@ smk::ScanArgs scan_args(sm_ctx* c, const uint8_t* d_text, uint64_t n, uint32_t m
     a.m = m;
     a.r = pl.r;
     a.ng = (uint32_t)pl.groups.size();
+    a.b1 = pl.b1;
+    a.b2 = pl.b2;
+    a.gather = 0x01041040u;
+    a.packed_words = smk::packed_words_for(g.stage_bytes);
     a.stage_bytes = g.stage_bytes;
     a.stages = g.stages;
     a.status = c->d_status;
@@ -414,7 +436,7 @@ static sm_status search(sm_ctx* c, const uint8_t* d_text, uint64_t n, const uint
     const uint64_t nstarts = n - m + 1;
     const int mode1 = report ? smk::kModeTileCount : smk::kModeCount;
     Grid gr;
-    st = plan_grid(c, mode1, pl.seven, m, nstarts, &gr);
+    st = plan_grid(c, mode1, pl.kind, m, nstarts, &gr);
     if (st != SM_OK) return st;
     if (report) {
         st = grow(&c->d_warp_counts, &c->warp_counts_cap, (size_t)gr.ntiles * smk::kConsumerWarps,
@@ -425,12 +447,12 @@ static sm_status search(sm_ctx* c, const uint8_t* d_text, uint64_t n, const uint
     cudaError_t e;
     if (report && (e = cudaMemsetAsync(c->d_partials, 0, sizeof(uint64_t) * gr.grid, s)) != cudaSuccess)
         return cuda_fail(e, "clearing the range counts");
-    e = smk::launch_scan(mode1, pl.seven, gr.grid, gr.smem, s, a, pl.qc.data(), pl.groups.data());
+    e = smk::launch_scan(mode1, pl.kind, gr.grid, gr.smem, s, a, pl.qc.data(), pl.groups.data());
     if (e != cudaSuccess) return cuda_fail(e, "scan launch");
     if (report) {
         a.d_pos = d_pos;
         a.cap = cap;
-        e = smk::launch_scan(smk::kModeWrite, pl.seven, gr.grid, gr.smem, s, a, pl.qc.data(), pl.groups.data());
+        e = smk::launch_scan(smk::kModeWrite, pl.kind, gr.grid, gr.smem, s, a, pl.qc.data(), pl.groups.data());
         if (e != cudaSuccess) return cuda_fail(e, "report launch");
     }
     return SM_OK;

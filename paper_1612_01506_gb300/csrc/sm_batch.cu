@@ -81,25 +81,6 @@ struct BatchDesc {
 };
 
 
-// Consumer-wide barrier (the 8 consumer warps, barrier 1) that also returns
-// whether any consumer thread passed v = true.
-__device__ __forceinline__ bool consumers_any(bool v) {
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\t"
-        "setp.ne.u32 q, %1, 0;\n\t"
-        "bar.red.or.pred p, 1, %2, q;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(r)
-        : "r"((uint32_t)v), "n"(kConsumerWarps * 32)
-        : "memory");
-    return r != 0;
-}
-
-__device__ __forceinline__ void consumers_sync() {
-    asm volatile("bar.sync 1, %0;" ::"n"(kConsumerWarps * 32) : "memory");
-}
-
 __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constant__ BatchArgs A) {
     extern __shared__ __align__(128) uint8_t smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);

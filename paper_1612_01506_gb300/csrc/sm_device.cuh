@@ -101,6 +101,25 @@ __device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity, uin
     return true;
 }
 
+// Consumer-wide barrier (the 8 consumer warps, barrier 1) that also returns
+// whether any consumer thread passed v = true.
+__device__ __forceinline__ bool consumers_any(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.or.pred p, 1, %2, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(kConsumerWarps * 32)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void consumers_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(kConsumerWarps * 32) : "memory");
+}
+
 // ------------------------------------------------------------ tile staging
 
 // One tile's copy: text bytes [s0, need_end) of a text of length n at
@@ -409,6 +428,159 @@ __device__ __forceinline__ uint32_t warp_tile(const uint4* __restrict__ b4, cons
     }
     __syncwarp();   // the queue is reused by the next tile
     return tile_count;
+}
+
+// ------------------------------------------------------------ packed texts
+
+// Texts of at most four distinct symbols are compared on 2-bit codes: a
+// symbol's code is its bits b1 and b2 (bit b1 -> code bit 0, b2 -> bit 1),
+// two bit positions where the text's symbols all differ. 16 codes fill a
+// 32-bit word, code k of packed word u being the symbol at byte 16u + k of
+// the stage buffer, in bits 2k and 2k + 1.
+//
+// The 2-bit codes of the four bytes of w, in bits 8j .. 8j + 1 of byte j.
+template <bool ADJ>
+__device__ __forceinline__ uint32_t byte_codes(uint32_t w, uint32_t b1, uint32_t b2) {
+    if (ADJ) return (w >> b1) & 0x03030303u;   // b2 == b1 + 1
+    return ((w >> b1) & 0x01010101u) | ((w >> (b2 - 1)) & 0x02020202u);
+}
+
+// 16 bytes -> one packed word. Multiplying the byte codes by gather =
+// 0x01041040 moves the code of byte j to bits 24 + 2j (the partial products
+// below bit 24 sum to less than 2^24, so nothing carries into byte 3); byte
+// permutes collect the four top bytes.
+template <bool ADJ>
+__device__ __forceinline__ uint32_t pack16(const uint4& x, uint32_t b1, uint32_t b2, uint32_t gather) {
+    const uint32_t u0 = byte_codes<ADJ>(x.x, b1, b2) * gather;
+    const uint32_t u1 = byte_codes<ADJ>(x.y, b1, b2) * gather;
+    const uint32_t u2 = byte_codes<ADJ>(x.z, b1, b2) * gather;
+    const uint32_t u3 = byte_codes<ADJ>(x.w, b1, b2) * gather;
+    return __byte_perm(__byte_perm(u0, u1, 0x7373u), __byte_perm(u2, u3, 0x7373u), 0x5410u);
+}
+
+// One compare on packed words, accumulated for the lane's 64 starts (four
+// packed words of 16 starts) in each of two tiles: y[t] |= window ^ (c..c),
+// with a[t], b[t] the lane's packed words 4E' .. 4E' + 7 past its first in
+// tile t. v = (e << 8) | code with e = text misalignment + pattern position;
+// the caller guarantees E' == e >> 6 and D == (e >> 4) & 3. ALIGNED:
+// e mod 16 == 0 (no shift).
+template <int D, bool ALIGNED>
+__device__ __forceinline__ void acc_packed(const uint4 (&a)[2], const uint4 (&b)[2], uint32_t v,
+                                           uint32_t (&y)[2][4]) {
+    const uint32_t P = (v & 3u) * 0x55555555u;
+    const uint32_t sh = ((v >> 8) & 15u) << 1;
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const uint32_t X[8] = {a[t].x, a[t].y, a[t].z, a[t].w, b[t].x, b[t].y, b[t].z, b[t].w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            y[t][i] |= (ALIGNED ? X[D + i] : __funnelshift_r(X[D + i], X[D + i + 1], sh)) ^ P;
+    }
+}
+
+// found bits (bit 2k of a packed word: start k) of the 2-bit fields of y
+// that are zero
+__device__ __forceinline__ uint32_t zero_fields(uint32_t y) { return ~(y | (y >> 1)) & 0x55555555u; }
+
+__device__ __forceinline__ uint32_t valid_fields(int64_t lim) {
+    if (lim >= 16) return 0x55555555u;
+    if (lim <= 0) return 0u;
+    return 0x55555555u & ((1u << (2 * lim)) - 1u);
+}
+
+// One consumer warp's 2048 starts in each of two staged tiles against one
+// pattern, on the packed words pk[t] of tile t (lane l's 64 starts from
+// packed word 128 warp + 4l); the second tile takes part only when `two`.
+// Same algorithm as warp_tile: the dense phase runs the r peeled compares
+// (window groups: E' in bits 0-8, aligned compare of class D at bit 9 + D,
+// number of other compares of class D in bits 13 + 4D .. 16 + 4D) and one
+// zero test; then each lane continues its surviving 16-start words through
+// compares r .. m-1 with early exit. Returns the lane's matches per tile;
+// with WRITE also writes tile t's positions in ascending order from rank
+// out[t] (first `cap` only).
+template <bool WRITE, bool DIRECT, class QC>
+__device__ __forceinline__ uint2 packed_tiles(const uint32_t* const (&pk)[2], bool two, uint32_t warp,
+                                              uint32_t lane, QC qc, uint32_t m, uint32_t r, uint32_t ng,
+                                              uint64_t nstarts, const uint64_t (&s0)[2], const uint64_t (&out)[2],
+                                              uint64_t* __restrict__ d_pos, uint64_t cap) {
+    const uint32_t w0 = warp * 128u + lane * 4u;   // lane's first packed word
+    uint32_t y[2][4] = {{0u, 0u, 0u, 0u}, {0u, 0u, 0u, 0u}};
+    for (uint32_t g = 0, j = 0; g < ng; ++g) {
+        const uint32_t gd = qc.group(g);
+        const uint32_t u = (w0 >> 2) + (gd & 0x1FFu);
+        uint4 a[2], b[2];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const uint4* p4 = reinterpret_cast<const uint4*>(pk[t]);
+            a[t] = p4[u];
+            b[t] = p4[u + 1];
+        }
+        if (gd & (1u << 9)) acc_packed<0, true>(a, b, qc(j++), y);
+        if (gd & (1u << 10)) acc_packed<1, true>(a, b, qc(j++), y);
+        if (gd & (1u << 11)) acc_packed<2, true>(a, b, qc(j++), y);
+        if (gd & (1u << 12)) acc_packed<3, true>(a, b, qc(j++), y);
+        for (uint32_t k = (gd >> 13) & 15u; k; --k) acc_packed<0, false>(a, b, qc(j++), y);
+        for (uint32_t k = (gd >> 17) & 15u; k; --k) acc_packed<1, false>(a, b, qc(j++), y);
+        for (uint32_t k = (gd >> 21) & 15u; k; --k) acc_packed<2, false>(a, b, qc(j++), y);
+        for (uint32_t k = (gd >> 25) & 15u; k; --k) acc_packed<3, false>(a, b, qc(j++), y);
+    }
+    uint32_t f[2][4];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) f[t][i] = (t == 0 || two) ? zero_fields(y[t][i]) : 0u;
+        if (s0[t] + kTile > nstarts) {   // last tile: clear starts beyond n - m
+            const int64_t lim = (int64_t)(nstarts - s0[t]) - (int64_t)(warp * kWarpStarts + lane * 64u);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) f[t][i] &= valid_fields(lim - 16 * i);
+        }
+    }
+    // surviving starts continue one compare at a time; rare when r is planned
+    uint32_t any = 0;
+#pragma unroll
+    for (int t = 0; t < 2; ++t) any |= (f[t][0] | f[t][1]) | (f[t][2] | f[t][3]);
+    if (!(DIRECT && r >= m) && __any_sync(kFull, any != 0u)) {
+        for (uint32_t j = r; j < m && any; ++j) {
+            const uint32_t v = qc(j);
+            const uint32_t e = v >> 8;
+            const uint32_t P = (v & 3u) * 0x55555555u;
+            const uint32_t sh = (e & 15u) << 1;
+            any = 0;
+#pragma unroll
+            for (int t = 0; t < 2; ++t)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if (f[t][i]) {
+                        const uint32_t W = w0 + i + (e >> 4);
+                        f[t][i] &= zero_fields(__funnelshift_r(pk[t][W], pk[t][W + 1], sh) ^ P);
+                    }
+                    any |= f[t][i];
+                }
+        }
+    }
+    uint32_t n[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) n[t] = __popc(f[t][0] | (f[t][1] << 1)) + __popc(f[t][2] | (f[t][3] << 1));
+    if (WRITE) {
+        // positions in order: lanes, then words, then starts
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const uint32_t inc = warp_incl_scan(n[t], lane);
+            uint64_t rk = out[t] + inc - n[t];
+            const uint64_t pos0 = s0[t] + warp * kWarpStarts + 64u * lane;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                uint32_t fw = f[t][i];
+                while (fw) {
+                    const uint32_t k = (uint32_t)(__ffs(fw) - 1) >> 1;
+                    if (rk < cap) d_pos[rk] = pos0 + 16u * i + k;
+                    ++rk;
+                    fw &= fw - 1;
+                }
+            }
+        }
+    }
+    return make_uint2(n[0], n[1]);
 }
 
 }  // namespace dev

@@ -21,6 +21,12 @@ constexpr int kMaxStages = 8;
 constexpr uint32_t kStatusTrunc = 1u;
 constexpr uint32_t kStatusTimeout = 2u;
 
+// Compare variants of the scan kernel: bytes (exact zero-byte test), 7-bit
+// bytes (a cheaper test), and 2-bit codes of texts with at most four
+// distinct symbols (code bits b1, b2 adjacent or not).
+enum ScanKind : int { kKindBytes = 0, kKindSeven = 1, kKindPackedAdj = 2, kKindPacked = 3, kKinds = 4 };
+inline bool kind_packed(int kind) { return kind >= kKindPackedAdj; }
+
 enum ScanMode : int {
     kModeCount = 0,      // count only: per-CTA partial counts, last CTA writes *d_count
     kModeTileCount = 1,  // as kModeCount, and per-(tile, warp) counts for a report; the partials
@@ -41,6 +47,9 @@ struct ScanArgs {
     uint32_t stages;         // pipeline depth, 2..kMaxStages
     uint32_t one;            // the value 1 (keeps an add on the multiply-add pipe)
     uint32_t ng;             // window groups of the peeled compares
+    uint32_t b1, b2;         // packed kinds: the symbol bits that form the 2-bit codes
+    uint32_t gather;         // packed kinds: 0x01041040 (see pack16)
+    uint32_t packed_words;   // packed kinds: words of one packed tile buffer
     uint32_t test_skip_copy; // test hook: 1 = never issue the first tile's copy
     uint32_t* status;        // deferred status word
     uint64_t* partials;      // counting: per-CTA counts; tile-count/write: per tile-range counts (grid entries)
@@ -76,17 +85,23 @@ constexpr uint32_t kScanHeader = 512;
 constexpr uint32_t kQueueCap = kWarpStarts / 16;                           // entries per warp
 constexpr uint32_t kQueueBytes = kConsumerWarps * kQueueCap * 4;           // 4 KiB
 
-inline size_t scan_smem_bytes(uint32_t stage_bytes, uint32_t stages) {
-    return kScanHeader + kQueueBytes + (size_t)stage_bytes * stages;
+// Packed kinds: one tile of 2-bit codes takes a word per 16-byte unit of
+// the stage buffer, plus 8 words of load slack; four such buffers (two
+// rounds of two tiles) replace the survivor queues.
+inline uint32_t packed_words_for(uint32_t stage_bytes) { return stage_bytes / 16 + 8; }
+
+inline size_t scan_smem_bytes(uint32_t stage_bytes, uint32_t stages, int kind = kKindBytes) {
+    const size_t mid = kind_packed(kind) ? (size_t)16 * packed_words_for(stage_bytes) : kQueueBytes;
+    return kScanHeader + mid + (size_t)stage_bytes * stages;
 }
 
 // Launch a scan kernel. `qc` holds the m compare descriptors (e << 8) | p[q],
 // e = (text address mod 16) + q, in scan order and `groups` the a.ng window
 // groups of the first a.r (both as planned by plan_dense).
-cudaError_t launch_scan(int mode, bool seven, uint32_t grid, size_t smem, cudaStream_t s,
+cudaError_t launch_scan(int mode, int kind, uint32_t grid, size_t smem, cudaStream_t s,
                         const ScanArgs& a, const uint32_t* qc, const uint32_t* groups);
-// Resident CTAs per SM of the scan kernel used for (m, mode, seven) with this smem.
-int scan_occupancy(int mode, bool seven, uint32_t m, size_t smem);
+// Resident CTAs per SM of the scan kernel used for (m, mode, kind) with this smem.
+int scan_occupancy(int mode, int kind, uint32_t m, size_t smem);
 // Raise the dynamic shared-memory limit of every scan kernel.
 cudaError_t scan_prepare(size_t max_smem);
 

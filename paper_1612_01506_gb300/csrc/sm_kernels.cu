@@ -55,17 +55,20 @@ struct StageDesc {
 #ifndef SMK_MIN_BLOCKS
 #define SMK_MIN_BLOCKS 3
 #endif
-template <int MAXM, int MODE, bool SEVEN>
+template <int MAXM, int MODE, int KIND>
 __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __grid_constant__ ScanArgs A,
                                                         const __grid_constant__ PatArg<MAXM> P) {
+    constexpr bool SEVEN = KIND == kKindSeven;
+    constexpr bool PACKED = KIND >= kKindPackedAdj;
     extern __shared__ __align__(128) uint8_t smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);                  // [kMaxStages]
     uint64_t* empty = reinterpret_cast<uint64_t*>(smem + 64);            // [kMaxStages]
     StageDesc* desc = reinterpret_cast<StageDesc*>(smem + 128);          // [kMaxStages]
     uint64_t* red = reinterpret_cast<uint64_t*>(smem + 256);             // [kConsumerWarps + 1]
     uint32_t* flag = reinterpret_cast<uint32_t*>(smem + 336);
-    uint32_t* queues = reinterpret_cast<uint32_t*>(smem + kScanHeader);        // [kConsumerWarps][kQueueCap]
-    uint8_t* bufs = smem + kScanHeader + kQueueBytes;
+    uint32_t* queues = reinterpret_cast<uint32_t*>(smem + kScanHeader);  // [kConsumerWarps][kQueueCap]
+    uint32_t* pbuf = reinterpret_cast<uint32_t*>(smem + kScanHeader);    // packed: [2][2][A.packed_words]
+    uint8_t* bufs = smem + kScanHeader + (PACKED ? 16u * A.packed_words : kQueueBytes);
 
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t SB = A.stage_bytes, S = A.stages, m = A.m, r = A.r, one = A.one;
@@ -168,6 +171,81 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
             for (uint32_t st = 0; st < S && st < issued; ++st)
                 (void)wait_bounded(&full[st], ((issued - 1 - st) / S) & 1u, A.spin_ns);
         __syncwarp();
+    } else if constexpr (PACKED) {
+        // ------------------------------------------- consumers, 2-bit codes
+        // Rounds of two tiles: every consumer thread packs its 16-byte units
+        // of each tile's stage into a packed buffer and releases the stage;
+        // one consumer barrier (which also agrees on leaving) makes the
+        // packed tiles visible; then each warp compares its 2048 starts of
+        // both tiles at once. The buffer pair of a round is rewritten two
+        // rounds later, after every warp has passed the next round's
+        // barrier, i.e. finished comparing.
+        constexpr bool ADJ = KIND == kKindPackedAdj;
+        const uint32_t units = SB / 16, b1 = A.b1, b2 = A.b2, gather = A.gather, PW = A.packed_words;
+        const uint32_t u0 = warp * (kWarpStarts / 16) + lane;
+        for (uint32_t s = 0, phase = 0, t = 0;; ++t) {
+            uint32_t* pw[2] = {pbuf + (t & 1u) * 2u * PW, pbuf + (t & 1u) * 2u * PW + PW};
+            StageDesc d[2] = {{kEnd, 0}, {kEnd, 0}};
+            bool ok = true;
+            uint32_t ss = s, ph = phase;
+            for (int k = 0; k < 2; ++k) {
+                ok = __all_sync(kFull, wait_bounded(&full[ss], ph, A.spin_ns));
+                if (!ok) break;
+                d[k] = desc[ss];
+                if (d[k].tile == kEnd) break;
+                const uint4* b4 = reinterpret_cast<const uint4*>(bufs + (size_t)ss * SB);
+                uint4 x[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) x[c] = b4[u0 + 32 * c];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) pw[k][u0 + 32 * c] = pack16<ADJ>(x[c], b1, b2, gather);
+                for (uint32_t u = kTile / 16 + tid; u < units; u += kConsumerWarps * 32)
+                    pw[k][u] = pack16<ADJ>(b4[u], b1, b2, gather);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[ss]);
+                if (++ss == S) {
+                    ss = 0;
+                    ph ^= 1u;
+                }
+            }
+            if (consumers_any(!ok)) {
+                if (lane == 0 && !ok) atomicOr(A.status, kStatusTimeout);
+                break;
+            }
+            if (d[0].tile == kEnd) break;
+            const bool two = d[1].tile != kEnd;
+            const uint64_t s0[2] = {d[0].tile * kTile, two ? d[1].tile * kTile : 0};
+            uint64_t out[2] = {0, 0};
+            if (MODE == kModeWrite) {
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
+                    if (k == 0 || two) {
+                        const uint32_t cw =
+                            lane < warp ? __ldcg(A.warp_counts + d[k].tile * kConsumerWarps + lane) : 0u;
+                        out[k] = d[k].offset + warp_sum_u32(cw);
+                    }
+            }
+            const uint32_t* const pk[2] = {pw[0], two ? pw[1] : pw[0]};
+            const uint2 c = packed_tiles<MODE == kModeWrite, MODE == kModeCount>(
+                pk, two, warp, lane, ParamQC<MAXM>{&P}, m, r, A.ng, A.nstarts, s0, out, A.d_pos, A.cap);
+            if (MODE == kModeTileCount) {
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    if (k == 1 && !two) break;
+                    const uint32_t wsum = warp_sum_u32(k == 0 ? c.x : c.y);
+                    if (lane == 0) {
+                        A.warp_counts[d[k].tile * kConsumerWarps + warp] = wsum;
+                        if (wsum)
+                            atomicAdd(reinterpret_cast<unsigned long long*>(A.partials) + d[k].tile / A.tiles_per_cta,
+                                      (unsigned long long)wsum);
+                    }
+                }
+            }
+            my_count += c.x + c.y;
+            if (!two) break;   // the second slot held the end mark
+            s = ss;
+            phase = ph;
+        }
     } else {
         // ---------------------------------------------------------- consumers
         uint32_t* q = queues + warp * kQueueCap;
@@ -308,7 +386,7 @@ __global__ void __launch_bounds__(kHistThreads) hist_kernel(const HistArgs A) {
 
 // ------------------------------------------------------------ dispatch
 
-template <int MAXM, int MODE, bool SEVEN>
+template <int MAXM, int MODE, int KIND>
 cudaError_t launch_one(uint32_t grid, size_t smem, cudaStream_t st, const ScanArgs& a, const uint32_t* qc,
                        const uint32_t* groups) {
     if (a.ng > (uint32_t)PatArg<MAXM>::kGroups) return cudaErrorInvalidValue;
@@ -318,55 +396,75 @@ cudaError_t launch_one(uint32_t grid, size_t smem, cudaStream_t st, const ScanAr
     for (; j < (uint32_t)MAXM; ++j) p.qc[j] = 0;
     for (j = 0; j < a.ng; ++j) p.grp[j] = groups[j];
     for (; j < (uint32_t)PatArg<MAXM>::kGroups; ++j) p.grp[j] = 0;
-    scan_kernel<MAXM, MODE, SEVEN><<<grid, kThreads, smem, st>>>(a, p);
+    scan_kernel<MAXM, MODE, KIND><<<grid, kThreads, smem, st>>>(a, p);
     return cudaGetLastError();
 }
 
-template <int MODE, bool SEVEN>
-const void* kernel_ptr(uint32_t m) {
-    if (m <= (uint32_t)kSmallM) return reinterpret_cast<const void*>(&scan_kernel<kSmallM, MODE, SEVEN>);
-    return reinterpret_cast<const void*>(&scan_kernel<kLargeM, MODE, SEVEN>);
+template <int MAXM, int MODE>
+cudaError_t launch_kind(int kind, uint32_t grid, size_t smem, cudaStream_t st, const ScanArgs& a, const uint32_t* qc,
+                        const uint32_t* groups) {
+    switch (kind) {
+        case kKindBytes: return launch_one<MAXM, MODE, kKindBytes>(grid, smem, st, a, qc, groups);
+        case kKindSeven: return launch_one<MAXM, MODE, kKindSeven>(grid, smem, st, a, qc, groups);
+        case kKindPackedAdj: return launch_one<MAXM, MODE, kKindPackedAdj>(grid, smem, st, a, qc, groups);
+        default: return launch_one<MAXM, MODE, kKindPacked>(grid, smem, st, a, qc, groups);
+    }
 }
 
-const void* pick(int mode, bool seven, uint32_t m) {
+template <int MODE, int KIND>
+const void* kernel_ptr(uint32_t m) {
+    if (m <= (uint32_t)kSmallM) return reinterpret_cast<const void*>(&scan_kernel<kSmallM, MODE, KIND>);
+    return reinterpret_cast<const void*>(&scan_kernel<kLargeM, MODE, KIND>);
+}
+
+template <int MODE>
+const void* pick_kind(int kind, uint32_t m) {
+    switch (kind) {
+        case kKindBytes: return kernel_ptr<MODE, kKindBytes>(m);
+        case kKindSeven: return kernel_ptr<MODE, kKindSeven>(m);
+        case kKindPackedAdj: return kernel_ptr<MODE, kKindPackedAdj>(m);
+        default: return kernel_ptr<MODE, kKindPacked>(m);
+    }
+}
+
+const void* pick(int mode, int kind, uint32_t m) {
     switch (mode) {
-        case kModeCount: return seven ? kernel_ptr<kModeCount, true>(m) : kernel_ptr<kModeCount, false>(m);
-        case kModeTileCount:
-            return seven ? kernel_ptr<kModeTileCount, true>(m) : kernel_ptr<kModeTileCount, false>(m);
-        default: return seven ? kernel_ptr<kModeWrite, true>(m) : kernel_ptr<kModeWrite, false>(m);
+        case kModeCount: return pick_kind<kModeCount>(kind, m);
+        case kModeTileCount: return pick_kind<kModeTileCount>(kind, m);
+        default: return pick_kind<kModeWrite>(kind, m);
     }
 }
 
 }  // namespace
 
-cudaError_t launch_scan(int mode, bool seven, uint32_t grid, size_t smem, cudaStream_t s, const ScanArgs& a,
+cudaError_t launch_scan(int mode, int kind, uint32_t grid, size_t smem, cudaStream_t s, const ScanArgs& a,
                         const uint32_t* qc, const uint32_t* groups) {
     const bool small = a.m <= (uint32_t)kSmallM;
-#define SMK_LAUNCH(MODE)                                                                            \
-    if (small) return seven ? launch_one<kSmallM, MODE, true>(grid, smem, s, a, qc, groups)                 \
-                            : launch_one<kSmallM, MODE, false>(grid, smem, s, a, qc, groups);              \
-    return seven ? launch_one<kLargeM, MODE, true>(grid, smem, s, a, qc, groups)                            \
-                 : launch_one<kLargeM, MODE, false>(grid, smem, s, a, qc, groups);
     switch (mode) {
-        case kModeCount: SMK_LAUNCH(kModeCount)
-        case kModeTileCount: SMK_LAUNCH(kModeTileCount)
-        default: SMK_LAUNCH(kModeWrite)
+        case kModeCount:
+            return small ? launch_kind<kSmallM, kModeCount>(kind, grid, smem, s, a, qc, groups)
+                         : launch_kind<kLargeM, kModeCount>(kind, grid, smem, s, a, qc, groups);
+        case kModeTileCount:
+            return small ? launch_kind<kSmallM, kModeTileCount>(kind, grid, smem, s, a, qc, groups)
+                         : launch_kind<kLargeM, kModeTileCount>(kind, grid, smem, s, a, qc, groups);
+        default:
+            return small ? launch_kind<kSmallM, kModeWrite>(kind, grid, smem, s, a, qc, groups)
+                         : launch_kind<kLargeM, kModeWrite>(kind, grid, smem, s, a, qc, groups);
     }
-#undef SMK_LAUNCH
 }
 
-int scan_occupancy(int mode, bool seven, uint32_t m, size_t smem) {
+int scan_occupancy(int mode, int kind, uint32_t m, size_t smem) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pick(mode, seven, m), kThreads, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pick(mode, kind, m), kThreads, smem) != cudaSuccess)
         return 0;
     return nb;
 }
 
 cudaError_t scan_prepare(size_t max_smem) {
     for (int mode = 0; mode < 3; ++mode)
-        for (int sv = 0; sv < 2; ++sv)
+        for (int kind = 0; kind < kKinds; ++kind)
             for (uint32_t m : {1u, (uint32_t)kLargeM}) {
-                cudaError_t e = cudaFuncSetAttribute(pick(mode, sv != 0, m),
+                cudaError_t e = cudaFuncSetAttribute(pick(mode, kind, m),
                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
                 if (e != cudaSuccess) return e;
             }

@@ -113,7 +113,7 @@ extern "C" sm_status sm_report_noalloc(const uint8_t* d_text, uint64_t n, const 
     while (a.stages > 2 && smk::scan_smem_bytes(a.stage_bytes, a.stages) > su.max_smem) --a.stages;
     const size_t smem = smk::scan_smem_bytes(a.stage_bytes, a.stages);
     if (smem > su.max_smem) return SM_ENOTSUP;
-    const int occ = smk::scan_occupancy(smk::kModeTileCount, false, m, smem);
+    const int occ = smk::scan_occupancy(smk::kModeTileCount, smk::kKindBytes, m, smem);
     if (occ <= 0) return SM_ECUDA;
     uint64_t want = (uint64_t)su.num_sms * (uint64_t)occ;
     if (want > kMaxCtas) want = kMaxCtas;
@@ -132,9 +132,9 @@ extern "C" sm_status sm_report_noalloc(const uint8_t* d_text, uint64_t n, const 
     // the array keeps the previous call's contents: clear status, ticket,
     // tile counter and the range counts
     if (cudaMemsetAsync(su.scratch, 0, kPartialsOff + sizeof(uint64_t) * grid, s) != cudaSuccess) return SM_ECUDA;
-    if (smk::launch_scan(smk::kModeTileCount, false, grid, smem, s, a, qc, groups) != cudaSuccess) return SM_ECUDA;
+    if (smk::launch_scan(smk::kModeTileCount, smk::kKindBytes, grid, smem, s, a, qc, groups) != cudaSuccess) return SM_ECUDA;
     a.d_pos = d_pos;
     a.cap = cap;
-    if (smk::launch_scan(smk::kModeWrite, false, grid, smem, s, a, qc, groups) != cudaSuccess) return SM_ECUDA;
+    if (smk::launch_scan(smk::kModeWrite, smk::kKindBytes, grid, smem, s, a, qc, groups) != cudaSuccess) return SM_ECUDA;
     return SM_OK;
 }

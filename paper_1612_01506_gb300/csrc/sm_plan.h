@@ -196,4 +196,90 @@ inline uint32_t plan_dense(const uint32_t* v, uint32_t m, const double* freq, ui
     return r;
 }
 
+// ------------------------------------------------------------ packed texts
+
+// Bit positions b1 < b2 at which the text's symbols (at most four; hist has
+// 256 bins) all differ, so that (bit b1, bit b2) is an injective 2-bit code.
+// Prefers adjacent positions. False when the text has more than four
+// symbols or no such pair exists.
+inline bool packed_code_bits(const uint64_t* hist, uint32_t* b1, uint32_t* b2) {
+    uint32_t sym[4], ns = 0;
+    for (uint32_t c = 0; c < 256; ++c)
+        if (hist[c]) {
+            if (ns == 4) return false;
+            sym[ns++] = c;
+        }
+    if (ns == 0) return false;
+    for (uint32_t pass = 0; pass < 2; ++pass)
+        for (uint32_t x = 0; x < 8; ++x)
+            for (uint32_t z = x + 1; z < 8; ++z) {
+                if ((pass == 0) != (z == x + 1)) continue;
+                uint32_t seen = 0;
+                bool ok = true;
+                for (uint32_t i = 0; i < ns && ok; ++i) {
+                    const uint32_t code = ((sym[i] >> x) & 1u) | (((sym[i] >> z) & 1u) << 1);
+                    ok = !((seen >> code) & 1u);
+                    seen |= 1u << code;
+                }
+                if (ok) {
+                    *b1 = x;
+                    *b2 = z;
+                    return true;
+                }
+            }
+    return false;
+}
+
+// Packed group descriptor: window E' = e >> 6 (four packed words) in bits
+// 0-8; bit 9 + D set when the group has the compare of class D = (e >> 4) & 3
+// with e mod 16 == 0 (no shift); bits 13 + 4D .. 16 + 4D the number (0..15)
+// of its other compares of class D.
+constexpr uint32_t max_packed_groups_for(uint32_t m) { return (14 + m) / 64 + 1; }
+
+// Plans the dense phase on 2-bit codes. v[j] = (e << 8) | code in the order
+// pi, freq[j] the text frequency of its symbol (nullptr: unknown). A packed
+// compare costs a few integer instructions per 16 starts, so the first
+// compares of pi are peeled until fewer than 1e-5 of the starts are
+// expected to survive (or all m; r_fixed > 0 peels r_fixed). Output as for
+// plan_dense, with packed group descriptors.
+inline uint32_t plan_packed(const uint32_t* v, uint32_t m, const double* freq, uint32_t r_fixed, uint32_t* qc,
+                            uint32_t* groups, uint32_t max_groups, uint32_t* ng) {
+    uint32_t r = 0;
+    if (r_fixed) {
+        r = r_fixed < m ? r_fixed : m;
+    } else if (!freq) {
+        r = m < 16 ? m : 16;
+    } else {
+        double alive = 1.0;
+        while (r < m && r < 64 && (r < 2 || alive >= 1e-5)) alive *= freq[r++];
+    }
+    auto win = [](uint32_t x) { return x >> 14; };               // e >> 6
+    auto cls = [](uint32_t x) { return (x >> 12) & 3u; };        // (e >> 4) & 3
+    auto unshifted = [](uint32_t x) { return ((x >> 8) & 15u) == 0; };
+    uint32_t o = 0, g = 0;
+    int64_t prev = -1;
+    while (o < r) {
+        uint32_t E = ~0u;
+        for (uint32_t a = 0; a < r; ++a)
+            if ((int64_t)win(v[a]) > prev && win(v[a]) < E) E = win(v[a]);
+        prev = E;
+        uint32_t desc = E;
+        for (uint32_t pass = 0; pass < 2; ++pass)
+            for (uint32_t d = 0; d < 4; ++d) {
+                uint32_t cnt = 0;
+                for (uint32_t a = 0; a < r; ++a)
+                    if (win(v[a]) == E && cls(v[a]) == d && unshifted(v[a]) == (pass == 0)) {
+                        qc[o++] = v[a];
+                        ++cnt;
+                    }
+                desc |= pass == 0 ? (cnt << (9 + d)) : (cnt << (13 + 4 * d));
+            }
+        if (g >= max_groups) return 0;
+        groups[g++] = desc;
+    }
+    for (uint32_t j = r; j < m; ++j) qc[o++] = v[j];
+    *ng = g;
+    return r;
+}
+
 }  // namespace smk

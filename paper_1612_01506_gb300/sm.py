@@ -36,8 +36,11 @@ class SmError(RuntimeError):
         self.status = status
 
 
+SM_SEARCH_BYTES = 1
+
+
 class SearchOpts(C.Structure):
-    _fields_ = [("peel", C.c_uint32), ("reserved", C.c_uint32), ("h_hist256", C.POINTER(C.c_uint64))]
+    _fields_ = [("peel", C.c_uint32), ("flags", C.c_uint32), ("h_hist256", C.POINTER(C.c_uint64))]
 
 
 _lib = None
@@ -187,11 +190,12 @@ def sm_order_fixed(pattern, mode: int) -> np.ndarray:
     return pi[: p.size]
 
 
-def _opts(peel: int, hist):
-    if not peel and hist is None:
+def _opts(peel: int, hist, bytes_only: bool = False):
+    if not peel and hist is None and not bytes_only:
         return None, None
     h = None if hist is None else np.ascontiguousarray(hist, dtype=np.uint64)
-    o = SearchOpts(peel, 0, h.ctypes.data_as(C.POINTER(C.c_uint64)) if h is not None else None)
+    o = SearchOpts(peel, SM_SEARCH_BYTES if bytes_only else 0,
+                   h.ctypes.data_as(C.POINTER(C.c_uint64)) if h is not None else None)
     return o, h
 
 
@@ -204,14 +208,17 @@ def _pi(pi, m):
     return a.ctypes.data_as(C.POINTER(C.c_uint32)), a
 
 
-def sm_count(ctx: Ctx, text, pattern, pi=None, out=None, stream=None, peel: int = 0, hist=None):
-    """Enqueue a count; returns the 1-element int64 device tensor it writes."""
+def sm_count(ctx: Ctx, text, pattern, pi=None, out=None, stream=None, peel: int = 0, hist=None,
+             bytes_only: bool = False):
+    """Enqueue a count; returns the 1-element int64 device tensor it writes.
+    bytes_only: compare bytes even where the 2-bit codes of a text of at most
+    four symbols apply (SM_SEARCH_BYTES)."""
     import torch
     p = _bytes(pattern)
     if out is None:
         out = torch.empty(1, dtype=torch.int64, device=text.device)
     pip, _keep_pi = _pi(pi, p.size)
-    o, _keep_h = _opts(peel, hist)
+    o, _keep_h = _opts(peel, hist, bytes_only)
     lib = load()
     if o is None:
         st = lib.sm_count(ctx.handle, _dev_ptr(text, ("torch.uint8",)), text.numel(), _u8p(p), p.size, pip,
@@ -224,7 +231,7 @@ def sm_count(ctx: Ctx, text, pattern, pi=None, out=None, stream=None, peel: int 
 
 
 def sm_report(ctx: Ctx, text, pattern, cap: int, pi=None, out_pos=None, out_count=None, stream=None,
-              peel: int = 0, hist=None):
+              peel: int = 0, hist=None, bytes_only: bool = False):
     """Enqueue a report; returns (positions int64[cap], count int64[1]) device tensors."""
     import torch
     p = _bytes(pattern)
@@ -233,7 +240,7 @@ def sm_report(ctx: Ctx, text, pattern, cap: int, pi=None, out_pos=None, out_coun
     if out_count is None:
         out_count = torch.empty(1, dtype=torch.int64, device=text.device)
     pip, _keep_pi = _pi(pi, p.size)
-    o, _keep_h = _opts(peel, hist)
+    o, _keep_h = _opts(peel, hist, bytes_only)
     lib = load()
     if o is None:
         st = lib.sm_report(ctx.handle, _dev_ptr(text, ("torch.uint8",)), text.numel(), _u8p(p), p.size, pip,

@@ -318,7 +318,12 @@ struct GlobalQC {
 // the chunk's found bits and index); each lane then takes
 // one chunk and continues with compares r .. m-1, two per zero-byte test,
 // leaving as soon as the chunk's found flags are all zero - the early exit
-// of Algorithm 2, taken per 16-start chunk.
+// of Algorithm 2, taken per 16-start chunk. A chunk still alive after
+// kLaneCompares compares is finished by the whole warp.
+// Compares a lane takes alone in the sparse phase before the warp shares
+// the rest of a surviving chunk.
+constexpr uint32_t kLaneCompares = 16;
+
 template <bool SEVEN, bool WRITE, bool DIRECT, class QC>
 __device__ __forceinline__ uint32_t warp_tile(const uint4* __restrict__ b4, const uint32_t* __restrict__ b32,
                                               uint32_t c0, uint32_t wq, uint32_t warp, uint32_t lane, QC qc,
@@ -399,12 +404,32 @@ __device__ __forceinline__ uint32_t warp_tile(const uint4* __restrict__ b4, cons
             for (int i = 0; i < 4; ++i) g[i] = (x << (7 - i)) & 0x80808080u;
         }
         const uint32_t W = wq + 4u * k;   // word index of the chunk's first start
-        for (uint32_t j = r; j < m && ((g[0] | g[1]) | (g[2] | g[3])); j += 2) {
+        const uint32_t jl = min(m, r + kLaneCompares);
+        for (uint32_t j = r; j < jl && ((g[0] | g[1]) | (g[2] | g[3])); j += 2) {
             uint32_t y[4] = {0u, 0u, 0u, 0u};
             acc_window(b32, W, qc(j), y);
             acc_window(b32, W, qc(min(j + 1, m - 1)), y);   // an odd tail repeats compare j
 #pragma unroll
             for (int i = 0; i < 4; ++i) g[i] = keep_zero<SEVEN>(g[i], y[i], one);
+        }
+        // chunks still alive after kLaneCompares compares (long patterns that
+        // match or nearly match): the whole warp takes the remaining
+        // compares of one chunk at a time, lane l every 32nd from jl + l,
+        // and ANDs the found bits across lanes
+        uint32_t pend = __ballot_sync(kFull, jl < m && ((g[0] | g[1]) | (g[2] | g[3])) != 0u);
+        while (pend) {
+            const uint32_t src = (uint32_t)__ffs(pend) - 1u;
+            pend &= pend - 1u;
+            const uint32_t Ws = __shfl_sync(kFull, W, src);
+            uint32_t y[4] = {0u, 0u, 0u, 0u};
+            for (uint32_t j = jl + lane; j < m; j += 32) acc_window(b32, Ws, qc(j), y);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                uint32_t t = keep_zero<SEVEN>(0x80808080u, y[i], one);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) t &= __shfl_xor_sync(kFull, t, o);
+                if (lane == src) g[i] &= t;
+            }
         }
         const uint32_t n = (__popc(g[0]) + __popc(g[1])) + (__popc(g[2]) + __popc(g[3]));
         if (WRITE) {
@@ -540,7 +565,8 @@ __device__ __forceinline__ uint2 packed_tiles(const uint32_t* const (&pk)[2], bo
 #pragma unroll
     for (int t = 0; t < 2; ++t) any |= (f[t][0] | f[t][1]) | (f[t][2] | f[t][3]);
     if (!(DIRECT && r >= m) && __any_sync(kFull, any != 0u)) {
-        for (uint32_t j = r; j < m && any; ++j) {
+        const uint32_t jl = min(m, r + kLaneCompares);
+        for (uint32_t j = r; j < jl && any; ++j) {
             const uint32_t v = qc(j);
             const uint32_t e = v >> 8;
             const uint32_t P = (v & 3u) * 0x55555555u;
@@ -557,6 +583,30 @@ __device__ __forceinline__ uint2 packed_tiles(const uint32_t* const (&pk)[2], bo
                     any |= f[t][i];
                 }
         }
+        // words still alive: the whole warp takes the remaining compares of
+        // one word at a time (lane l every 32nd from jl + l) and ANDs
+#pragma unroll
+        for (int t = 0; t < 2; ++t)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                uint32_t pend = __ballot_sync(kFull, jl < m && f[t][i] != 0u);
+                while (pend) {
+                    const uint32_t src = (uint32_t)__ffs(pend) - 1u;
+                    pend &= pend - 1u;
+                    const uint32_t ws = __shfl_sync(kFull, w0, src) + i;
+                    uint32_t y = 0;
+                    for (uint32_t j = jl + lane; j < m; j += 32) {
+                        const uint32_t v = qc(j);
+                        const uint32_t e = v >> 8;
+                        const uint32_t W = ws + (e >> 4);
+                        y |= __funnelshift_r(pk[t][W], pk[t][W + 1], (e & 15u) << 1) ^ ((v & 3u) * 0x55555555u);
+                    }
+                    uint32_t keep = zero_fields(y);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) keep &= __shfl_xor_sync(kFull, keep, o);
+                    if (lane == src) f[t][i] &= keep;
+                }
+            }
     }
     uint32_t n[2];
 #pragma unroll

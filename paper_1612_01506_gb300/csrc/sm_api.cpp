@@ -33,6 +33,8 @@ struct sm_ctx {
     size_t partials_cap = 0;          // entries
     uint32_t* d_warp_counts = nullptr;
     size_t warp_counts_cap = 0;       // entries
+    uint32_t* d_bitmaps = nullptr;    // report: per-(tile, warp) found bitmaps
+    size_t bitmaps_cap = 0;           // words
     uint32_t stages = 4;
     bool stages_fixed = false;        // set by SM_KNOB_STAGES; otherwise fewer stages may raise occupancy
     uint32_t grid_override = 0;
@@ -186,18 +188,18 @@ int occupancy(sm_ctx* c, int mode, int kind, uint32_t m, size_t smem) {
     return o;
 }
 
-sm_status plan_grid(sm_ctx* c, int mode, int kind, uint32_t m, uint64_t nstarts, Grid* g) {
+sm_status plan_grid(sm_ctx* c, int mode, int kind, bool report, uint32_t m, uint64_t nstarts, Grid* g) {
     g->ntiles = (nstarts + smk::kTile - 1) / smk::kTile;
     g->stage_bytes = smk::stage_bytes_for(m);
     g->stages = c->stages;
-    while (g->stages > 2 && smk::scan_smem_bytes(g->stage_bytes, g->stages, kind) > c->max_smem) --g->stages;
-    g->smem = smk::scan_smem_bytes(g->stage_bytes, g->stages, kind);
+    while (g->stages > 2 && smk::scan_smem_bytes(g->stage_bytes, g->stages, kind, report) > c->max_smem) --g->stages;
+    g->smem = smk::scan_smem_bytes(g->stage_bytes, g->stages, kind, report);
     if (g->smem > c->max_smem) return fail(SM_ENOTSUP, "pattern too long for shared memory");
     int occ = occupancy(c, mode, kind, m, g->smem);
     if (occ <= 0) return fail(SM_ECUDA, "scan kernel cannot be resident (smem %zu)", g->smem);
     // one stage fewer is worth it when it lets another CTA reside on each SM
     while (!c->stages_fixed && g->stages > 2) {
-        const size_t sm2 = smk::scan_smem_bytes(g->stage_bytes, g->stages - 1, kind);
+        const size_t sm2 = smk::scan_smem_bytes(g->stage_bytes, g->stages - 1, kind, report);
         const int o2 = occupancy(c, mode, kind, m, sm2);
         if (o2 <= occ) break;
         --g->stages;
@@ -319,6 +321,7 @@ void sm_destroy(sm_ctx* c) {
     if (c->h_status) cudaFreeHost(c->h_status);
     if (c->d_partials) cudaFree(c->d_partials);
     if (c->d_warp_counts) cudaFree(c->d_warp_counts);
+    if (c->d_bitmaps) cudaFree(c->d_bitmaps);
     delete c;
 }
 
@@ -436,23 +439,38 @@ static sm_status search(sm_ctx* c, const uint8_t* d_text, uint64_t n, const uint
     const uint64_t nstarts = n - m + 1;
     const int mode1 = report ? smk::kModeTileCount : smk::kModeCount;
     Grid gr;
-    st = plan_grid(c, mode1, pl.kind, m, nstarts, &gr);
+    st = plan_grid(c, mode1, pl.kind, report, m, nstarts, &gr);
     if (st != SM_OK) return st;
     if (report) {
         st = grow(&c->d_warp_counts, &c->warp_counts_cap, (size_t)gr.ntiles * smk::kConsumerWarps,
                   "per-warp tile counts");
         if (st != SM_OK) return st;
+        st = grow(&c->d_bitmaps, &c->bitmaps_cap, (size_t)gr.ntiles * smk::kConsumerWarps * smk::kBitmapWords,
+                  "found bitmaps");
+        if (st != SM_OK) return st;
     }
     smk::ScanArgs a = scan_args(c, d_text, n, m, pl, gr, d_count);
     cudaError_t e;
-    if (report && (e = cudaMemsetAsync(c->d_partials, 0, sizeof(uint64_t) * gr.grid, s)) != cudaSuccess)
-        return cuda_fail(e, "clearing the range counts");
+    if (report) {
+        // a report: the tile-count pass (per-range counts, per-warp-tile
+        // counts and found bitmaps), then the positions from the bitmaps
+        if ((e = cudaMemsetAsync(c->d_partials, 0, sizeof(uint64_t) * gr.grid, s)) != cudaSuccess)
+            return cuda_fail(e, "clearing the range counts");
+        a.bitmaps = c->d_bitmaps;
+    }
     e = smk::launch_scan(mode1, pl.kind, gr.grid, gr.smem, s, a, pl.qc.data(), pl.groups.data());
     if (e != cudaSuccess) return cuda_fail(e, "scan launch");
     if (report) {
-        a.d_pos = d_pos;
-        a.cap = cap;
-        e = smk::launch_scan(smk::kModeWrite, pl.kind, gr.grid, gr.smem, s, a, pl.qc.data(), pl.groups.data());
+        smk::WriteArgs w{};
+        w.ntiles = gr.ntiles;
+        w.tiles_per_cta = gr.per_cta;
+        w.partials = c->d_partials;
+        w.warp_counts = c->d_warp_counts;
+        w.bitmaps = c->d_bitmaps;
+        w.d_pos = d_pos;
+        w.cap = cap;
+        w.status = c->d_status;
+        e = smk::launch_bitmap_write(gr.grid, s, w);
         if (e != cudaSuccess) return cuda_fail(e, "report launch");
     }
     return SM_OK;

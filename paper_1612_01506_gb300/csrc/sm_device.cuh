@@ -284,6 +284,35 @@ struct PatArg {
     uint32_t grp[kGroups];    // window groups of the peeled compares
 };
 
+// Stores one batch of a warp's match positions in rank order. The lane's n
+// positions have ranks excl .. excl + n - 1 of the batch's tot and are
+// base + rel; for_each(cb) calls cb(k, rel) for the lane's k-th position in
+// ascending order. Positions pass through the warp's staging area stg
+// (kStageCap words) slice by slice, so that consecutive lanes store
+// consecutive ranks. Ranks at or beyond cap (counted from the batch's first
+// rank `out`) are dropped.
+constexpr uint32_t kStageCap = 256;
+
+template <class ForEach>
+__device__ __forceinline__ void staged_write(uint32_t* stg, uint32_t lane, uint32_t excl, uint32_t n, uint32_t tot,
+                                             uint64_t base, uint64_t out, uint64_t* __restrict__ d_pos,
+                                             uint64_t cap, ForEach for_each) {
+    for (uint32_t p0 = 0; p0 < tot; p0 += kStageCap) {
+        if (n && excl < p0 + kStageCap && excl + n > p0)
+            for_each([&](uint32_t k, uint32_t rel) {
+                const uint32_t rk = excl + k - p0;   // wraps to a large value below the slice
+                if (rk < kStageCap) stg[rk] = rel;
+            });
+        __syncwarp();
+        const uint32_t cnt = min(kStageCap, tot - p0);
+        for (uint32_t o = lane; o < cnt; o += 32) {
+            const uint64_t g = out + p0 + o;
+            if (g < cap) d_pos[g] = base + stg[o];
+        }
+        __syncwarp();
+    }
+}
+
 // ------------------------------------------------------------ one warp-tile
 
 // Compare descriptors and window groups held in the kernel's parameter block.
@@ -308,6 +337,9 @@ struct GlobalQC {
 // start s0) are out of range. Returns this lane's number of matches; with
 // WRITE, also writes the positions in ascending order from rank `out`
 // (first `cap` only). DIRECT: a count may skip the compaction when r >= m.
+// bm (tile-count pass of a report): when the warp-tile has matches, its
+// 2048 found bits in start order are stored to bm (64 words), built in the
+// warp's shared scratch sbm (64 words).
 //
 // Dense phase: the r peeled compares for all 2048 starts, folded into one
 // zero-byte test. They arrive in ng window groups: the two 16-byte units of
@@ -329,7 +361,8 @@ __device__ __forceinline__ uint32_t warp_tile(const uint4* __restrict__ b4, cons
                                               uint32_t c0, uint32_t wq, uint32_t warp, uint32_t lane, QC qc,
                                               uint32_t m, uint32_t r, uint32_t ng, uint32_t one,
                                               uint64_t nstarts, uint64_t s0, uint32_t* q,
-                                              uint64_t out, uint64_t* __restrict__ d_pos, uint64_t cap) {
+                                              uint64_t out, uint64_t* __restrict__ d_pos, uint64_t cap,
+                                              uint32_t* __restrict__ bm = nullptr, uint32_t* sbm = nullptr) {
     uint32_t f[kChunks][4];
 #pragma unroll
     for (int c = 0; c < kChunks; ++c)
@@ -391,6 +424,10 @@ __device__ __forceinline__ uint32_t warp_tile(const uint4* __restrict__ b4, cons
         }
         qn += (tot >> (8 * c)) & 0xFFu;
     }
+    if (bm) {   // the warp-tile's found bitmap, one 16-bit mask per chunk, starts at zero
+        sbm[2 * lane] = 0u;
+        sbm[2 * lane + 1] = 0u;
+    }
     __syncwarp();
 
     uint32_t tile_count = 0;   // this lane's share of the warp's matches in the tile
@@ -432,6 +469,13 @@ __device__ __forceinline__ uint32_t warp_tile(const uint4* __restrict__ b4, cons
             }
         }
         const uint32_t n = (__popc(g[0]) + __popc(g[1])) + (__popc(g[2]) + __popc(g[3]));
+        if (bm && n) {
+            // chunk k's 16 found bits in start order (start 4i + b: word i, byte b)
+            uint32_t m16 = 0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) m16 |= ((((g[i] >> 7) & 0x01010101u) * 0x01020408u) >> 24) << (4 * i);
+            reinterpret_cast<uint16_t*>(sbm)[k] = (uint16_t)m16;
+        }
         if (WRITE) {
             const uint32_t inc = warp_incl_scan(n, lane);
             uint64_t rk = out + inc - n;
@@ -452,6 +496,10 @@ __device__ __forceinline__ uint32_t warp_tile(const uint4* __restrict__ b4, cons
         }
     }
     __syncwarp();   // the queue is reused by the next tile
+    if (bm && warp_sum_u32(tile_count)) {   // store the bitmap of a warp-tile with matches
+        bm[2 * lane] = sbm[2 * lane];
+        bm[2 * lane + 1] = sbm[2 * lane + 1];
+    }
     return tile_count;
 }
 
@@ -503,6 +551,15 @@ __device__ __forceinline__ void acc_packed(const uint4 (&a)[2], const uint4 (&b)
     }
 }
 
+// bit 2k of x -> bit k (k = 0..15)
+__device__ __forceinline__ uint32_t compress_even(uint32_t x) {
+    x &= 0x55555555u;
+    x = (x | (x >> 1)) & 0x33333333u;
+    x = (x | (x >> 2)) & 0x0F0F0F0Fu;
+    x = (x | (x >> 4)) & 0x00FF00FFu;
+    return (x | (x >> 8)) & 0x0000FFFFu;
+}
+
 // found bits (bit 2k of a packed word: start k) of the 2-bit fields of y
 // that are zero
 __device__ __forceinline__ uint32_t zero_fields(uint32_t y) { return ~(y | (y >> 1)) & 0x55555555u; }
@@ -522,12 +579,15 @@ __device__ __forceinline__ uint32_t valid_fields(int64_t lim) {
 // zero test; then each lane continues its surviving 16-start words through
 // compares r .. m-1 with early exit. Returns the lane's matches per tile;
 // with WRITE also writes tile t's positions in ascending order from rank
-// out[t] (first `cap` only).
+// out[t] (first `cap` only). bm[t] (tile-count pass of a report): when the
+// warp-tile of tile t has matches, its found bitmap (64 words, start order)
+// is stored there.
 template <bool WRITE, bool DIRECT, class QC>
 __device__ __forceinline__ uint2 packed_tiles(const uint32_t* const (&pk)[2], bool two, uint32_t warp,
                                               uint32_t lane, QC qc, uint32_t m, uint32_t r, uint32_t ng,
                                               uint64_t nstarts, const uint64_t (&s0)[2], const uint64_t (&out)[2],
-                                              uint64_t* __restrict__ d_pos, uint64_t cap) {
+                                              uint64_t* __restrict__ d_pos, uint64_t cap,
+                                              uint32_t* const (&bm)[2]) {
     const uint32_t w0 = warp * 128u + lane * 4u;   // lane's first packed word
     uint32_t y[2][4] = {{0u, 0u, 0u, 0u}, {0u, 0u, 0u, 0u}};
     for (uint32_t g = 0, j = 0; g < ng; ++g) {
@@ -611,6 +671,17 @@ __device__ __forceinline__ uint2 packed_tiles(const uint32_t* const (&pk)[2], bo
     uint32_t n[2];
 #pragma unroll
     for (int t = 0; t < 2; ++t) n[t] = __popc(f[t][0] | (f[t][1] << 1)) + __popc(f[t][2] | (f[t][3] << 1));
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+        if (bm[t] && warp_sum_u32(n[t])) {
+            // the warp-tile's found bitmap in start order: lane l's 64 starts
+            // are words 2l, 2l + 1 (found bit 2k of a packed word -> bit k)
+            uint32_t c[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) c[i] = compress_even(f[t][i]);
+            bm[t][2 * lane] = c[0] | (c[1] << 16);
+            bm[t][2 * lane + 1] = c[2] | (c[3] << 16);
+        }
     if (WRITE) {
         // positions in order: lanes, then words, then starts
 #pragma unroll

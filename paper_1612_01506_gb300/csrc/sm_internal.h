@@ -57,6 +57,7 @@ struct ScanArgs {
     unsigned long long* tile_next;  // next unclaimed tile of the counting modes (scratch, zero between launches)
     uint64_t* d_count;       // result count
     uint32_t* warp_counts;   // per-(tile, warp) counts (scratch, ntiles x 8; report only)
+    uint32_t* bitmaps;       // report: per-(tile, warp) found bitmaps (ntiles x 8 x 64 words) or null
     uint64_t* d_pos;         // report output
     uint64_t cap;            // report capacity
     uint64_t spin_ns;        // limit of every bounded wait, in ns
@@ -90,8 +91,14 @@ constexpr uint32_t kQueueBytes = kConsumerWarps * kQueueCap * 4;           // 4 
 // rounds of two tiles) replace the survivor queues.
 inline uint32_t packed_words_for(uint32_t stage_bytes) { return stage_bytes / 16 + 8; }
 
-inline size_t scan_smem_bytes(uint32_t stage_bytes, uint32_t stages, int kind = kKindBytes) {
-    const size_t mid = kind_packed(kind) ? (size_t)16 * packed_words_for(stage_bytes) : kQueueBytes;
+// Reports: the byte kinds build each warp-tile's found bitmap in shared
+// memory (64 words per warp).
+constexpr uint32_t kBitmapWords = kWarpStarts / 32;
+constexpr uint32_t kBitmapBytes = kConsumerWarps * kBitmapWords * 4;   // 2 KiB
+
+inline size_t scan_smem_bytes(uint32_t stage_bytes, uint32_t stages, int kind = kKindBytes, bool report = false) {
+    const size_t mid = kind_packed(kind) ? (size_t)16 * packed_words_for(stage_bytes)
+                                         : kQueueBytes + (report ? kBitmapBytes : 0u);
     return kScanHeader + mid + (size_t)stage_bytes * stages;
 }
 
@@ -107,5 +114,19 @@ cudaError_t scan_prepare(size_t max_smem);
 
 constexpr int kHistThreads = 256;
 cudaError_t launch_hist(uint32_t grid, cudaStream_t s, const HistArgs& a);
+
+// Second pass of a report: positions from the found bitmaps of the first.
+struct WriteArgs {
+    uint64_t ntiles;
+    uint64_t tiles_per_cta;       // CTA b writes the tiles of range b
+    const uint64_t* partials;     // per-range match counts of the first pass
+    const uint32_t* warp_counts;  // per-(tile, warp) counts
+    const uint32_t* bitmaps;      // per-(tile, warp) found bitmaps
+    uint64_t* d_pos;
+    uint64_t cap;
+    uint32_t* status;
+};
+constexpr int kWriteThreads = 32 * kConsumerWarps;
+cudaError_t launch_bitmap_write(uint32_t grid, cudaStream_t s, const WriteArgs& a);
 
 }  // namespace smk

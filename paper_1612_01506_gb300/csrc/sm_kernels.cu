@@ -68,7 +68,9 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
     uint32_t* flag = reinterpret_cast<uint32_t*>(smem + 336);
     uint32_t* queues = reinterpret_cast<uint32_t*>(smem + kScanHeader);  // [kConsumerWarps][kQueueCap]
     uint32_t* pbuf = reinterpret_cast<uint32_t*>(smem + kScanHeader);    // packed: [2][2][A.packed_words]
-    uint8_t* bufs = smem + kScanHeader + (PACKED ? 16u * A.packed_words : kQueueBytes);
+    uint32_t* sbms = reinterpret_cast<uint32_t*>(smem + kScanHeader + kQueueBytes);   // bytes, tile-count
+    uint8_t* bufs = smem + kScanHeader +
+                    (PACKED ? 16u * A.packed_words : kQueueBytes + (MODE == kModeTileCount ? kBitmapBytes : 0u));
 
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t SB = A.stage_bytes, S = A.stages, m = A.m, r = A.r, one = A.one;
@@ -226,8 +228,13 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
                     }
             }
             const uint32_t* const pk[2] = {pw[0], two ? pw[1] : pw[0]};
+            uint32_t* const bm[2] = {
+                MODE == kModeTileCount && A.bitmaps
+                    ? A.bitmaps + (d[0].tile * kConsumerWarps + warp) * kBitmapWords : nullptr,
+                MODE == kModeTileCount && A.bitmaps && two
+                    ? A.bitmaps + (d[1].tile * kConsumerWarps + warp) * kBitmapWords : nullptr};
             const uint2 c = packed_tiles<MODE == kModeWrite, MODE == kModeCount>(
-                pk, two, warp, lane, ParamQC<MAXM>{&P}, m, r, A.ng, A.nstarts, s0, out, A.d_pos, A.cap);
+                pk, two, warp, lane, ParamQC<MAXM>{&P}, m, r, A.ng, A.nstarts, s0, out, A.d_pos, A.cap, bm);
             if (MODE == kModeTileCount) {
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
@@ -269,9 +276,11 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
                 const uint32_t cw = lane < warp ? __ldcg(A.warp_counts + d.tile * kConsumerWarps + lane) : 0u;
                 out = d.offset + warp_sum_u32(cw);
             }
+            uint32_t* bm = MODE == kModeTileCount && A.bitmaps
+                               ? A.bitmaps + (d.tile * kConsumerWarps + warp) * kBitmapWords : nullptr;
             const uint32_t tile_count = warp_tile<SEVEN, MODE == kModeWrite, MODE == kModeCount>(
                 b4, b32, c0, wq, warp, lane, ParamQC<MAXM>{&P}, m, r, A.ng, one,
-                A.nstarts, s0, q, out, A.d_pos, A.cap);
+                A.nstarts, s0, q, out, A.d_pos, A.cap, bm, sbms + warp * kBitmapWords);
 
             if (MODE == kModeTileCount) {
                 const uint32_t wsum = warp_sum_u32(tile_count);
@@ -324,6 +333,128 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
             *A.ticket = 0u;
             *A.tile_next = 0ull;
         }
+    }
+}
+
+// ------------------------------------------------------------ report writes
+
+// Second pass of a report: CTA b writes the match positions of the tiles of
+// range b from the found bitmaps the tile-count pass stored (no text is
+// read again). Its first rank is the sum of the earlier ranges' counts. The
+// range's warp counts are read into shared memory kWalk tiles at a time and
+// scanned there (tile offsets, warp offsets); then every warp turns the
+// bitmaps of its own warp-tiles with matches into positions, staged through
+// shared memory so that the stores are coalesced, loading the next bitmap
+// while it writes the current one.
+constexpr uint32_t kWalk = 256;   // tiles per pass over shared memory (one per thread)
+
+__global__ void __launch_bounds__(kWriteThreads) bitmap_write_kernel(const __grid_constant__ WriteArgs W) {
+    static_assert(kWalk == kWriteThreads, "one tile per thread");
+    __shared__ uint32_t stage[kConsumerWarps][kStageCap];
+    __shared__ uint32_t woff[kWalk][kConsumerWarps];  // warp offsets within the tile
+    __shared__ uint32_t ttot[kWalk];                  // tile totals
+    __shared__ uint32_t toff[kWalk];                  // tile offsets within the pass
+    __shared__ uint64_t red[kConsumerWarps];
+    __shared__ uint64_t base_s;
+    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint64_t t0 = (uint64_t)blockIdx.x * W.tiles_per_cta;
+    const uint64_t t1 = min(t0 + W.tiles_per_cta, W.ntiles);
+
+    // first rank of the range: the counts of the earlier ranges
+    uint64_t v = 0;
+    for (uint32_t i = tid; i < blockIdx.x; i += kWriteThreads) v += __ldcg(W.partials + i);
+    v = warp_sum_u64(v);
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (tid == 0) {
+        uint64_t b = 0;
+        for (int w = 0; w < kConsumerWarps; ++w) b += red[w];
+        base_s = b;
+        if (blockIdx.x == 0) {
+            uint64_t t = 0;
+            for (uint32_t i = 0; i < gridDim.x; ++i) t += __ldcg(W.partials + i);
+            if (t > W.cap) atomicOr(W.status, kStatusTrunc);
+        }
+    }
+    __syncthreads();
+    uint64_t base = base_s;
+
+    uint32_t* stg = stage[warp];
+    for (uint64_t p0 = t0; p0 < t1; p0 += kWalk) {
+        const uint32_t np = (uint32_t)min((uint64_t)kWalk, t1 - p0);
+        // thread i: tile p0 + i -> warp offsets within the tile and its total
+        uint32_t tot = 0;
+        if (tid < np) {
+            const uint4* src = reinterpret_cast<const uint4*>(W.warp_counts + (p0 + tid) * kConsumerWarps);
+            const uint4 a = __ldcg(src), b = __ldcg(src + 1);
+            const uint32_t c[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int w = 0; w < kConsumerWarps; ++w) {
+                woff[tid][w] = tot;
+                tot += c[w];
+            }
+            ttot[tid] = tot;
+        }
+        // exclusive scan of the tile totals over the pass
+        const uint32_t inc = warp_incl_scan(tot, lane);
+        if (lane == 31) red[warp] = inc;
+        __syncthreads();
+        uint32_t wbase = 0;
+        for (uint32_t w = 0; w < warp; ++w) wbase += (uint32_t)red[w];
+        if (tid < np) toff[tid] = wbase + inc - tot;
+        uint64_t pass_tot = 0;
+        for (int w = 0; w < kConsumerWarps; ++w) pass_tot += red[w];
+        __syncthreads();
+
+        // warp w: its warp-tiles with matches, in tile order (the bitmap of
+        // the next one is loaded while the current one is written)
+        uint32_t i = 0;
+        uint32_t w0 = 0, w1 = 0;
+        auto own = [&](uint32_t k) -> uint32_t {   // matches of warp-tile (p0 + k, warp)
+            return (warp + 1 < kConsumerWarps ? woff[k][warp + 1] : ttot[k]) - woff[k][warp];
+        };
+        auto next_from = [&](uint32_t k) -> uint32_t {
+            while (k < np && own(k) == 0) ++k;
+            return k;
+        };
+        i = next_from(0);
+        if (i < np) {
+            const uint32_t* bm = W.bitmaps + ((p0 + i) * kConsumerWarps + warp) * kBitmapWords;
+            w0 = __ldcg(bm + 2 * lane);
+            w1 = __ldcg(bm + 2 * lane + 1);
+        }
+        while (i < np) {
+            const uint32_t j2 = next_from(i + 1);
+            uint32_t n0 = 0, n1 = 0;
+            if (j2 < np) {
+                const uint32_t* bm = W.bitmaps + ((p0 + j2) * kConsumerWarps + warp) * kBitmapWords;
+                n0 = __ldcg(bm + 2 * lane);
+                n1 = __ldcg(bm + 2 * lane + 1);
+            }
+            const uint32_t mine = own(i);
+            const uint32_t n = __popc(w0) + __popc(w1);
+            const uint32_t inc2 = warp_incl_scan(n, lane);
+            const uint64_t tile = p0 + i;
+            const uint32_t a0 = w0, a1 = w1;
+            staged_write(stg, lane, inc2 - n, n, mine, tile * kTile + warp * kWarpStarts,
+                         base + toff[i] + woff[i][warp], W.d_pos, W.cap, [&](auto&& cb) {
+                             uint32_t kk = 0, fw = a0;
+                             while (fw) {
+                                 cb(kk++, 64u * lane + (uint32_t)(__ffs(fw) - 1));
+                                 fw &= fw - 1;
+                             }
+                             fw = a1;
+                             while (fw) {
+                                 cb(kk++, 64u * lane + 32u + (uint32_t)(__ffs(fw) - 1));
+                                 fw &= fw - 1;
+                             }
+                         });
+            i = j2;
+            w0 = n0;
+            w1 = n1;
+        }
+        base += pass_tot;
+        __syncthreads();   // the pass's tables are rewritten by the next one
     }
 }
 
@@ -469,6 +600,11 @@ cudaError_t scan_prepare(size_t max_smem) {
                 if (e != cudaSuccess) return e;
             }
     return cudaSuccess;
+}
+
+cudaError_t launch_bitmap_write(uint32_t grid, cudaStream_t s, const WriteArgs& a) {
+    bitmap_write_kernel<<<grid, kWriteThreads, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_hist(uint32_t grid, cudaStream_t s, const HistArgs& a) {

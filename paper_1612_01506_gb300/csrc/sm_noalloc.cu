@@ -110,8 +110,9 @@ extern "C" sm_status sm_report_noalloc(const uint8_t* d_text, uint64_t n, const 
     a.ng = ng;
     a.stage_bytes = smk::stage_bytes_for(m);
     a.stages = 4;
-    while (a.stages > 2 && smk::scan_smem_bytes(a.stage_bytes, a.stages) > su.max_smem) --a.stages;
-    const size_t smem = smk::scan_smem_bytes(a.stage_bytes, a.stages);
+    while (a.stages > 2 && smk::scan_smem_bytes(a.stage_bytes, a.stages, smk::kKindBytes, true) > su.max_smem)
+        --a.stages;
+    const size_t smem = smk::scan_smem_bytes(a.stage_bytes, a.stages, smk::kKindBytes, true);
     if (smem > su.max_smem) return SM_ENOTSUP;
     const int occ = smk::scan_occupancy(smk::kModeTileCount, smk::kKindBytes, m, smem);
     if (occ <= 0) return SM_ECUDA;

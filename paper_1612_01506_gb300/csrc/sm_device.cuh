@@ -288,10 +288,13 @@ struct PatArg {
 // positions have ranks excl .. excl + n - 1 of the batch's tot and are
 // base + rel; for_each(cb) calls cb(k, rel) for the lane's k-th position in
 // ascending order. Positions pass through the warp's staging area stg
-// (kStageCap words) slice by slice, so that consecutive lanes store
-// consecutive ranks. Ranks at or beyond cap (counted from the batch's first
-// rank `out`) are dropped.
-constexpr uint32_t kStageCap = 256;
+// (kStageWords words) slice by slice, so that consecutive lanes store
+// consecutive ranks. Staged rank x sits at word x + x / 32: lanes whose
+// ranks are spaced evenly (by up to 32) then write distinct banks, where the
+// plain layout would put them on two. Ranks at or beyond cap (counted from
+// the batch's first rank `out`) are dropped.
+constexpr uint32_t kStageCap = 1024;
+constexpr uint32_t kStageWords = kStageCap + kStageCap / 32;
 
 template <class ForEach>
 __device__ __forceinline__ void staged_write(uint32_t* stg, uint32_t lane, uint32_t excl, uint32_t n, uint32_t tot,
@@ -301,13 +304,13 @@ __device__ __forceinline__ void staged_write(uint32_t* stg, uint32_t lane, uint3
         if (n && excl < p0 + kStageCap && excl + n > p0)
             for_each([&](uint32_t k, uint32_t rel) {
                 const uint32_t rk = excl + k - p0;   // wraps to a large value below the slice
-                if (rk < kStageCap) stg[rk] = rel;
+                if (rk < kStageCap) stg[rk + (rk >> 5)] = rel;
             });
         __syncwarp();
         const uint32_t cnt = min(kStageCap, tot - p0);
-        for (uint32_t o = lane; o < cnt; o += 32) {
+        for (uint32_t o = lane, i = 0; o < cnt; o += 32, ++i) {
             const uint64_t g = out + p0 + o;
-            if (g < cap) d_pos[g] = base + stg[o];
+            if (g < cap) d_pos[g] = base + stg[o + i];
         }
         __syncwarp();
     }
@@ -400,7 +403,24 @@ __device__ __forceinline__ uint32_t warp_tile(const uint4* __restrict__ b4, cons
             for (int i = 0; i < 4; ++i) f[c][i] &= valid_mask(lim - (512 * c + 4 * i));
     }
 
-    if (DIRECT && r >= m) return count_flags<kChunks>(f);
+    if (DIRECT && r >= m) {
+        // every compare peeled: the found bits are final. With bm, store the
+        // bitmap (chunk k = 32c + lane: 16 bits, start order) when the
+        // warp-tile has matches
+        const uint32_t cnt = count_flags<kChunks>(f);
+        if (bm && warp_sum_u32(cnt)) {
+            uint16_t* bm16 = reinterpret_cast<uint16_t*>(bm);
+#pragma unroll
+            for (int c = 0; c < kChunks; ++c) {
+                uint32_t m16 = 0;
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    m16 |= ((((f[c][i] >> 7) & 0x01010101u) * 0x01020408u) >> 24) << (4 * i);
+                bm16[32 * c + lane] = (uint16_t)m16;
+            }
+        }
+        return cnt;
+    }
 
     // byte c: 1 if chunk c of this lane has a surviving start
     uint32_t alive = 0;
@@ -679,8 +699,7 @@ __device__ __forceinline__ uint2 packed_tiles(const uint32_t* const (&pk)[2], bo
             uint32_t c[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) c[i] = compress_even(f[t][i]);
-            bm[t][2 * lane] = c[0] | (c[1] << 16);
-            bm[t][2 * lane + 1] = c[2] | (c[3] << 16);
+            reinterpret_cast<uint2*>(bm[t])[lane] = make_uint2(c[0] | (c[1] << 16), c[2] | (c[3] << 16));
         }
     if (WRITE) {
         // positions in order: lanes, then words, then starts

@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
                     ? A.bitmaps + (d[0].tile * kConsumerWarps + warp) * kBitmapWords : nullptr,
                 MODE == kModeTileCount && A.bitmaps && two
                     ? A.bitmaps + (d[1].tile * kConsumerWarps + warp) * kBitmapWords : nullptr};
-            const uint2 c = packed_tiles<MODE == kModeWrite, MODE == kModeCount>(
+            const uint2 c = packed_tiles<MODE == kModeWrite, MODE != kModeWrite>(
                 pk, two, warp, lane, ParamQC<MAXM>{&P}, m, r, A.ng, A.nstarts, s0, out, A.d_pos, A.cap, bm);
             if (MODE == kModeTileCount) {
 #pragma unroll
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
             }
             uint32_t* bm = MODE == kModeTileCount && A.bitmaps
                                ? A.bitmaps + (d.tile * kConsumerWarps + warp) * kBitmapWords : nullptr;
-            const uint32_t tile_count = warp_tile<SEVEN, MODE == kModeWrite, MODE == kModeCount>(
+            const uint32_t tile_count = warp_tile<SEVEN, MODE == kModeWrite, MODE != kModeWrite>(
                 b4, b32, c0, wq, warp, lane, ParamQC<MAXM>{&P}, m, r, A.ng, one,
                 A.nstarts, s0, q, out, A.d_pos, A.cap, bm, sbms + warp * kBitmapWords);
 
@@ -350,7 +350,7 @@ constexpr uint32_t kWalk = 256;   // tiles per pass over shared memory (one per 
 
 __global__ void __launch_bounds__(kWriteThreads) bitmap_write_kernel(const __grid_constant__ WriteArgs W) {
     static_assert(kWalk == kWriteThreads, "one tile per thread");
-    __shared__ uint32_t stage[kConsumerWarps][kStageCap];
+    __shared__ uint32_t stage[kConsumerWarps][kStageWords];
     __shared__ uint32_t woff[kWalk][kConsumerWarps];  // warp offsets within the tile
     __shared__ uint32_t ttot[kWalk];                  // tile totals
     __shared__ uint32_t toff[kWalk];                  // tile offsets within the pass
@@ -419,17 +419,19 @@ __global__ void __launch_bounds__(kWriteThreads) bitmap_write_kernel(const __gri
         };
         i = next_from(0);
         if (i < np) {
-            const uint32_t* bm = W.bitmaps + ((p0 + i) * kConsumerWarps + warp) * kBitmapWords;
-            w0 = __ldcg(bm + 2 * lane);
-            w1 = __ldcg(bm + 2 * lane + 1);
+            const uint2 x = __ldcg(reinterpret_cast<const uint2*>(W.bitmaps + ((p0 + i) * kConsumerWarps + warp) *
+                                                                                  kBitmapWords) + lane);
+            w0 = x.x;
+            w1 = x.y;
         }
         while (i < np) {
             const uint32_t j2 = next_from(i + 1);
             uint32_t n0 = 0, n1 = 0;
             if (j2 < np) {
-                const uint32_t* bm = W.bitmaps + ((p0 + j2) * kConsumerWarps + warp) * kBitmapWords;
-                n0 = __ldcg(bm + 2 * lane);
-                n1 = __ldcg(bm + 2 * lane + 1);
+                const uint2 x = __ldcg(reinterpret_cast<const uint2*>(W.bitmaps + ((p0 + j2) * kConsumerWarps +
+                                                                                     warp) * kBitmapWords) + lane);
+                n0 = x.x;
+                n1 = x.y;
             }
             const uint32_t mine = own(i);
             const uint32_t n = __popc(w0) + __popc(w1);

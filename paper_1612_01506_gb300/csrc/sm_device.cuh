@@ -284,6 +284,19 @@ struct PatArg {
     uint32_t grp[kGroups];    // window groups of the peeled compares
 };
 
+// A 16-start chunk's found flags packed as in the survivor queue (word i,
+// byte b at bit 8b + i) -> 16 bits in start order (start 4i + b at bit
+// 4i + b): gather the nibbles, then transpose the 4 x 4 bit matrix.
+__device__ __forceinline__ uint32_t chunk_mask16(uint32_t x) {
+    x &= 0x0F0F0F0Fu;
+    x = (x | (x >> 4)) & 0x00FF00FFu;
+    x = (x | (x >> 8)) & 0x0000FFFFu;
+    uint32_t t = (x ^ (x >> 3)) & 0x0A0Au;
+    x ^= t ^ (t << 3);
+    t = (x ^ (x >> 6)) & 0x00CCu;
+    return x ^ t ^ (t << 6);
+}
+
 // Stores one batch of a warp's match positions in rank order. The lane's n
 // positions have ranks excl .. excl + n - 1 of the batch's tot and are
 // base + rel; for_each(cb) calls cb(k, rel) for the lane's k-th position in
@@ -411,13 +424,9 @@ __device__ __forceinline__ uint32_t warp_tile(const uint4* __restrict__ b4, cons
         if (bm && warp_sum_u32(cnt)) {
             uint16_t* bm16 = reinterpret_cast<uint16_t*>(bm);
 #pragma unroll
-            for (int c = 0; c < kChunks; ++c) {
-                uint32_t m16 = 0;
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    m16 |= ((((f[c][i] >> 7) & 0x01010101u) * 0x01020408u) >> 24) << (4 * i);
-                bm16[32 * c + lane] = (uint16_t)m16;
-            }
+            for (int c = 0; c < kChunks; ++c)
+                bm16[32 * c + lane] = (uint16_t)chunk_mask16(((f[c][0] >> 7) | (f[c][1] >> 6)) |
+                                                             ((f[c][2] >> 5) | (f[c][3] >> 4)));
         }
         return cnt;
     }
@@ -489,13 +498,9 @@ __device__ __forceinline__ uint32_t warp_tile(const uint4* __restrict__ b4, cons
             }
         }
         const uint32_t n = (__popc(g[0]) + __popc(g[1])) + (__popc(g[2]) + __popc(g[3]));
-        if (bm && n) {
-            // chunk k's 16 found bits in start order (start 4i + b: word i, byte b)
-            uint32_t m16 = 0;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) m16 |= ((((g[i] >> 7) & 0x01010101u) * 0x01020408u) >> 24) << (4 * i);
-            reinterpret_cast<uint16_t*>(sbm)[k] = (uint16_t)m16;
-        }
+        if (bm && n)   // chunk k's 16 found bits in start order
+            reinterpret_cast<uint16_t*>(sbm)[k] =
+                (uint16_t)chunk_mask16(((g[0] >> 7) | (g[1] >> 6)) | ((g[2] >> 5) | (g[3] >> 4)));
         if (WRITE) {
             const uint32_t inc = warp_incl_scan(n, lane);
             uint64_t rk = out + inc - n;

@@ -451,16 +451,14 @@ static sm_status search(sm_ctx* c, const uint8_t* d_text, uint64_t n, const uint
     }
     smk::ScanArgs a = scan_args(c, d_text, n, m, pl, gr, d_count);
     cudaError_t e;
-    if (report) {
-        // a report: the tile-count pass (per-range counts, per-warp-tile
-        // counts and found bitmaps), then the positions from the bitmaps
-        if ((e = cudaMemsetAsync(c->d_partials, 0, sizeof(uint64_t) * gr.grid, s)) != cudaSuccess)
-            return cuda_fail(e, "clearing the range counts");
-        a.bitmaps = c->d_bitmaps;
-    }
+    // a report: the tile-count pass (per-warp-tile counts and found
+    // bitmaps), the per-range counts, then the positions from the bitmaps
+    if (report) a.bitmaps = c->d_bitmaps;
     e = smk::launch_scan(mode1, pl.kind, gr.grid, gr.smem, s, a, pl.qc.data(), pl.groups.data());
     if (e != cudaSuccess) return cuda_fail(e, "scan launch");
     if (report) {
+        e = smk::launch_range_sums(gr.grid, s, c->d_warp_counts, gr.ntiles, gr.per_cta, c->d_partials);
+        if (e != cudaSuccess) return cuda_fail(e, "range count launch");
         smk::WriteArgs w{};
         w.ntiles = gr.ntiles;
         w.tiles_per_cta = gr.per_cta;

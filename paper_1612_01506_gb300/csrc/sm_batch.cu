@@ -35,8 +35,13 @@ using namespace dev;
 constexpr uint32_t kMaxSlots = 4096;   // patterns one CTA counts in shared memory
 constexpr uint32_t kHistChunk = 65536; // bytes per histogram work item
 // A pattern whose rarest symbol has at most this frequency in its text takes
-// the candidate path (expected candidates per tile <= 0.08 * 16384).
+// the candidate path (expected candidates per tile <= 0.08 * 16384) ...
 constexpr double kCandidateFreq = 0.08;
+// ... when its text region has at least kCandidateMin such patterns: the
+// symbol index of a staged tile costs about as much as the dense scan of a
+// dozen patterns (measured on GB300: ~16 us per tile and CTA against
+// ~1.3 us for one dense pattern), so fewer run the dense scan.
+constexpr uint32_t kCandidateMin = 16;
 
 struct BatchText {        // a text, or one group of <= kMaxSlots of its patterns
     uint64_t off;         // byte offset in the packed texts
@@ -347,9 +352,11 @@ struct Guard {
 // and their window groups from plan_dense) or the candidate path (compares
 // in order pi, the first being the rarest symbol).
 struct PatDesc {
-    BatchPat pat{};
-    std::vector<uint32_t> qc;
-    bool cand = false;
+    BatchPat pat{};             // the dense scan
+    std::vector<uint32_t> qc;   // its m compares in scan order, then its window groups
+    BatchPat cpat{};            // the candidate path (when cand)
+    std::vector<uint32_t> cqc;  // its m compares in the order pi
+    bool cand = false;   // the rarest symbol is rare enough for the candidate path
     bool zero = false;   // a symbol never occurs in the text, or m > n: count 0
 };
 
@@ -364,12 +371,12 @@ PatDesc describe(const uint8_t* p, uint32_t m, const uint32_t* h, uint64_t n, ui
     std::stable_sort(pi.begin(), pi.end(), [&](uint32_t a, uint32_t b) { return h[p[a]] < h[p[b]]; });
     std::vector<uint32_t> v(m);
     for (uint32_t j = 0; j < m; ++j) v[j] = ((pi[j] + delta) << 8) | p[pi[j]];
-    d.pat = BatchPat{0, m, 1, 0, out, text7 ? 1u : 0u};   // ng = 0: no peeled compares (candidate path)
     if ((double)h[p[pi[0]]] / (double)n < smk::kCandidateFreq) {
         d.cand = true;
-        d.qc = std::move(v);
-        return d;
+        d.cpat = BatchPat{0, m, 1, 0, out, text7 ? 1u : 0u};   // ng = 0: no peeled compares
+        d.cqc = v;
     }
+    d.pat = BatchPat{0, m, 1, 0, out, text7 ? 1u : 0u};
     std::vector<double> freq(m);
     for (uint32_t j = 0; j < m; ++j) freq[j] = (double)h[p[pi[j]]] / (double)n;
     // the m compares in scan order, then the window groups of the peeled ones
@@ -396,12 +403,15 @@ struct Tables {
 // Entries for one text region [off, off + n) counting starts below slimit:
 // groups of at most kMaxSlots patterns, dense ones first.
 void add_text(Tables& T, uint64_t off, uint64_t n, uint64_t slimit, const std::vector<const PatDesc*>& ds) {
+    uint32_t ncand = 0;
+    for (const PatDesc* d : ds) ncand += (!d->zero && d->cand) ? 1u : 0u;
+    const bool use_cand = ncand >= smk::kCandidateMin;
     std::vector<const PatDesc*> order;
     for (const PatDesc* d : ds)
-        if (!d->zero && !d->cand) order.push_back(d);
+        if (!d->zero && !(use_cand && d->cand)) order.push_back(d);
     const size_t ndense = order.size();
     for (const PatDesc* d : ds)
-        if (!d->zero && d->cand) order.push_back(d);
+        if (!d->zero && use_cand && d->cand) order.push_back(d);
     for (size_t g0 = 0; g0 < order.size(); g0 += kMaxSlots) {
         const size_t g1 = std::min(order.size(), g0 + kMaxSlots);
         BatchText e{off, n, 0, slimit, (uint32_t)T.pats.size(), 0, 0, 0, 0, 0};
@@ -414,10 +424,12 @@ void add_text(Tables& T, uint64_t off, uint64_t n, uint64_t slimit, const std::v
                 e.pmid = (uint32_t)T.pats.size();
                 any_cand = true;
             }
-            BatchPat bp = d->pat;
+            const bool c = i >= ndense;   // candidate path
+            const std::vector<uint32_t>& qc = c ? d->cqc : d->qc;
+            BatchPat bp = c ? d->cpat : d->pat;
             bp.qc_off = (uint32_t)T.qc.size();
-            T.qc.insert(T.qc.end(), d->qc.begin(), d->qc.end());
-            if (d->cand) mask[(d->qc[0] & 0xFFu) >> 5] |= 1u << (d->qc[0] & 31u);
+            T.qc.insert(T.qc.end(), qc.begin(), qc.end());
+            if (c) mask[(qc[0] & 0xFFu) >> 5] |= 1u << (qc[0] & 31u);
             T.pats.push_back(bp);
             e.maxm = std::max(e.maxm, bp.m);
             mn = std::min(mn, bp.m);

@@ -29,10 +29,10 @@ inline bool kind_packed(int kind) { return kind >= kKindPackedAdj; }
 
 enum ScanMode : int {
     kModeCount = 0,      // count only: per-CTA partial counts, last CTA writes *d_count
-    kModeTileCount = 1,  // as kModeCount, and per-(tile, warp) counts for a report; the partials
-                         // are per range of tiles_per_cta tiles (zeroed by the caller)
+    kModeTileCount = 1,  // as kModeCount, and per-(tile, warp) counts (and found bitmaps) for a
+                         // report
     kModeWrite = 2       // report: write ascending positions of tiles with matches; CTA b owns
-                         // tile range b
+                         // tile range b (partials: per-range counts from launch_range_sums)
 };
 
 struct ScanArgs {
@@ -40,7 +40,7 @@ struct ScanArgs {
     uint64_t n;
     uint64_t nstarts;        // n - m + 1
     uint64_t ntiles;         // ceil(nstarts / kTile)
-    uint64_t tiles_per_cta;  // each CTA owns one contiguous range of tiles
+    uint64_t tiles_per_cta;  // write mode: each CTA owns one contiguous range of tiles
     uint32_t m;
     uint32_t r;              // peeled compares, 1..m (dense phase)
     uint32_t stage_bytes;    // shared-memory bytes per pipeline stage (multiple of 128)
@@ -52,7 +52,7 @@ struct ScanArgs {
     uint32_t packed_words;   // packed kinds: words of one packed tile buffer
     uint32_t test_skip_copy; // test hook: 1 = never issue the first tile's copy
     uint32_t* status;        // deferred status word
-    uint64_t* partials;      // counting: per-CTA counts; tile-count/write: per tile-range counts (grid entries)
+    uint64_t* partials;      // counting modes: per-CTA counts; write: per tile-range counts (grid entries)
     uint32_t* ticket;        // last-CTA ticket (scratch, zero between launches)
     unsigned long long* tile_next;  // next unclaimed tile of the counting modes (scratch, zero between launches)
     uint64_t* d_count;       // result count
@@ -128,5 +128,8 @@ struct WriteArgs {
 };
 constexpr int kWriteThreads = 32 * kConsumerWarps;
 cudaError_t launch_bitmap_write(uint32_t grid, cudaStream_t s, const WriteArgs& a);
+// Between the passes: partials[b] = matches in tiles [b T, (b + 1) T), one block per range.
+cudaError_t launch_range_sums(uint32_t grid, cudaStream_t s, const uint32_t* warp_counts, uint64_t ntiles,
+                              uint64_t tiles_per_range, uint64_t* partials);
 
 }  // namespace smk

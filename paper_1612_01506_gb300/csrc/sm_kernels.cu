@@ -240,12 +240,7 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
                 for (int k = 0; k < 2; ++k) {
                     if (k == 1 && !two) break;
                     const uint32_t wsum = warp_sum_u32(k == 0 ? c.x : c.y);
-                    if (lane == 0) {
-                        A.warp_counts[d[k].tile * kConsumerWarps + warp] = wsum;
-                        if (wsum)
-                            atomicAdd(reinterpret_cast<unsigned long long*>(A.partials) + d[k].tile / A.tiles_per_cta,
-                                      (unsigned long long)wsum);
-                    }
+                    if (lane == 0) A.warp_counts[d[k].tile * kConsumerWarps + warp] = wsum;
                 }
             }
             my_count += c.x + c.y;
@@ -284,11 +279,7 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
 
             if (MODE == kModeTileCount) {
                 const uint32_t wsum = warp_sum_u32(tile_count);
-                if (lane == 0) {
-                    A.warp_counts[d.tile * kConsumerWarps + warp] = wsum;
-                    if (wsum) atomicAdd(reinterpret_cast<unsigned long long*>(A.partials) + d.tile / A.tiles_per_cta,
-                                        (unsigned long long)wsum);
-                }
+                if (lane == 0) A.warp_counts[d.tile * kConsumerWarps + warp] = wsum;
             }
             my_count += tile_count;
             __syncwarp();
@@ -302,9 +293,9 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
 
     if (MODE == kModeWrite) return;
 
-    // count: CTA total -> partials; tile-count: the consumers added each
-    // tile's count to its range's partial. The last CTA to finish writes the
-    // sum and clears the ticket and the tile counter for the next launch.
+    // CTA total -> partials; the last CTA to finish writes the sum and
+    // clears the ticket and the tile counter for the next launch. (A report
+    // then overwrites the partials with per-range counts: range_sum_kernel.)
     const uint64_t ws = warp_sum_u64((uint64_t)my_count);
     if (lane == 0) red[warp] = ws;
     __threadfence();
@@ -312,7 +303,7 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
     if (tid == 0) {
         uint64_t tot = 0;
         for (int w = 0; w < kConsumerWarps + 1; ++w) tot += red[w];
-        if (MODE == kModeCount) A.partials[blockIdx.x] = tot;
+        A.partials[blockIdx.x] = tot;
         __threadfence();
         const uint32_t t = atomicAdd(A.ticket, 1u);
         *flag = (t == gridDim.x - 1) ? 1u : 0u;
@@ -337,6 +328,36 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
 }
 
 // ------------------------------------------------------------ report writes
+
+// Between the two passes of a report: block b sums the per-(tile, warp)
+// counts of range b (tiles [b T, (b + 1) T), T = tiles_per_range) into
+// partials[b]. The tile-count pass writes only per-warp-tile counts; a
+// per-range atomic there put every warp of the GPU on the same few
+// addresses (tiles are claimed in order) and cost up to 2x the scan.
+__global__ void __launch_bounds__(kWriteThreads) range_sum_kernel(const uint32_t* __restrict__ warp_counts,
+                                                                  uint64_t ntiles, uint64_t tiles_per_range,
+                                                                  uint64_t* __restrict__ partials) {
+    __shared__ uint64_t red[kWriteThreads / 32];
+    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint64_t t0 = (uint64_t)blockIdx.x * tiles_per_range;
+    const uint64_t t1 = min(t0 + tiles_per_range, ntiles);
+    // a tile's 8 counts are two 16-byte words
+    const uint4* src = reinterpret_cast<const uint4*>(warp_counts + t0 * kConsumerWarps);
+    const uint64_t nv = t1 > t0 ? 2 * (t1 - t0) : 0;
+    uint64_t v = 0;
+    for (uint64_t i = tid; i < nv; i += kWriteThreads) {
+        const uint4 x = __ldcg(src + i);
+        v += (uint64_t)((x.x + x.y) + (x.z + x.w));
+    }
+    v = warp_sum_u64(v);
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (tid == 0) {
+        uint64_t t = 0;
+        for (int w = 0; w < kWriteThreads / 32; ++w) t += red[w];
+        partials[blockIdx.x] = t;
+    }
+}
 
 // Second pass of a report: CTA b writes the match positions of the tiles of
 // range b from the found bitmaps the tile-count pass stored (no text is
@@ -602,6 +623,12 @@ cudaError_t scan_prepare(size_t max_smem) {
                 if (e != cudaSuccess) return e;
             }
     return cudaSuccess;
+}
+
+cudaError_t launch_range_sums(uint32_t grid, cudaStream_t s, const uint32_t* warp_counts, uint64_t ntiles,
+                              uint64_t tiles_per_range, uint64_t* partials) {
+    range_sum_kernel<<<grid, kWriteThreads, 0, s>>>(warp_counts, ntiles, tiles_per_range, partials);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_bitmap_write(uint32_t grid, cudaStream_t s, const WriteArgs& a) {

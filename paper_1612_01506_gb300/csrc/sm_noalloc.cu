@@ -12,7 +12,7 @@
 //   [0, 4)        deferred status bits (written by kernels, not read back)
 //   [4, 8)        last-CTA ticket (must be 0 when a call starts)
 //   [8, 16)       tile counter of the tile-count pass (must be 0 when a call starts)
-//   [256, ..)     partial counts per tile range, kMaxCtas x uint64 (cleared by each call)
+//   [256, ..)     per-CTA, then per-range partial counts, kMaxCtas x uint64
 //   [.., end)     per-(tile, warp) match counts, kMaxTiles x 8 x uint32
 // kMaxTiles bounds the text: at most kMaxTiles * 16384 start positions.
 #include "sm.h"
@@ -130,10 +130,12 @@ extern "C" sm_status sm_report_noalloc(const uint8_t* d_text, uint64_t n, const 
     a.d_count = d_count;
     a.spin_ns = 1000000000ull;
 
-    // the array keeps the previous call's contents: clear status, ticket,
-    // tile counter and the range counts
-    if (cudaMemsetAsync(su.scratch, 0, kPartialsOff + sizeof(uint64_t) * grid, s) != cudaSuccess) return SM_ECUDA;
+    // the array keeps the previous call's contents: clear status, ticket
+    // and tile counter
+    if (cudaMemsetAsync(su.scratch, 0, kPartialsOff, s) != cudaSuccess) return SM_ECUDA;
     if (smk::launch_scan(smk::kModeTileCount, smk::kKindBytes, grid, smem, s, a, qc, groups) != cudaSuccess) return SM_ECUDA;
+    if (smk::launch_range_sums(grid, s, a.warp_counts, a.ntiles, a.tiles_per_cta, a.partials) != cudaSuccess)
+        return SM_ECUDA;
     a.d_pos = d_pos;
     a.cap = cap;
     if (smk::launch_scan(smk::kModeWrite, smk::kKindBytes, grid, smem, s, a, qc, groups) != cudaSuccess) return SM_ECUDA;

@@ -61,11 +61,13 @@ def to_dev(torch, flat, offset=3):
     return buf[offset:offset + flat.size]
 
 
-@pytest.mark.parametrize("seed", [1, 2, 3])
-def test_batch_mixed(torch, ctx, seed):
+# 8 patterns per text: every pattern runs the dense scan; 40: texts with at
+# least 16 patterns whose rarest symbol is rare run the candidate path
+@pytest.mark.parametrize("seed,per_text", [(1, 8), (2, 8), (3, 40), (4, 40)])
+def test_batch_mixed(torch, ctx, seed, per_text):
     sizes = [0, 1, 17, 5000, 40_000, 3 * 16384 + 11, 200_000, 7]
     kinds = [4, 20, "markov95", 256, 4, 2, "markov95", 64]
-    texts, flat, off, pats, pt = make_batch(seed, sizes, kinds, 8, 600)
+    texts, flat, off, pats, pt = make_batch(seed, sizes, kinds, per_text, 600)
     d = to_dev(torch, flat)
     b = sm.sm_batch_create(ctx, d, off, pats, pt)
     got = sm.sm_batch_count(b).cpu().numpy()[: len(pats)]

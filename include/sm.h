@@ -219,6 +219,19 @@ sm_status sm_batch_create(sm_ctx* ctx, const uint8_t* d_texts, const int64_t* h_
                           const uint8_t* h_pats, const int64_t* h_pat_off, const int32_t* h_pat_text,
                           uint32_t npats, sm_batch** out, sm_stream_t stream);
 sm_status sm_batch_count(sm_batch* batch, int64_t* d_counts, sm_stream_t stream);
+/*
+ * sm_batch_report: the reporting version (Sec. 2.1) for the whole batch.
+ * Writes d_counts[k] as sm_batch_count does and the positions of pattern k,
+ * ascending, to d_pos[d_pos_off[k] .. d_pos_off[k+1]) (device int64 offsets,
+ * npats + 1 entries; at most that many positions, the count stays the full
+ * count, and a pattern with more sets SM_ETRUNC for sm_sync). Three passes
+ * over the texts' tiles: counts per (pattern, tile), their prefix sums per
+ * pattern, then the writes of the tiles with matches. The first call
+ * allocates 12 bytes per (pattern, tile) in the batch; later calls allocate
+ * nothing.
+ */
+sm_status sm_batch_report(sm_batch* batch, int64_t* d_counts, uint64_t* d_pos, const int64_t* d_pos_off,
+                          sm_stream_t stream);
 void sm_batch_destroy(sm_batch* batch);
 
 /*
@@ -226,8 +239,9 @@ void sm_batch_destroy(sm_batch* batch);
  * d_pat_text and the packed patterns d_pats are device arrays laid out as
  * above. Counts go to d_counts. When d_pos is not NULL, the positions of
  * pattern k are written in ascending order to d_pos[d_pos_off[k] ..
- * d_pos_off[k+1]) (at most that many; the count stays the full count).
- * Synchronous: copies the metadata to the host, plans, runs and waits.
+ * d_pos_off[k+1]) (at most that many; the count stays the full count), as
+ * sm_batch_report does. Synchronous: copies the metadata to the host, plans,
+ * runs and waits.
  */
 sm_status sm_count_batch(sm_ctx* ctx, const uint8_t* d_texts, const int64_t* d_text_off, uint32_t ntexts,
                          const uint8_t* d_pats, const int64_t* d_pat_off, const int32_t* d_pat_text,
@@ -253,6 +267,14 @@ sm_status sm_count_batch(sm_ctx* ctx, const uint8_t* d_texts, const int64_t* d_t
  *                      Asynchronous on `stream`; allocates nothing once its
  *                      two table buffers have grown to the batch size.
  *   sm_stepper_retire  forget qid.
+ *   sm_stepper_report  report nq patterns (h_pats / h_pat_off packed as for
+ *                      sm_batch_create) over the whole text in one batched
+ *                      report: counts to d_counts[0..nq), ascending positions
+ *                      of pattern k to d_pos[h_pos_off[k] .. h_pos_off[k+1])
+ *                      (host offsets; at most that many, SM_ETRUNC beyond).
+ *                      Asynchronous on `stream`; it first waits for the
+ *                      previous report of this stepper, whose tables and
+ *                      per-(pattern, tile) counters (12 bytes each) it reuses.
  * One stepper is driven from one host thread and one stream.
  */
 typedef struct sm_stepper sm_stepper;
@@ -263,6 +285,8 @@ sm_status sm_stepper_admit(sm_stepper* stepper, uint32_t qid, const uint8_t* h_p
 sm_status sm_stepper_step(sm_stepper* stepper, const uint32_t* h_qids, uint32_t nq, uint32_t chunk,
                           int64_t* d_counts, sm_stream_t stream);
 sm_status sm_stepper_retire(sm_stepper* stepper, uint32_t qid);
+sm_status sm_stepper_report(sm_stepper* stepper, const uint8_t* h_pats, const int64_t* h_pat_off, uint32_t nq,
+                            const int64_t* h_pos_off, uint64_t* d_pos, int64_t* d_counts, sm_stream_t stream);
 void sm_stepper_destroy(sm_stepper* stepper);
 
 /* ------------------------------------------------------- no allocation */

@@ -61,6 +61,23 @@ struct BatchPat {
     uint32_t ng;          // window groups of the peeled compares (after the m compares in the qc table)
     uint32_t out;         // index of the pattern in the caller's arrays
     uint32_t seven;       // 1: text and pattern are 7-bit
+    uint64_t tb;          // reports: the pattern's first per-tile counter
+};
+
+// Batched reports run the batch kernel three ways: counting; counting plus a
+// count per (pattern, tile); and writing positions. Between the last two,
+// batch_prefix_kernel turns each pattern's tile counts into the rank of its
+// first match in every tile.
+constexpr int kBatchCount = 0;
+constexpr int kBatchTileCount = 1;
+constexpr int kBatchWrite = 2;
+
+// A pattern's per-tile counters: tcnt[tb .. tb + nt) (tile counts) and
+// toff[tb .. tb + nt] (their exclusive prefix sums, then the total).
+struct PatTiles {
+    uint64_t tb;
+    uint32_t nt;
+    uint32_t out;         // index of the pattern in the caller's arrays
 };
 
 struct BatchArgs {
@@ -73,6 +90,10 @@ struct BatchArgs {
     const uint64_t* cta_items;  // grid + 1: CTA b takes items [cta_items[b], cta_items[b+1])
     const uint32_t* cta_pbase;  // grid: first pattern counted by CTA b (its slot 0)
     int64_t* d_counts;
+    uint32_t* tcnt;             // tile count: per-(pattern, tile) counts, zeroed by the caller
+    const uint64_t* toff;       // write: per-(pattern, tile) ranks of the first match
+    uint64_t* d_pos;            // write: positions of pattern `out` go to d_pos + pos_off[out] ...
+    const int64_t* pos_off;     // ... at most pos_off[out + 1] - pos_off[out] of them
     uint32_t stage_bytes, stages, one, nslots;
     uint32_t index_cap;         // entries of the per-tile position index (0: no index)
     uint32_t* status;
@@ -86,11 +107,13 @@ struct BatchDesc {
 };
 
 
+template <int MODE>
 __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constant__ BatchArgs A) {
     extern __shared__ __align__(128) uint8_t smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     uint64_t* empty = reinterpret_cast<uint64_t*>(smem + 64);
     BatchDesc* desc = reinterpret_cast<BatchDesc*>(smem + 128);
+    uint32_t* wcnt = reinterpret_cast<uint32_t*>(smem + 256);   // write: [2][kConsumerWarps] warp counts
     uint32_t* queues = reinterpret_cast<uint32_t*>(smem + kScanHeader);
     uint32_t* slots = reinterpret_cast<uint32_t*>(smem + kScanHeader + kQueueBytes);
     uint8_t* after_slots = smem + kScanHeader + kQueueBytes + ((A.nslots * 4u + 127u) & ~127u);
@@ -172,6 +195,7 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constan
         uint32_t* q = queues + warp * kQueueCap;
         const uint32_t c0 = warp * (kWarpStarts / 16) + lane;
         const uint32_t wq = warp * (kWarpStarts / 4);
+        uint32_t wpar = 0;   // write: which half of wcnt the next pattern uses
         for (uint32_t s = 0, phase = 0;;) {
             const bool ok = __all_sync(kFull, wait_bounded(&full[s], phase, A.spin_ns));
             // every consumer warp leaves together (later tiles use consumer barriers)
@@ -193,6 +217,34 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constan
                 const uint64_t nst = min(T.n - P.m + 1, T.slimit);   // the plan keeps only m <= n
                 if (s0 >= nst) continue;
                 const GlobalQC qc{A.qc + P.qc_off, P.m};
+                if constexpr (MODE == kBatchWrite) {
+                    // a tile with matches: the warps count theirs, exchange
+                    // the counts, then write from their ranks (the tables of
+                    // this mode hold dense patterns only)
+                    const uint64_t o0 = __ldg(A.toff + P.tb + d.k);
+                    if (__ldg(A.toff + P.tb + d.k + 1) == o0) continue;   // the same for every warp
+                    uint32_t c = P.seven ? warp_tile<true, false, true>(b4, b32, c0, wq, warp, lane, qc, P.m, P.r,
+                                                                        P.ng, one, nst, s0, q, 0, nullptr, 0)
+                                         : warp_tile<false, false, true>(b4, b32, c0, wq, warp, lane, qc, P.m, P.r,
+                                                                         P.ng, one, nst, s0, q, 0, nullptr, 0);
+                    c = warp_sum_u32(c);
+                    uint32_t* wc = wcnt + wpar * kConsumerWarps;
+                    wpar ^= 1u;
+                    if (lane == 0) wc[warp] = c;
+                    consumers_sync();   // (the half written two patterns ago was read before the last sync)
+                    const uint32_t before = warp_sum_u32(lane < warp ? wc[lane] : 0u);
+                    if (c) {
+                        const int64_t pb = __ldg(A.pos_off + P.out);
+                        const uint64_t cap = (uint64_t)(__ldg(A.pos_off + P.out + 1) - pb);
+                        if (P.seven)
+                            warp_tile<true, true, false>(b4, b32, c0, wq, warp, lane, qc, P.m, P.r, P.ng, one, nst,
+                                                         s0, q, o0 + before, A.d_pos + pb, cap);
+                        else
+                            warp_tile<false, true, false>(b4, b32, c0, wq, warp, lane, qc, P.m, P.r, P.ng, one, nst,
+                                                          s0, q, o0 + before, A.d_pos + pb, cap);
+                    }
+                    continue;
+                }
                 uint32_t c;
                 if (P.seven)
                     c = warp_tile<true, false, true>(b4, b32, c0, wq, warp, lane, qc, P.m, P.r, P.ng, one, nst, s0, q,
@@ -201,7 +253,10 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constan
                     c = warp_tile<false, false, true>(b4, b32, c0, wq, warp, lane, qc, P.m, P.r, P.ng, one, nst, s0,
                                                       q, 0, nullptr, 0);
                 c = warp_sum_u32(c);
-                if (lane == 0 && c) atomicAdd(&slots[p - pbase], c);
+                if (lane == 0 && c) {
+                    atomicAdd(&slots[p - pbase], c);
+                    if (MODE == kBatchTileCount) atomicAdd(A.tcnt + P.tb + d.k, c);
+                }
             }
 
             // candidate patterns: their first (rarest) symbol is rare in the
@@ -264,7 +319,10 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constan
                         cnt += ok2;
                     }
                     cnt = warp_sum_u32(cnt);
-                    if (lane == 0 && cnt) atomicAdd(&slots[p - pbase], cnt);
+                    if (lane == 0 && cnt) {
+                        atomicAdd(&slots[p - pbase], cnt);
+                        if (MODE == kBatchTileCount) atomicAdd(A.tcnt + P.tb + d.k, cnt);
+                    }
                 }
             }
             __syncwarp();
@@ -275,10 +333,58 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constan
             }
         }
     }
+    if constexpr (MODE == kBatchWrite) return;
     __syncthreads();
     for (uint32_t i = tid; i < A.nslots; i += kThreads) {
         const uint32_t v = slots[i];
         if (v) atomicAdd(reinterpret_cast<unsigned long long*>(A.d_counts + A.pats[pbase + i].out), (unsigned long long)v);
+    }
+}
+
+// Batched reports, between the tile-count and write passes: block b takes
+// pattern pt[b] and writes the exclusive prefix sums of its tile counts and
+// then their total (toff[tb + nt]); a total above the pattern's position
+// capacity sets the truncation status.
+constexpr uint32_t kPrefixThreads = 256;
+
+__global__ void __launch_bounds__(kPrefixThreads) batch_prefix_kernel(const PatTiles* __restrict__ pt,
+                                                                      const uint32_t* __restrict__ tcnt,
+                                                                      uint64_t* __restrict__ toff,
+                                                                      const int64_t* __restrict__ pos_off,
+                                                                      uint32_t* status) {
+    __shared__ uint64_t wsum[kPrefixThreads / 32];
+    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const PatTiles P = pt[blockIdx.x];
+    uint64_t carry = 0;
+    for (uint64_t base = 0; base < P.nt; base += 4 * kPrefixThreads) {
+        uint32_t v[4], sum = 0;   // thread t: tiles base + 4t .. base + 4t + 3
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint64_t k = base + 4u * tid + i;
+            v[i] = k < P.nt ? tcnt[P.tb + k] : 0u;
+            sum += v[i];
+        }
+        const uint32_t inc = warp_incl_scan(sum, lane);
+        if (lane == 31) wsum[warp] = inc;
+        __syncthreads();
+        uint64_t before = carry, total = carry;
+        for (uint32_t w = 0; w < kPrefixThreads / 32; ++w) {
+            before += w < warp ? wsum[w] : 0u;
+            total += wsum[w];
+        }
+        uint64_t run = before + inc - sum;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint64_t k = base + 4u * tid + i;
+            if (k < P.nt) toff[P.tb + k] = run;
+            run += v[i];
+        }
+        carry = total;
+        __syncthreads();   // wsum is rewritten by the next round
+    }
+    if (tid == 0) {
+        toff[P.tb + P.nt] = carry;
+        if (carry > (uint64_t)(pos_off[P.out + 1] - pos_off[P.out])) atomicOr(status, kStatusTrunc);
     }
 }
 
@@ -331,6 +437,7 @@ using smk::BatchArgs;
 using smk::BatchPat;
 using smk::BatchText;
 using smk::kMaxSlots;
+using smk::PatTiles;
 using smk::kTile;
 
 struct Guard {
@@ -401,11 +508,15 @@ struct Tables {
 };
 
 // Entries for one text region [off, off + n) counting starts below slimit:
-// groups of at most kMaxSlots patterns, dense ones first.
-void add_text(Tables& T, uint64_t off, uint64_t n, uint64_t slimit, const std::vector<const PatDesc*>& ds) {
+// groups of at most kMaxSlots patterns, dense ones first. allow_cand = false
+// keeps every pattern on the dense scan (the write pass of a report); tb
+// (indexed by the caller's pattern index) gives each pattern's per-tile
+// counters for reports.
+void add_text(Tables& T, uint64_t off, uint64_t n, uint64_t slimit, const std::vector<const PatDesc*>& ds,
+              bool allow_cand = true, const std::vector<uint64_t>* tb = nullptr) {
     uint32_t ncand = 0;
     for (const PatDesc* d : ds) ncand += (!d->zero && d->cand) ? 1u : 0u;
-    const bool use_cand = ncand >= smk::kCandidateMin;
+    const bool use_cand = allow_cand && ncand >= smk::kCandidateMin;
     std::vector<const PatDesc*> order;
     for (const PatDesc* d : ds)
         if (!d->zero && !(use_cand && d->cand)) order.push_back(d);
@@ -428,6 +539,7 @@ void add_text(Tables& T, uint64_t off, uint64_t n, uint64_t slimit, const std::v
             const std::vector<uint32_t>& qc = c ? d->cqc : d->qc;
             BatchPat bp = c ? d->cpat : d->pat;
             bp.qc_off = (uint32_t)T.qc.size();
+            bp.tb = tb ? (*tb)[bp.out] : 0;
             T.qc.insert(T.qc.end(), qc.begin(), qc.end());
             if (c) mask[(qc[0] & 0xFFu) >> 5] |= 1u << (qc[0] & 31u);
             T.pats.push_back(bp);
@@ -497,9 +609,13 @@ Geometry geometry(sm_ctx* ctx, uint32_t maxm, bool need_index) {
     g.stages = sm_ctx_stages(ctx);
     // two resident CTAs per SM when the shared memory allows it
     while (g.stages > 2 && 2 * g.smem(kMaxSlots) > sm_ctx_max_smem(ctx)) --g.stages;
-    cudaFuncSetAttribute(smk::batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_ctx_max_smem(ctx));
+    const int ms = (int)sm_ctx_max_smem(ctx);
+    cudaFuncSetAttribute(smk::batch_kernel<smk::kBatchCount>, cudaFuncAttributeMaxDynamicSharedMemorySize, ms);
+    cudaFuncSetAttribute(smk::batch_kernel<smk::kBatchTileCount>, cudaFuncAttributeMaxDynamicSharedMemorySize, ms);
+    cudaFuncSetAttribute(smk::batch_kernel<smk::kBatchWrite>, cudaFuncAttributeMaxDynamicSharedMemorySize, ms);
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, smk::batch_kernel, smk::kThreads, g.smem(kMaxSlots));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, smk::batch_kernel<smk::kBatchTileCount>, smk::kThreads,
+                                                  g.smem(kMaxSlots));
     g.occ = std::max(occ, 1);
     return g;
 }
@@ -559,6 +675,55 @@ bool text_is_7bit(const uint32_t* h) {
     return true;
 }
 
+cudaError_t launch_batch(int mode, uint32_t grid, size_t smem, cudaStream_t st, const BatchArgs& a) {
+    if (!grid) return cudaSuccess;
+    switch (mode) {
+        case smk::kBatchCount: smk::batch_kernel<smk::kBatchCount><<<grid, smk::kThreads, smem, st>>>(a); break;
+        case smk::kBatchTileCount:
+            smk::batch_kernel<smk::kBatchTileCount><<<grid, smk::kThreads, smem, st>>>(a);
+            break;
+        default: smk::batch_kernel<smk::kBatchWrite><<<grid, smk::kThreads, smem, st>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+// Per-tile counters of a report: pattern k of length m[k] over a text of
+// len[k] bytes has nt = ceil((len - m + 1) / kTile) tiles (0 when m > len)
+// and counters [tb, tb + nt] (toff needs one more than tcnt). Returns the
+// total number of counters.
+uint64_t assign_tiles(const std::vector<uint32_t>& m, const std::vector<uint64_t>& len, std::vector<PatTiles>& pt,
+                      std::vector<uint64_t>& tb) {
+    const size_t np = m.size();
+    pt.resize(np);
+    tb.resize(np);
+    uint64_t o = 0;
+    for (size_t k = 0; k < np; ++k) {
+        const uint64_t nt = (uint64_t)m[k] > len[k] ? 0 : (len[k] - m[k] + 1 + smk::kTile - 1) / smk::kTile;
+        pt[k] = PatTiles{o, (uint32_t)nt, (uint32_t)k};
+        tb[k] = o;
+        o += nt + 1;
+    }
+    return o;
+}
+
+// The three passes of a report after the tables and counters are in place:
+// tile counts (and counts), per-pattern prefix sums, ordered writes.
+cudaError_t run_report(const BatchArgs& a1, uint32_t g1, size_t sm1, const BatchArgs& a2, uint32_t g2, size_t sm2,
+                       const PatTiles* d_pt, uint32_t npt, uint32_t* d_tcnt, uint64_t ntb, int64_t* d_counts,
+                       uint32_t ncounts, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    if (ncounts) e = cudaMemsetAsync(d_counts, 0, (size_t)ncounts * sizeof(int64_t), st);
+    if (e == cudaSuccess && ntb) e = cudaMemsetAsync(d_tcnt, 0, ntb * sizeof(uint32_t), st);
+    if (e == cudaSuccess) e = launch_batch(smk::kBatchTileCount, g1, sm1, st, a1);
+    if (e == cudaSuccess && npt) {
+        smk::batch_prefix_kernel<<<npt, smk::kPrefixThreads, 0, st>>>(d_pt, d_tcnt, const_cast<uint64_t*>(a2.toff),
+                                                                      a2.pos_off, a2.status);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = launch_batch(smk::kBatchWrite, g2, sm2, st, a2);
+    return e;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ batch
@@ -571,6 +736,16 @@ struct sm_batch {
     size_t smem = 0;
     BatchArgs args{};
     void* d_mem = nullptr;   // one allocation holding every table
+    // reports: the write pass's tables (dense scans only) and the
+    // per-(pattern, tile) counters, allocated by the first report
+    uint32_t wgrid = 0;
+    size_t wsmem = 0;
+    BatchArgs wargs{};
+    void* d_wmem = nullptr;
+    const PatTiles* d_pt = nullptr;   // in d_wmem, one per caller pattern
+    uint64_t ntb = 0;
+    uint32_t* d_tcnt = nullptr;
+    uint64_t* d_toff = nullptr;
 };
 
 extern "C" sm_status sm_batch_create(sm_ctx* ctx, const uint8_t* d_texts, const int64_t* h_text_off, uint32_t ntexts,
@@ -627,53 +802,75 @@ extern "C" sm_status sm_batch_create(sm_ctx* ctx, const uint8_t* d_texts, const 
         if (e != cudaSuccess) return sm_fail_internal(SM_ECUDA, cudaGetErrorString(e));
     }
 
-    // 2. patterns grouped by text, described under their text's frequencies
+    // 2. patterns described under their text's frequencies; per-tile
+    // counters for reports
+    std::vector<PatDesc> descs(npats);
+    std::vector<uint32_t> ms(npats);
+    std::vector<uint64_t> lens(npats);
+    for (uint32_t k = 0; k < npats; ++k) {
+        const uint32_t x = (uint32_t)h_pat_text[k];
+        const uint64_t n = (uint64_t)(h_text_off[x + 1] - h_text_off[x]);
+        const uint32_t* h = &hist[(size_t)x * 256];
+        const uint32_t delta = (uint32_t)((reinterpret_cast<uintptr_t>(d_texts) + (uint64_t)h_text_off[x]) & 15u);
+        ms[k] = (uint32_t)(h_pat_off[k + 1] - h_pat_off[k]);
+        lens[k] = n;
+        descs[k] = describe(h_pats + h_pat_off[k], ms[k], h, n, delta, text_is_7bit(h), k);
+    }
+    std::vector<PatTiles> pt;
+    std::vector<uint64_t> tb;
+    const uint64_t ntb = assign_tiles(ms, lens, pt, tb);
+    // tables of the counting (and tile-count) pass, and of the write pass
     std::vector<uint32_t> by_text(npats);
     std::iota(by_text.begin(), by_text.end(), 0u);
     std::stable_sort(by_text.begin(), by_text.end(),
                      [&](uint32_t a, uint32_t b) { return h_pat_text[a] < h_pat_text[b]; });
-    Tables T;
-    size_t kk = 0;
-    for (uint32_t x = 0; x < ntexts; ++x) {
-        const uint64_t n = (uint64_t)(h_text_off[x + 1] - h_text_off[x]);
-        const uint32_t* h = &hist[(size_t)x * 256];
-        const bool text7 = text_is_7bit(h);
-        const uint32_t delta = (uint32_t)((reinterpret_cast<uintptr_t>(d_texts) + (uint64_t)h_text_off[x]) & 15u);
-        std::vector<PatDesc> descs;
-        for (; kk < npats && (uint32_t)h_pat_text[by_text[kk]] == x; ++kk) {
-            const uint32_t k = by_text[kk];
-            descs.push_back(describe(h_pats + h_pat_off[k], (uint32_t)(h_pat_off[k + 1] - h_pat_off[k]), h, n, delta,
-                                     text7, k));
-        }
+    Tables T, W;
+    for (size_t kk = 0, x = 0; x < ntexts; ++x) {
         std::vector<const PatDesc*> ptrs;
-        for (const PatDesc& d : descs) ptrs.push_back(&d);
-        add_text(T, (uint64_t)h_text_off[x], n, ~0ull, ptrs);
+        for (; kk < npats && (uint32_t)h_pat_text[by_text[kk]] == x; ++kk) ptrs.push_back(&descs[by_text[kk]]);
+        const uint64_t n = (uint64_t)(h_text_off[x + 1] - h_text_off[x]);
+        add_text(T, (uint64_t)h_text_off[x], n, ~0ull, ptrs, true, &tb);
+        add_text(W, (uint64_t)h_text_off[x], n, ~0ull, ptrs, false, &tb);
     }
     const Geometry g = geometry(ctx, T.maxm, T.need_index);
     finish(T, (uint64_t)sm_ctx_num_sms(ctx) * g.occ);
+    const Geometry gw = geometry(ctx, W.maxm, false);
+    finish(W, (uint64_t)sm_ctx_num_sms(ctx) * gw.occ);
 
-    // 3. one allocation for every table
+    // 3. one allocation for each pass's tables (the write pass's also holds
+    // the per-pattern counter ranges)
     const Layout L = layout_of(T);
-    std::vector<char> host(L.total);
-    pack(T, L, host.data());
+    const Layout LW = layout_of(W);
+    const size_t pt_off = LW.total, wtotal = pt_off + std::max<size_t>(pt.size(), 1) * sizeof(PatTiles);
+    std::vector<char> host(std::max(L.total, wtotal));
     sm_batch* b = new sm_batch();
     b->ctx = ctx;
     b->device = sm_ctx_device(ctx);
     b->npats = npats;
-    if (cudaMalloc(&b->d_mem, L.total) != cudaSuccess) {
+    b->ntb = ntb;
+    if (cudaMalloc(&b->d_mem, L.total) != cudaSuccess || cudaMalloc(&b->d_wmem, wtotal) != cudaSuccess) {
         cudaGetLastError();
-        delete b;
+        sm_batch_destroy(b);
         return sm_fail_internal(SM_ENOMEM, "batch plan tables");
     }
-    const cudaError_t e = cudaMemcpy(b->d_mem, host.data(), L.total, cudaMemcpyHostToDevice);
+    pack(T, L, host.data());
+    cudaError_t e = cudaMemcpy(b->d_mem, host.data(), L.total, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        pack(W, LW, host.data());
+        if (!pt.empty()) std::memcpy(host.data() + pt_off, pt.data(), pt.size() * sizeof(PatTiles));
+        e = cudaMemcpy(b->d_wmem, host.data(), wtotal, cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
-        cudaFree(b->d_mem);
-        delete b;
+        sm_batch_destroy(b);
         return sm_fail_internal(SM_ECUDA, cudaGetErrorString(e));
     }
     b->args = args_for(ctx, d_texts, T, L, static_cast<char*>(b->d_mem), g);
     b->grid = (uint32_t)T.cta_pbase.size();
     b->smem = g.smem(T.nslots);
+    b->wargs = args_for(ctx, d_texts, W, LW, static_cast<char*>(b->d_wmem), gw);
+    b->wgrid = (uint32_t)W.cta_pbase.size();
+    b->wsmem = gw.smem(W.nslots);
+    b->d_pt = reinterpret_cast<const PatTiles*>(static_cast<char*>(b->d_wmem) + pt_off);
     *out = b;
     return SM_OK;
 }
@@ -685,12 +882,37 @@ extern "C" sm_status sm_batch_count(sm_batch* b, int64_t* d_counts, sm_stream_t 
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = cudaSuccess;
     if (b->npats) e = cudaMemsetAsync(d_counts, 0, (size_t)b->npats * sizeof(int64_t), st);
-    if (e == cudaSuccess && b->grid) {
+    if (e == cudaSuccess) {
         BatchArgs a = b->args;
         a.d_counts = d_counts;
-        smk::batch_kernel<<<b->grid, smk::kThreads, b->smem, st>>>(a);
-        e = cudaGetLastError();
+        e = launch_batch(smk::kBatchCount, b->grid, b->smem, st, a);
     }
+    return e == cudaSuccess ? SM_OK : sm_fail_internal(SM_ECUDA, cudaGetErrorString(e));
+}
+
+extern "C" sm_status sm_batch_report(sm_batch* b, int64_t* d_counts, uint64_t* d_pos, const int64_t* d_pos_off,
+                                     sm_stream_t stream) {
+    if (!b) return sm_fail_internal(SM_EINVAL, "batch is NULL");
+    if (b->npats && (!d_counts || !d_pos_off)) return sm_fail_internal(SM_EINVAL, "d_counts or d_pos_off is NULL");
+    Guard g(b->device);
+    if (!b->d_tcnt && b->ntb) {   // the counters, once per batch
+        if (cudaMalloc(&b->d_tcnt, b->ntb * sizeof(uint32_t)) != cudaSuccess ||
+            cudaMalloc(&b->d_toff, b->ntb * sizeof(uint64_t)) != cudaSuccess) {
+            cudaGetLastError();
+            if (b->d_tcnt) cudaFree(b->d_tcnt);
+            b->d_tcnt = nullptr;
+            return sm_fail_internal(SM_ENOMEM, "report tile counters");
+        }
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    BatchArgs a1 = b->args, a2 = b->wargs;
+    a1.d_counts = d_counts;
+    a1.tcnt = b->d_tcnt;
+    a2.toff = b->d_toff;
+    a2.d_pos = d_pos;
+    a2.pos_off = d_pos_off;
+    const cudaError_t e = run_report(a1, b->grid, b->smem, a2, b->wgrid, b->wsmem, b->d_pt, b->npats, b->d_tcnt,
+                                     b->ntb, d_counts, b->npats, st);
     return e == cudaSuccess ? SM_OK : sm_fail_internal(SM_ECUDA, cudaGetErrorString(e));
 }
 
@@ -699,6 +921,9 @@ extern "C" void sm_batch_destroy(sm_batch* b) {
     Guard g(b->device);
     cudaDeviceSynchronize();
     if (b->d_mem) cudaFree(b->d_mem);
+    if (b->d_wmem) cudaFree(b->d_wmem);
+    if (b->d_tcnt) cudaFree(b->d_tcnt);
+    if (b->d_toff) cudaFree(b->d_toff);
     delete b;
 }
 
@@ -711,14 +936,12 @@ extern "C" sm_status sm_count_batch(sm_ctx* ctx, const uint8_t* d_texts, const i
     if (d_pos && !d_pos_off) return sm_fail_internal(SM_EINVAL, "d_pos needs d_pos_off");
     Guard g(sm_ctx_device(ctx));
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    std::vector<int64_t> text_off(ntexts + 1), pat_off(npats + 1), pos_off(d_pos ? npats + 1 : 0);
+    std::vector<int64_t> text_off(ntexts + 1), pat_off(npats + 1);
     std::vector<int32_t> pat_text(npats);
     cudaError_t e = cudaMemcpyAsync(text_off.data(), d_text_off, text_off.size() * 8, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && npats) {
         e = cudaMemcpyAsync(pat_off.data(), d_pat_off, pat_off.size() * 8, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(pat_text.data(), d_pat_text, pat_text.size() * 4, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess && d_pos)
-            e = cudaMemcpyAsync(pos_off.data(), d_pos_off, pos_off.size() * 8, cudaMemcpyDeviceToHost, st);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return sm_fail_internal(SM_ECUDA, cudaGetErrorString(e));
@@ -731,25 +954,8 @@ extern "C" sm_status sm_count_batch(sm_ctx* ctx, const uint8_t* d_texts, const i
     sm_status s = sm_batch_create(ctx, d_texts, text_off.data(), ntexts, pats.data(), pat_off.data(),
                                   pat_text.data(), npats, &b, stream);
     if (s != SM_OK) return s;
-    s = sm_batch_count(b, d_counts, stream);
-    if (s == SM_OK && d_pos) {
-        // positions: one ordered report per pattern into its slice of d_pos
-        uint64_t* d_tmp = nullptr;
-        if (cudaMalloc(&d_tmp, sizeof(uint64_t)) != cudaSuccess) {
-            cudaGetLastError();
-            s = sm_fail_internal(SM_ENOMEM, "report count");
-        }
-        for (uint32_t k = 0; s == SM_OK && k < npats; ++k) {
-            const int64_t cap = pos_off[k + 1] - pos_off[k];
-            if (cap <= 0) continue;
-            const int32_t x = pat_text[k];
-            s = sm_report(ctx, d_texts + text_off[x], (uint64_t)(text_off[x + 1] - text_off[x]),
-                          pats.data() + pat_off[k], (uint32_t)(pat_off[k + 1] - pat_off[k]), nullptr,
-                          d_pos + pos_off[k], (uint64_t)cap, d_tmp, stream);
-        }
-        cudaStreamSynchronize(st);
-        if (d_tmp) cudaFree(d_tmp);
-    }
+    // positions: the batched report (ordered positions of every pattern into its slice of d_pos)
+    s = d_pos ? sm_batch_report(b, d_counts, d_pos, d_pos_off, stream) : sm_batch_count(b, d_counts, stream);
     cudaStreamSynchronize(st);
     sm_batch_destroy(b);
     return s;
@@ -781,9 +987,33 @@ struct sm_stepper {
         size_t cap = 0;
         cudaEvent_t ev = nullptr;
         bool used = false;
-    } buf[2];
+    } buf[2], rbuf;            // step tables (alternating); report tables
     int cur = 0;
+    uint32_t* d_tcnt = nullptr;   // report counters
+    uint64_t* d_toff = nullptr;
+    uint64_t rcap = 0;
 };
+
+namespace {
+
+// Grows a table buffer (pinned host staging and its device copy) to `need` bytes.
+bool grow_buf(sm_stepper::Buf& b, size_t need) {
+    if (b.cap >= need) return true;
+    const size_t cap = std::max(need, 2 * b.cap);
+    if (b.h) cudaFreeHost(b.h);
+    if (b.d) cudaFree(b.d);
+    b.h = nullptr;
+    b.d = nullptr;
+    b.cap = 0;
+    if (cudaMallocHost(&b.h, cap) != cudaSuccess || cudaMalloc(&b.d, cap) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    b.cap = cap;
+    return true;
+}
+
+}  // namespace
 
 extern "C" sm_status sm_stepper_create(sm_ctx* ctx, const uint8_t* d_text, uint64_t n, uint64_t chunk_bytes,
                                        uint32_t max_m, const uint64_t* h_hist256, sm_stepper** out) {
@@ -806,8 +1036,8 @@ extern "C" sm_status sm_stepper_create(sm_ctx* ctx, const uint8_t* d_text, uint6
     for (int c = 0; c < 256; ++c) s->hist[c] = (uint32_t)std::min<uint64_t>(h_hist256[c], 0xFFFFFFFFull);
     s->text7 = text_is_7bit(s->hist);
     s->geo = geometry(ctx, max_m, true);
-    for (auto& b : s->buf)
-        if (cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming) != cudaSuccess) {
+    for (auto* b : {&s->buf[0], &s->buf[1], &s->rbuf})
+        if (cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
             sm_stepper_destroy(s);
             return sm_fail_internal(SM_ECUDA, "event");
@@ -858,29 +1088,92 @@ extern "C" sm_status sm_stepper_step(sm_stepper* s, const uint32_t* h_qids, uint
     sm_stepper::Buf& b = s->buf[s->cur];
     s->cur ^= 1;
     if (b.used && cudaEventSynchronize(b.ev) != cudaSuccess) return sm_fail_internal(SM_ECUDA, "event wait");
-    if (b.cap < L.total) {
-        const size_t cap = std::max(L.total, 2 * b.cap);
-        if (b.h) cudaFreeHost(b.h);
-        if (b.d) cudaFree(b.d);
-        b.h = nullptr;
-        b.d = nullptr;
-        b.cap = 0;
-        if (cudaMallocHost(&b.h, cap) != cudaSuccess || cudaMalloc(&b.d, cap) != cudaSuccess) {
-            cudaGetLastError();
-            return sm_fail_internal(SM_ENOMEM, "stepper tables");
-        }
-        b.cap = cap;
-    }
+    if (!grow_buf(b, L.total)) return sm_fail_internal(SM_ENOMEM, "stepper tables");
     pack(T, L, b.h);
     cudaError_t e = cudaMemcpyAsync(b.d, b.h, L.total, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) {
         BatchArgs a = args_for(s->ctx, s->d_text, T, L, b.d, s->geo);
         a.d_counts = d_counts;
-        smk::batch_kernel<<<(uint32_t)T.cta_pbase.size(), smk::kThreads, s->geo.smem(T.nslots), st>>>(a);
-        e = cudaGetLastError();
+        e = launch_batch(smk::kBatchCount, (uint32_t)T.cta_pbase.size(), s->geo.smem(T.nslots), st, a);
     }
     if (e == cudaSuccess) e = cudaEventRecord(b.ev, st);
     b.used = true;
+    return e == cudaSuccess ? SM_OK : sm_fail_internal(SM_ECUDA, cudaGetErrorString(e));
+}
+
+extern "C" sm_status sm_stepper_report(sm_stepper* s, const uint8_t* h_pats, const int64_t* h_pat_off, uint32_t nq,
+                                       const int64_t* h_pos_off, uint64_t* d_pos, int64_t* d_counts,
+                                       sm_stream_t stream) {
+    if (!s || (nq && (!h_pats || !h_pat_off || !h_pos_off || !d_counts))) return sm_fail_internal(SM_EINVAL, "NULL argument");
+    if (nq && h_pos_off[nq] > h_pos_off[0] && !d_pos) return sm_fail_internal(SM_EINVAL, "d_pos is NULL");
+    for (uint32_t k = 0; k < nq; ++k) {
+        const int64_t m = h_pat_off[k + 1] - h_pat_off[k];
+        if (m < 1 || m > (int64_t)SM_MAX_M) return sm_fail_internal(SM_EINVAL, "pattern length out of range");
+        if (h_pos_off[k + 1] < h_pos_off[k]) return sm_fail_internal(SM_EINVAL, "position offsets must not decrease");
+    }
+    if (!nq) return SM_OK;
+    Guard g(s->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    // the previous report's tables and counters are reused
+    if (s->rbuf.used && cudaEventSynchronize(s->rbuf.ev) != cudaSuccess) return sm_fail_internal(SM_ECUDA, "event wait");
+    std::vector<PatDesc> descs(nq);
+    std::vector<const PatDesc*> ptrs(nq);
+    std::vector<uint32_t> ms(nq);
+    std::vector<uint64_t> lens(nq, s->n);
+    for (uint32_t k = 0; k < nq; ++k) {
+        ms[k] = (uint32_t)(h_pat_off[k + 1] - h_pat_off[k]);
+        descs[k] = describe(h_pats + h_pat_off[k], ms[k], s->hist, s->n, s->delta, s->text7, k);
+        ptrs[k] = &descs[k];
+    }
+    std::vector<PatTiles> pt;
+    std::vector<uint64_t> tb;
+    const uint64_t ntb = assign_tiles(ms, lens, pt, tb);
+    Tables T, W;
+    add_text(T, 0, s->n, ~0ull, ptrs, true, &tb);
+    add_text(W, 0, s->n, ~0ull, ptrs, false, &tb);
+    const Geometry g1 = geometry(s->ctx, std::max(T.maxm, 1u), T.need_index);
+    finish(T, (uint64_t)sm_ctx_num_sms(s->ctx) * g1.occ);
+    const Geometry g2 = geometry(s->ctx, std::max(W.maxm, 1u), false);
+    finish(W, (uint64_t)sm_ctx_num_sms(s->ctx) * g2.occ);
+    const Layout L = layout_of(T), LW = layout_of(W);
+    const size_t o_w = L.total, o_pt = o_w + LW.total, o_po = o_pt + ((pt.size() * sizeof(PatTiles) + 255) & ~(size_t)255);
+    const size_t total = o_po + (size_t)(nq + 1) * sizeof(int64_t);
+    if (!grow_buf(s->rbuf, total)) return sm_fail_internal(SM_ENOMEM, "report tables");
+    if (s->rcap < ntb) {
+        const uint64_t cap = std::max<uint64_t>(ntb, 2 * s->rcap);
+        if (s->d_tcnt) cudaFree(s->d_tcnt);
+        if (s->d_toff) cudaFree(s->d_toff);
+        s->d_tcnt = nullptr;
+        s->d_toff = nullptr;
+        s->rcap = 0;
+        if (cudaMalloc(&s->d_tcnt, cap * sizeof(uint32_t)) != cudaSuccess ||
+            cudaMalloc(&s->d_toff, cap * sizeof(uint64_t)) != cudaSuccess) {
+            cudaGetLastError();
+            return sm_fail_internal(SM_ENOMEM, "report tile counters");
+        }
+        s->rcap = cap;
+    }
+    char* h = s->rbuf.h;
+    char* d = s->rbuf.d;
+    pack(T, L, h);
+    pack(W, LW, h + o_w);
+    std::memcpy(h + o_pt, pt.data(), pt.size() * sizeof(PatTiles));
+    for (uint32_t k = 0; k <= nq; ++k) reinterpret_cast<int64_t*>(h + o_po)[k] = h_pos_off[k] - h_pos_off[0];
+    cudaError_t e = cudaMemcpyAsync(d, h, total, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        BatchArgs a1 = args_for(s->ctx, s->d_text, T, L, d, g1);
+        BatchArgs a2 = args_for(s->ctx, s->d_text, W, LW, d + o_w, g2);
+        a1.d_counts = d_counts;
+        a1.tcnt = s->d_tcnt;
+        a2.toff = s->d_toff;
+        a2.d_pos = d_pos ? d_pos + h_pos_off[0] : nullptr;
+        a2.pos_off = reinterpret_cast<const int64_t*>(d + o_po);
+        e = run_report(a1, (uint32_t)T.cta_pbase.size(), g1.smem(T.nslots), a2, (uint32_t)W.cta_pbase.size(),
+                       g2.smem(W.nslots), reinterpret_cast<const PatTiles*>(d + o_pt), nq, s->d_tcnt, ntb, d_counts,
+                       nq, st);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(s->rbuf.ev, st);
+    s->rbuf.used = true;
     return e == cudaSuccess ? SM_OK : sm_fail_internal(SM_ECUDA, cudaGetErrorString(e));
 }
 
@@ -888,10 +1181,12 @@ extern "C" void sm_stepper_destroy(sm_stepper* s) {
     if (!s) return;
     Guard g(s->device);
     cudaDeviceSynchronize();
-    for (auto& b : s->buf) {
-        if (b.h) cudaFreeHost(b.h);
-        if (b.d) cudaFree(b.d);
-        if (b.ev) cudaEventDestroy(b.ev);
+    for (auto* b : {&s->buf[0], &s->buf[1], &s->rbuf}) {
+        if (b->h) cudaFreeHost(b->h);
+        if (b->d) cudaFree(b->d);
+        if (b->ev) cudaEventDestroy(b->ev);
     }
+    if (s->d_tcnt) cudaFree(s->d_tcnt);
+    if (s->d_toff) cudaFree(s->d_toff);
     delete s;
 }

@@ -5,9 +5,10 @@ the next chunk for all active queries in one batched launch
 (``sm_stepper_step``), so queries in flight share each pass over the text.
 A query is admitted whenever a counter slot is free -- it joins at whatever
 chunk comes next -- and its count is complete after one step on every chunk.
-A report query then needs a position buffer of exactly count x 8 bytes; it is
-admitted when the report memory budget has room, and its positions are
-written by ``sm_report`` on a second stream while the next steps run.
+A report query then needs a position buffer of exactly count x 8 bytes; the
+report queries waiting when no report batch is in flight are admitted up to
+the report memory budget and reported together (``sm_stepper_report``: one
+batched report over the text) on a second stream while the next steps run.
 
 Every query's result is the same as when it runs alone (the tests check
 this against single calls and the CPU oracle).
@@ -56,6 +57,9 @@ def _bind_stepper():
     lib.sm_stepper_step.restype = st
     lib.sm_stepper_retire.argtypes = [vp, C.c_uint32]
     lib.sm_stepper_retire.restype = st
+    i64p = C.POINTER(C.c_int64)
+    lib.sm_stepper_report.argtypes = [vp, u8p, i64p, C.c_uint32, i64p, vp, vp, vp]
+    lib.sm_stepper_report.restype = st
     lib.sm_stepper_destroy.argtypes = [vp]
     lib.sm_stepper_destroy.restype = None
     lib._stepper_bound = True
@@ -72,8 +76,7 @@ class Server:
         self.text = text
         self.dev = text.device
         self.lib = _bind_stepper()
-        self.ctx = sm.sm_create(self.dev.index or 0)           # steps, on self.stream
-        self.rctx = sm.sm_create(self.dev.index or 0)          # reports, on self.rstream
+        self.ctx = sm.sm_create(self.dev.index or 0)           # steps on self.stream, reports on self.rstream
         self.stream = torch.cuda.Stream(device=self.dev)
         self.rstream = torch.cuda.Stream(device=self.dev)
         self.hist = sm.sm_histogram(self.ctx, text, stream=self.stream)
@@ -198,32 +201,50 @@ class Server:
                     q.done = now
                     self.done.append(q)
         self.finishing = keep
-        # reports: admitted by the memory their position buffers need
+        # a finished report batch: its queries are done
+        keep = []
+        for ev, qs, need in self.reporting:
+            if ev.query():
+                now = self.now()
+                for q in qs:
+                    q.done = now
+                    self.done.append(q)
+                self.report_reserved -= need
+            else:
+                keep.append((ev, qs, need))
+        self.reporting = keep
+        # the next report batch (one in flight): the waiting report queries
+        # whose position buffers (count x 8 bytes) fit the memory budget,
+        # reported together in one batched pass over the text
+        if self.reporting or not self.report_wait:
+            return
+        batch, need = [], 0
         while self.report_wait:
             q = self.report_wait[0]
-            need = max(q.count, 1) * 8
-            if self.report_reserved and self.report_reserved + need > self.report_budget:
+            b = max(q.count, 1) * 8
+            if batch and need + b > self.report_budget:
                 break
             self.report_wait.popleft()
-            self.report_reserved += need
-            with torch.cuda.stream(self.rstream):
-                pos = torch.empty(max(q.count, 1), dtype=torch.int64, device=self.dev)
-                cnt = torch.empty(1, dtype=torch.int64, device=self.dev)
-            sm.sm_report(self.rctx, self.text, q.pattern, q.count, pi=sm.sm_order(q.pattern, self.hist),
-                         out_pos=pos, out_count=cnt, stream=self.rstream, hist=self.hist)
-            ev = torch.cuda.Event()
-            ev.record(self.rstream)
-            q.positions = pos[: q.count]
-            self.reporting.append((ev, q, need))
-        keep = []
-        for ev, q, need in self.reporting:
-            if ev.query():
-                q.done = self.now()
-                self.report_reserved -= need
-                self.done.append(q)
-            else:
-                keep.append((ev, q, need))
-        self.reporting = keep
+            batch.append(q)
+            need += b
+        pos_off = np.zeros(len(batch) + 1, np.int64)
+        pos_off[1:] = np.cumsum([q.count for q in batch])
+        pat_off = np.zeros(len(batch) + 1, np.int64)
+        pat_off[1:] = np.cumsum([len(q.pattern) for q in batch])
+        flat = np.frombuffer(b"".join(q.pattern for q in batch), np.uint8)
+        with torch.cuda.stream(self.rstream):
+            pos = torch.empty(max(int(pos_off[-1]), 1), dtype=torch.int64, device=self.dev)
+            cnt = torch.empty(len(batch), dtype=torch.int64, device=self.dev)
+        sm._check(self.lib.sm_stepper_report(
+            self.stepper, flat.ctypes.data_as(C.POINTER(C.c_uint8)), pat_off.ctypes.data_as(C.POINTER(C.c_int64)),
+            len(batch), pos_off.ctypes.data_as(C.POINTER(C.c_int64)), pos.data_ptr(), cnt.data_ptr(),
+            self.rstream.cuda_stream))
+        ev = torch.cuda.Event()
+        ev.record(self.rstream)
+        for k, q in enumerate(batch):
+            q.positions = pos[pos_off[k]:pos_off[k + 1]]
+        self.report_reserved += need
+        self.reporting.append((ev, batch, need))
 
     # ------------------------------------------------------------ drivers
     def run(self, queries: list[Query], time_scale: float = 1.0, max_steps: int | None = None) -> list[Query]:

@@ -25,9 +25,9 @@ SM_NOALLOC_MAX_STARTS = 16384 * 16384
 # Every symbol the header declares (checked against include/sm.h by the tests).
 EXPORTS = ("sm_create", "sm_destroy", "sm_last_error", "sm_status_string", "sm_sync", "sm_set_knob",
            "sm_histogram", "sm_order", "sm_order_fixed", "sm_count", "sm_count_ex", "sm_report",
-           "sm_report_ex", "sm_report_noalloc", "sm_batch_create", "sm_batch_count", "sm_batch_destroy",
-           "sm_count_batch", "sm_stepper_create", "sm_stepper_chunks", "sm_stepper_admit", "sm_stepper_step",
-           "sm_stepper_retire", "sm_stepper_destroy")
+           "sm_report_ex", "sm_report_noalloc", "sm_batch_create", "sm_batch_count", "sm_batch_report",
+           "sm_batch_destroy", "sm_count_batch", "sm_stepper_create", "sm_stepper_chunks", "sm_stepper_admit",
+           "sm_stepper_step", "sm_stepper_retire", "sm_stepper_report", "sm_stepper_destroy")
 
 
 class SmError(RuntimeError):
@@ -80,6 +80,7 @@ def load():
         "sm_batch_create": (st, [vp, vp, C.POINTER(C.c_int64), u32, u8p, C.POINTER(C.c_int64),
                                  C.POINTER(C.c_int32), u32, C.POINTER(vp), vp]),
         "sm_batch_count": (st, [vp, vp, vp]),
+        "sm_batch_report": (st, [vp, vp, vp, vp, vp]),
         "sm_batch_destroy": (None, [vp]),
         "sm_count_batch": (st, [vp, vp, vp, u32, vp, vp, vp, u32, vp, vp, vp, vp]),
     }
@@ -301,6 +302,20 @@ def sm_batch_count(batch: Batch, out=None, stream=None):
         out = torch.empty(max(batch.npats, 1), dtype=torch.int64, device=batch.texts.device)
     _check(load().sm_batch_count(batch.handle, _dev_ptr(out, _WORD64), _stream(stream)))
     return out
+
+
+def sm_batch_report(batch: Batch, d_pos_off, d_pos=None, out=None, stream=None):
+    """Enqueue the batched report: positions of pattern k, ascending, into
+    d_pos[d_pos_off[k] .. d_pos_off[k+1]) (d_pos_off: int64 CUDA tensor,
+    npats + 1 entries; d_pos allocated when None). Returns (counts, d_pos)."""
+    import torch
+    if out is None:
+        out = torch.empty(max(batch.npats, 1), dtype=torch.int64, device=batch.texts.device)
+    if d_pos is None:
+        d_pos = torch.empty(max(int(d_pos_off[-1].item()), 1), dtype=torch.int64, device=batch.texts.device)
+    _check(load().sm_batch_report(batch.handle, _dev_ptr(out, _WORD64), _dev_ptr(d_pos, _WORD64),
+                                  _dev_ptr(d_pos_off, _WORD64), _stream(stream)))
+    return out, d_pos
 
 
 def sm_count_batch(ctx: Ctx, texts, d_text_off, d_pats, d_pat_off, d_pat_text, d_counts, d_pos=None,

@@ -128,8 +128,76 @@ def test_count_batch_device_metadata_with_positions(torch, ctx):
     counts = torch.zeros(len(pats), dtype=torch.int64, device="cuda")
     dpos = torch.zeros(max(int(poff[-1]), 1), dtype=torch.int64, device="cuda")
     sm.sm_count_batch(ctx, d, T(off), T(pflat), T(pat_off), T(pt), counts, dpos, T(poff))
+    assert sm.sm_sync(ctx) == (sm.SM_ETRUNC if (caps < want).any() else sm.SM_OK)
     assert np.array_equal(counts.cpu().numpy(), want)
     allpos = dpos.cpu().numpy().view(np.uint64)
     for k, (p, x) in enumerate(zip(pats, pt)):
         pos, c = oracle.naive_report(p, texts[x])
         assert np.array_equal(allpos[poff[k]:poff[k + 1]], pos[: caps[k]])
+
+
+def oracle_positions(texts, pats, pt, caps):
+    out = []
+    for p, x, c in zip(pats, pt, caps):
+        pos, _ = oracle.naive_report(p, texts[x])
+        out.append(pos[:c])
+    return out
+
+
+@pytest.mark.parametrize("seed,per_text", [(21, 6), (22, 40)])
+def test_batch_report_mixed(torch, ctx, seed, per_text):
+    # ordered positions of every pattern in one batched report: dense and
+    # candidate counting passes, empty and tiny texts, truncated capacities
+    sizes = [0, 1, 17, 5000, 40_000, 3 * 16384 + 11, 200_000, 7]
+    kinds = [4, 20, "markov95", 256, 4, 2, "markov95", 64]
+    texts, flat, off, pats, pt = make_batch(seed, sizes, kinds, per_text, 600)
+    want = expected(texts, pats, pt)
+    d = to_dev(torch, flat)
+    b = sm.sm_batch_create(ctx, d, off, pats, pt)
+    sm.sm_sync(ctx)   # no status left from earlier calls
+    for trunc in (False, True):
+        caps = np.minimum(want, 7) if trunc else want
+        poff = np.zeros(len(pats) + 1, np.int64)
+        poff[1:] = np.cumsum(caps)
+        d_off = torch.from_numpy(poff).cuda()
+        counts, dpos = sm.sm_batch_report(b, d_off)
+        st = sm.sm_sync(ctx)
+        assert st == (sm.SM_ETRUNC if trunc and (caps < want).any() else sm.SM_OK)
+        assert np.array_equal(counts.cpu().numpy()[: len(pats)], want)
+        allpos = dpos.cpu().numpy().view(np.uint64)
+        for k, pos in enumerate(oracle_positions(texts, pats, pt, caps)):
+            assert np.array_equal(allpos[poff[k]:poff[k + 1]], pos), (k, len(pats[k]), pt[k])
+    # counting with the same plan still works after a report
+    assert np.array_equal(sm.sm_batch_count(b).cpu().numpy()[: len(pats)], want)
+
+
+def test_batch_report_dense_matches(torch, ctx):
+    # short patterns on small alphabets: matches in almost every tile, many
+    # patterns per text (the candidate counting pass on the byte text)
+    t2 = synth.uniform(5 * 16384 + 333, 2, seed=0, stream=31)
+    t4 = synth.uniform(7 * 16384 + 5, 4, seed=0, stream=32)
+    tm = synth.markov95(300_000, seed=0, stream=33)
+    texts = [t2, t4, tm]
+    r = np.random.default_rng(34)
+    pats, pt = [], []
+    for x, t in enumerate(texts):
+        for _ in range(30):
+            m = int(r.integers(1, 9))
+            s0 = int(r.integers(0, t.size - m + 1))
+            pats.append(t[s0:s0 + m].tobytes())
+            pt.append(x)
+    off = np.zeros(4, np.int64)
+    off[1:] = np.cumsum([t.size for t in texts])
+    flat = np.concatenate(texts)
+    want = expected(texts, pats, pt)
+    d = to_dev(torch, flat, 5)
+    b = sm.sm_batch_create(ctx, d, off, pats, np.array(pt, np.int32))
+    sm.sm_sync(ctx)
+    poff = np.zeros(len(pats) + 1, np.int64)
+    poff[1:] = np.cumsum(want)
+    counts, dpos = sm.sm_batch_report(b, torch.from_numpy(poff).cuda())
+    assert sm.sm_sync(ctx) == sm.SM_OK
+    assert np.array_equal(counts.cpu().numpy(), want)
+    allpos = dpos.cpu().numpy().view(np.uint64)
+    for k, pos in enumerate(oracle_positions(texts, pats, pt, want)):
+        assert np.array_equal(allpos[poff[k]:poff[k + 1]], pos), k

@@ -76,3 +76,42 @@ def test_stepper_joins_at_any_chunk(torch):
     torch.cuda.synchronize()
     for q in qs:
         assert q.count == oracle.count_threads(q.pattern, t)
+
+
+def test_stepper_report_batch(torch):
+    # one batched report of many patterns over the resident text: absent
+    # symbols, m up to 4096, zero capacities, truncation
+    import ctypes as C
+    from paper_1612_01506_gb300.serve import Server
+    t = make_text(1 << 20)
+    text = torch.from_numpy(t).cuda()
+    server = Server(text, chunk_bytes=1 << 18, max_m=4096, max_active=8)
+    r = np.random.default_rng(5)
+    pats = []
+    for m in (1, 2, 3, 5, 8, 13, 40, 100, 700, 4096):
+        for _ in range(3):
+            s0 = int(r.integers(0, t.size - m + 1))
+            pats.append(t[s0:s0 + m].tobytes())
+    pats += [b"\x01ACGT", b"e" * 3, b"ACGT" * 7]
+    want = [oracle.count_threads(p, t) for p in pats]
+    for caps in (want, [min(c, 3) if k % 2 else c for k, c in enumerate(want)]):
+        pos_off = np.zeros(len(pats) + 1, np.int64)
+        pos_off[1:] = np.cumsum(caps)
+        pat_off = np.zeros(len(pats) + 1, np.int64)
+        pat_off[1:] = np.cumsum([len(p) for p in pats])
+        flat = np.frombuffer(b"".join(pats), np.uint8)
+        pos = torch.empty(max(int(pos_off[-1]), 1), dtype=torch.int64, device="cuda")
+        cnt = torch.empty(len(pats), dtype=torch.int64, device="cuda")
+        st = server.lib.sm_stepper_report(server.stepper, flat.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                          pat_off.ctypes.data_as(C.POINTER(C.c_int64)), len(pats),
+                                          pos_off.ctypes.data_as(C.POINTER(C.c_int64)), pos.data_ptr(),
+                                          cnt.data_ptr(), server.rstream.cuda_stream)
+        assert st == sm.SM_OK
+        server.rstream.synchronize()
+        trunc = any(c < w for c, w in zip(caps, want))
+        assert sm.sm_sync(server.ctx) == (sm.SM_ETRUNC if trunc else sm.SM_OK)
+        assert np.array_equal(cnt.cpu().numpy(), np.array(want, np.int64))
+        allpos = pos.cpu().numpy().view(np.uint64)
+        for k, p in enumerate(pats):
+            w, _ = oracle.report_threads(p, t, want[k])
+            assert np.array_equal(allpos[pos_off[k]:pos_off[k + 1]], w[: caps[k]]), (k, len(p))

@@ -78,6 +78,7 @@ struct PatTiles {
     uint64_t tb;
     uint32_t nt;
     uint32_t out;         // index of the pattern in the caller's arrays
+    uint64_t witem;       // the write pass's work item of the pattern's tile 0
 };
 
 struct BatchArgs {
@@ -94,6 +95,7 @@ struct BatchArgs {
     const uint64_t* toff;       // write: per-(pattern, tile) ranks of the first match
     uint64_t* d_pos;            // write: positions of pattern `out` go to d_pos + pos_off[out] ...
     const int64_t* pos_off;     // ... at most pos_off[out + 1] - pos_off[out] of them
+    const uint8_t* hit;         // write: 1 for the work items (tiles) where some pattern matches
     uint32_t stage_bytes, stages, one, nslots;
     uint32_t index_cap;         // entries of the per-tile position index (0: no index)
     uint32_t* status;
@@ -163,6 +165,8 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constan
             uint8_t* buf = bufs + (size_t)s * SB;
             BatchDesc d{0, ~0u, 0};
             TileCopy cp{0, 0, 0};
+            if (MODE == kBatchWrite)   // only tiles with matches are staged again
+                while (cursor < i1 && !__ldg(A.hit + cursor)) ++cursor;
             if (cursor < i1) {
                 const uint64_t item = cursor++;
                 while (A.tx[x + 1].item_begin <= item) ++x;
@@ -351,7 +355,7 @@ __global__ void __launch_bounds__(kPrefixThreads) batch_prefix_kernel(const PatT
                                                                       const uint32_t* __restrict__ tcnt,
                                                                       uint64_t* __restrict__ toff,
                                                                       const int64_t* __restrict__ pos_off,
-                                                                      uint32_t* status) {
+                                                                      uint8_t* __restrict__ hit, uint32_t* status) {
     __shared__ uint64_t wsum[kPrefixThreads / 32];
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const PatTiles P = pt[blockIdx.x];
@@ -376,7 +380,10 @@ __global__ void __launch_bounds__(kPrefixThreads) batch_prefix_kernel(const PatT
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const uint64_t k = base + 4u * tid + i;
-            if (k < P.nt) toff[P.tb + k] = run;
+            if (k < P.nt) {
+                toff[P.tb + k] = run;
+                if (v[i]) hit[P.witem + k] = 1;
+            }
             run += v[i];
         }
         carry = total;
@@ -388,10 +395,11 @@ __global__ void __launch_bounds__(kPrefixThreads) batch_prefix_kernel(const PatT
     }
 }
 
-// Per-text byte histograms: work item = (text, 64 KiB chunk).
-__global__ void __launch_bounds__(256) batch_hist_kernel(const uint8_t* texts, const int64_t* off,
+// Byte histograms of ranges texts[beg[x] .. end[x]): work item = (range,
+// 64 KiB piece).
+__global__ void __launch_bounds__(256) batch_hist_kernel(const uint8_t* texts, const int64_t* beg, const int64_t* end,
                                                          const uint64_t* chunk_begin, uint32_t ntexts,
-                                                         uint64_t nchunks, uint32_t* hist) {
+                                                         uint64_t nchunks, unsigned long long* hist) {
     __shared__ uint32_t h[8][256];
     const uint32_t tid = threadIdx.x, warp = tid >> 5;
     for (uint64_t item = blockIdx.x; item < nchunks; item += gridDim.x) {
@@ -403,16 +411,16 @@ __global__ void __launch_bounds__(256) batch_hist_kernel(const uint8_t* texts, c
             if (chunk_begin[mid] <= item) lo = mid; else hi = mid;
         }
         const uint32_t x = lo;
-        const uint64_t n = (uint64_t)(off[x + 1] - off[x]);
+        const uint64_t n = (uint64_t)(end[x] - beg[x]);
         const uint64_t b0 = (item - chunk_begin[x]) * kHistChunk;
         const uint64_t b1 = min(b0 + kHistChunk, n);
-        const uint8_t* t = texts + off[x];
+        const uint8_t* t = texts + beg[x];
         for (uint64_t i = b0 + tid; i < b1; i += 256) atomicAdd(&h[warp][t[i]], 1u);
         __syncthreads();
         {
             uint32_t v = 0;
             for (int w = 0; w < 8; ++w) v += h[w][tid];
-            if (v) atomicAdd(&hist[(uint64_t)x * 256 + tid], v);
+            if (v) atomicAdd(&hist[(uint64_t)x * 256 + tid], (unsigned long long)v);
         }
         __syncthreads();
     }
@@ -467,7 +475,7 @@ struct PatDesc {
     bool zero = false;   // a symbol never occurs in the text, or m > n: count 0
 };
 
-PatDesc describe(const uint8_t* p, uint32_t m, const uint32_t* h, uint64_t n, uint32_t delta, bool text7,
+PatDesc describe(const uint8_t* p, uint32_t m, const uint64_t* h, uint64_t n, uint32_t delta, bool text7,
                  uint32_t out) {
     PatDesc d;
     d.zero = (uint64_t)m > n;
@@ -505,15 +513,18 @@ struct Tables {
     uint64_t items = 0;
     uint32_t nslots = 1, maxm = 1;
     bool need_index = false;
+    uint32_t slot_hint() const { return (uint32_t)std::min<size_t>(pats.size(), kMaxSlots); }
 };
 
 // Entries for one text region [off, off + n) counting starts below slimit:
 // groups of at most kMaxSlots patterns, dense ones first. allow_cand = false
 // keeps every pattern on the dense scan (the write pass of a report); tb
 // (indexed by the caller's pattern index) gives each pattern's per-tile
-// counters for reports.
+// counters for reports; pt, when given, receives each pattern's first work
+// item.
 void add_text(Tables& T, uint64_t off, uint64_t n, uint64_t slimit, const std::vector<const PatDesc*>& ds,
-              bool allow_cand = true, const std::vector<uint64_t>* tb = nullptr) {
+              bool allow_cand = true, const std::vector<uint64_t>* tb = nullptr,
+              std::vector<PatTiles>* pt = nullptr) {
     uint32_t ncand = 0;
     for (const PatDesc* d : ds) ncand += (!d->zero && d->cand) ? 1u : 0u;
     const bool use_cand = allow_cand && ncand >= smk::kCandidateMin;
@@ -540,6 +551,7 @@ void add_text(Tables& T, uint64_t off, uint64_t n, uint64_t slimit, const std::v
             BatchPat bp = c ? d->cpat : d->pat;
             bp.qc_off = (uint32_t)T.qc.size();
             bp.tb = tb ? (*tb)[bp.out] : 0;
+            if (pt) (*pt)[bp.out].witem = T.items;   // the entry's first item (set below)
             T.qc.insert(T.qc.end(), qc.begin(), qc.end());
             if (c) mask[(qc[0] & 0xFFu) >> 5] |= 1u << (qc[0] & 31u);
             T.pats.push_back(bp);
@@ -602,20 +614,35 @@ struct Geometry {
     }
 };
 
-Geometry geometry(sm_ctx* ctx, uint32_t maxm, bool need_index) {
+// Shared-memory layout and residency of a launch whose patterns have length
+// <= maxm and whose CTAs count at most nslots patterns each: the stage
+// count is lowered while that lets more CTAs reside on an SM.
+Geometry geometry(sm_ctx* ctx, uint32_t maxm, bool need_index, uint32_t nslots = kMaxSlots) {
     Geometry g;
     g.SB = smk::stage_bytes_for(maxm);
     g.index_cap = need_index ? g.SB : 0u;
     g.stages = sm_ctx_stages(ctx);
-    // two resident CTAs per SM when the shared memory allows it
-    while (g.stages > 2 && 2 * g.smem(kMaxSlots) > sm_ctx_max_smem(ctx)) --g.stages;
+    nslots = std::max(1u, std::min(nslots, kMaxSlots));
+    while (g.stages > 2 && g.smem(nslots) > sm_ctx_max_smem(ctx)) --g.stages;
     const int ms = (int)sm_ctx_max_smem(ctx);
     cudaFuncSetAttribute(smk::batch_kernel<smk::kBatchCount>, cudaFuncAttributeMaxDynamicSharedMemorySize, ms);
     cudaFuncSetAttribute(smk::batch_kernel<smk::kBatchTileCount>, cudaFuncAttributeMaxDynamicSharedMemorySize, ms);
     cudaFuncSetAttribute(smk::batch_kernel<smk::kBatchWrite>, cudaFuncAttributeMaxDynamicSharedMemorySize, ms);
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, smk::batch_kernel<smk::kBatchTileCount>, smk::kThreads,
-                                                  g.smem(kMaxSlots));
+    auto occ_of = [&](const Geometry& x) {
+        int o = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, smk::batch_kernel<smk::kBatchTileCount>, smk::kThreads,
+                                                      x.smem(nslots));
+        return o;
+    };
+    int occ = occ_of(g);
+    while (g.stages > 2) {
+        Geometry f = g;
+        --f.stages;
+        const int o2 = occ_of(f);
+        if (o2 <= occ) break;
+        g = f;
+        occ = o2;
+    }
     g.occ = std::max(occ, 1);
     return g;
 }
@@ -669,7 +696,7 @@ BatchArgs args_for(sm_ctx* ctx, const uint8_t* d_texts, const Tables& T, const L
     return a;
 }
 
-bool text_is_7bit(const uint32_t* h) {
+bool text_is_7bit(const uint64_t* h) {
     for (int c = 0x80; c < 256; ++c)
         if (h[c]) return false;
     return true;
@@ -709,19 +736,57 @@ uint64_t assign_tiles(const std::vector<uint32_t>& m, const std::vector<uint64_t
 // The three passes of a report after the tables and counters are in place:
 // tile counts (and counts), per-pattern prefix sums, ordered writes.
 cudaError_t run_report(const BatchArgs& a1, uint32_t g1, size_t sm1, const BatchArgs& a2, uint32_t g2, size_t sm2,
-                       const PatTiles* d_pt, uint32_t npt, uint32_t* d_tcnt, uint64_t ntb, int64_t* d_counts,
-                       uint32_t ncounts, cudaStream_t st) {
+                       const PatTiles* d_pt, uint32_t npt, uint32_t* d_tcnt, uint64_t ntb, uint64_t nitems,
+                       int64_t* d_counts, uint32_t ncounts, cudaStream_t st) {
     cudaError_t e = cudaSuccess;
     if (ncounts) e = cudaMemsetAsync(d_counts, 0, (size_t)ncounts * sizeof(int64_t), st);
     if (e == cudaSuccess && ntb) e = cudaMemsetAsync(d_tcnt, 0, ntb * sizeof(uint32_t), st);
+    if (e == cudaSuccess && nitems) e = cudaMemsetAsync(const_cast<uint8_t*>(a2.hit), 0, nitems, st);
     if (e == cudaSuccess) e = launch_batch(smk::kBatchTileCount, g1, sm1, st, a1);
     if (e == cudaSuccess && npt) {
         smk::batch_prefix_kernel<<<npt, smk::kPrefixThreads, 0, st>>>(d_pt, d_tcnt, const_cast<uint64_t*>(a2.toff),
-                                                                      a2.pos_off, a2.status);
+                                                                      a2.pos_off, const_cast<uint8_t*>(a2.hit),
+                                                                      a2.status);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = launch_batch(smk::kBatchWrite, g2, sm2, st, a2);
     return e;
+}
+
+// Byte histograms of the ranges d_texts[beg[x] .. end[x]) (x < ntexts; ranges
+// may overlap), one launch over (range, 64 KiB) work items; synchronous on st.
+sm_status text_histograms(sm_ctx* ctx, const uint8_t* d_texts, const int64_t* beg, const int64_t* end,
+                          uint32_t ntexts, cudaStream_t st, std::vector<uint64_t>& hist) {
+    std::vector<uint64_t> chunk_begin(ntexts + 1, 0);
+    for (uint32_t x = 0; x < ntexts; ++x) {
+        const uint64_t n = (uint64_t)(end[x] - beg[x]);
+        chunk_begin[x + 1] = chunk_begin[x] + (n + smk::kHistChunk - 1) / smk::kHistChunk;
+    }
+    hist.assign((size_t)ntexts * 256, 0);
+    void* tmp = nullptr;
+    const size_t hb = hist.size() * 8, ob = (size_t)ntexts * 8, cb = (size_t)(ntexts + 1) * 8;
+    if (cudaMalloc(&tmp, hb + 2 * ob + cb) != cudaSuccess) {
+        cudaGetLastError();
+        return sm_fail_internal(SM_ENOMEM, "histogram workspace");
+    }
+    unsigned long long* d_hist = static_cast<unsigned long long*>(tmp);
+    int64_t* d_beg = reinterpret_cast<int64_t*>(static_cast<char*>(tmp) + hb);
+    int64_t* d_end = reinterpret_cast<int64_t*>(static_cast<char*>(tmp) + hb + ob);
+    uint64_t* d_cb = reinterpret_cast<uint64_t*>(static_cast<char*>(tmp) + hb + 2 * ob);
+    cudaError_t e = cudaMemsetAsync(d_hist, 0, hb, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_beg, beg, ob, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_end, end, ob, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_cb, chunk_begin.data(), cb, cudaMemcpyHostToDevice, st);
+    const uint64_t nchunks = chunk_begin[ntexts];
+    if (e == cudaSuccess && nchunks) {
+        const uint32_t grid = (uint32_t)std::min<uint64_t>(nchunks, (uint64_t)sm_ctx_num_sms(ctx) * 8);
+        smk::batch_hist_kernel<<<grid, 256, 0, st>>>(d_texts, d_beg, d_end, d_cb, ntexts, nchunks, d_hist);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hist.data(), d_hist, hb, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(tmp);
+    return e == cudaSuccess ? SM_OK : sm_fail_internal(SM_ECUDA, cudaGetErrorString(e));
 }
 
 }  // namespace
@@ -743,9 +808,10 @@ struct sm_batch {
     BatchArgs wargs{};
     void* d_wmem = nullptr;
     const PatTiles* d_pt = nullptr;   // in d_wmem, one per caller pattern
-    uint64_t ntb = 0;
+    uint64_t ntb = 0, nitems = 0;     // counters; work items of the write pass
     uint32_t* d_tcnt = nullptr;
     uint64_t* d_toff = nullptr;
+    uint8_t* d_hit = nullptr;
 };
 
 extern "C" sm_status sm_batch_create(sm_ctx* ctx, const uint8_t* d_texts, const int64_t* h_text_off, uint32_t ntexts,
@@ -771,36 +837,9 @@ extern "C" sm_status sm_batch_create(sm_ctx* ctx, const uint8_t* d_texts, const 
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
 
     // 1. per-text histograms on the device
-    std::vector<uint64_t> chunk_begin(ntexts + 1, 0);
-    for (uint32_t x = 0; x < ntexts; ++x) {
-        const uint64_t n = (uint64_t)(h_text_off[x + 1] - h_text_off[x]);
-        chunk_begin[x + 1] = chunk_begin[x] + (n + kHistChunk - 1) / kHistChunk;
-    }
-    std::vector<uint32_t> hist((size_t)ntexts * 256, 0);
-    {
-        void* tmp = nullptr;
-        const size_t hb = hist.size() * 4, ob = (size_t)(ntexts + 1) * 8, cb = (size_t)(ntexts + 1) * 8;
-        if (cudaMalloc(&tmp, hb + ob + cb) != cudaSuccess) {
-            cudaGetLastError();
-            return sm_fail_internal(SM_ENOMEM, "histogram workspace");
-        }
-        uint32_t* d_hist = static_cast<uint32_t*>(tmp);
-        int64_t* d_off = reinterpret_cast<int64_t*>(static_cast<char*>(tmp) + hb);
-        uint64_t* d_cb = reinterpret_cast<uint64_t*>(static_cast<char*>(tmp) + hb + ob);
-        cudaError_t e = cudaMemsetAsync(d_hist, 0, hb, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, h_text_off, ob, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(d_cb, chunk_begin.data(), cb, cudaMemcpyHostToDevice, st);
-        const uint64_t nchunks = chunk_begin[ntexts];
-        if (e == cudaSuccess && nchunks) {
-            const uint32_t grid = (uint32_t)std::min<uint64_t>(nchunks, (uint64_t)sm_ctx_num_sms(ctx) * 8);
-            batch_hist_kernel<<<grid, 256, 0, st>>>(d_texts, d_off, d_cb, ntexts, nchunks, d_hist);
-            e = cudaGetLastError();
-        }
-        if (e == cudaSuccess) e = cudaMemcpyAsync(hist.data(), d_hist, hb, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        cudaFree(tmp);
-        if (e != cudaSuccess) return sm_fail_internal(SM_ECUDA, cudaGetErrorString(e));
-    }
+    std::vector<uint64_t> hist;
+    const sm_status hs = text_histograms(ctx, d_texts, h_text_off, h_text_off + 1, ntexts, st, hist);
+    if (hs != SM_OK) return hs;
 
     // 2. patterns described under their text's frequencies; per-tile
     // counters for reports
@@ -810,7 +849,7 @@ extern "C" sm_status sm_batch_create(sm_ctx* ctx, const uint8_t* d_texts, const 
     for (uint32_t k = 0; k < npats; ++k) {
         const uint32_t x = (uint32_t)h_pat_text[k];
         const uint64_t n = (uint64_t)(h_text_off[x + 1] - h_text_off[x]);
-        const uint32_t* h = &hist[(size_t)x * 256];
+        const uint64_t* h = &hist[(size_t)x * 256];
         const uint32_t delta = (uint32_t)((reinterpret_cast<uintptr_t>(d_texts) + (uint64_t)h_text_off[x]) & 15u);
         ms[k] = (uint32_t)(h_pat_off[k + 1] - h_pat_off[k]);
         lens[k] = n;
@@ -830,11 +869,11 @@ extern "C" sm_status sm_batch_create(sm_ctx* ctx, const uint8_t* d_texts, const 
         for (; kk < npats && (uint32_t)h_pat_text[by_text[kk]] == x; ++kk) ptrs.push_back(&descs[by_text[kk]]);
         const uint64_t n = (uint64_t)(h_text_off[x + 1] - h_text_off[x]);
         add_text(T, (uint64_t)h_text_off[x], n, ~0ull, ptrs, true, &tb);
-        add_text(W, (uint64_t)h_text_off[x], n, ~0ull, ptrs, false, &tb);
+        add_text(W, (uint64_t)h_text_off[x], n, ~0ull, ptrs, false, &tb, &pt);
     }
-    const Geometry g = geometry(ctx, T.maxm, T.need_index);
+    const Geometry g = geometry(ctx, T.maxm, T.need_index, T.slot_hint());
     finish(T, (uint64_t)sm_ctx_num_sms(ctx) * g.occ);
-    const Geometry gw = geometry(ctx, W.maxm, false);
+    const Geometry gw = geometry(ctx, W.maxm, false, W.slot_hint());
     finish(W, (uint64_t)sm_ctx_num_sms(ctx) * gw.occ);
 
     // 3. one allocation for each pass's tables (the write pass's also holds
@@ -848,6 +887,7 @@ extern "C" sm_status sm_batch_create(sm_ctx* ctx, const uint8_t* d_texts, const 
     b->device = sm_ctx_device(ctx);
     b->npats = npats;
     b->ntb = ntb;
+    b->nitems = W.items;
     if (cudaMalloc(&b->d_mem, L.total) != cudaSuccess || cudaMalloc(&b->d_wmem, wtotal) != cudaSuccess) {
         cudaGetLastError();
         sm_batch_destroy(b);
@@ -897,10 +937,14 @@ extern "C" sm_status sm_batch_report(sm_batch* b, int64_t* d_counts, uint64_t* d
     Guard g(b->device);
     if (!b->d_tcnt && b->ntb) {   // the counters, once per batch
         if (cudaMalloc(&b->d_tcnt, b->ntb * sizeof(uint32_t)) != cudaSuccess ||
-            cudaMalloc(&b->d_toff, b->ntb * sizeof(uint64_t)) != cudaSuccess) {
+            cudaMalloc(&b->d_toff, b->ntb * sizeof(uint64_t)) != cudaSuccess ||
+            cudaMalloc(&b->d_hit, std::max<uint64_t>(b->nitems, 1)) != cudaSuccess) {
             cudaGetLastError();
-            if (b->d_tcnt) cudaFree(b->d_tcnt);
+            for (void* q : {(void*)b->d_tcnt, (void*)b->d_toff, (void*)b->d_hit})
+                if (q) cudaFree(q);
             b->d_tcnt = nullptr;
+            b->d_toff = nullptr;
+            b->d_hit = nullptr;
             return sm_fail_internal(SM_ENOMEM, "report tile counters");
         }
     }
@@ -911,8 +955,9 @@ extern "C" sm_status sm_batch_report(sm_batch* b, int64_t* d_counts, uint64_t* d
     a2.toff = b->d_toff;
     a2.d_pos = d_pos;
     a2.pos_off = d_pos_off;
+    a2.hit = b->d_hit;
     const cudaError_t e = run_report(a1, b->grid, b->smem, a2, b->wgrid, b->wsmem, b->d_pt, b->npats, b->d_tcnt,
-                                     b->ntb, d_counts, b->npats, st);
+                                     b->ntb, b->nitems, d_counts, b->npats, st);
     return e == cudaSuccess ? SM_OK : sm_fail_internal(SM_ECUDA, cudaGetErrorString(e));
 }
 
@@ -924,6 +969,7 @@ extern "C" void sm_batch_destroy(sm_batch* b) {
     if (b->d_wmem) cudaFree(b->d_wmem);
     if (b->d_tcnt) cudaFree(b->d_tcnt);
     if (b->d_toff) cudaFree(b->d_toff);
+    if (b->d_hit) cudaFree(b->d_hit);
     delete b;
 }
 
@@ -978,9 +1024,16 @@ struct sm_stepper {
     uint64_t n = 0, chunk = 0;
     uint32_t nchunks = 0, max_m = 0, delta = 0;
     bool text7 = true;
-    uint32_t hist[256] = {};
-    Geometry geo;
-    std::unordered_map<uint32_t, PatDesc> queries;
+    uint64_t hist[256] = {};      // the whole text's (reports, orders of the whole text)
+    // chunks with the same set of symbols form a class; a query is
+    // described once per class under the class's frequencies, and a chunk
+    // without one of its symbols is not scanned for it
+    std::vector<uint32_t> chunk_class;
+    std::vector<std::vector<uint64_t>> class_hist;
+    std::vector<uint64_t> class_n;
+    std::vector<bool> class_text7;
+    Geometry geo[2];   // steps without and with the candidate index (any active set)
+    std::unordered_map<uint32_t, std::vector<PatDesc>> queries;   // one per class
     struct Buf {
         char* d = nullptr;
         char* h = nullptr;
@@ -992,6 +1045,8 @@ struct sm_stepper {
     uint32_t* d_tcnt = nullptr;   // report counters
     uint64_t* d_toff = nullptr;
     uint64_t rcap = 0;
+    uint8_t* d_hit = nullptr;     // report: tiles with matches
+    uint64_t hcap = 0;
 };
 
 namespace {
@@ -1033,9 +1088,45 @@ extern "C" sm_status sm_stepper_create(sm_ctx* ctx, const uint8_t* d_text, uint6
     s->nchunks = (uint32_t)((n + chunk_bytes - 1) / chunk_bytes);
     s->max_m = max_m;
     s->delta = (uint32_t)(reinterpret_cast<uintptr_t>(d_text) & 15u);
-    for (int c = 0; c < 256; ++c) s->hist[c] = (uint32_t)std::min<uint64_t>(h_hist256[c], 0xFFFFFFFFull);
+    for (int c = 0; c < 256; ++c) s->hist[c] = h_hist256[c];
     s->text7 = text_is_7bit(s->hist);
-    s->geo = geometry(ctx, max_m, true);
+    {   // histograms of each chunk with its halo (a query's matches in the
+        // chunk can read max_m - 1 bytes past it) -> classes of chunks with
+        // equal symbol sets
+        std::vector<int64_t> beg(s->nchunks), end(s->nchunks);
+        for (uint32_t c = 0; c < s->nchunks; ++c) {
+            beg[c] = (int64_t)((uint64_t)c * chunk_bytes);
+            end[c] = (int64_t)std::min<uint64_t>((uint64_t)(c + 1) * chunk_bytes + max_m - 1, n);
+        }
+        std::vector<int64_t> off(s->nchunks + 1);
+        for (uint32_t c = 0; c <= s->nchunks; ++c) off[c] = (int64_t)std::min<uint64_t>((uint64_t)c * chunk_bytes, n);
+        std::vector<uint64_t> ch;
+        const sm_status hs =
+            s->nchunks ? text_histograms(ctx, d_text, beg.data(), end.data(), s->nchunks, nullptr, ch) : SM_OK;
+        if (hs != SM_OK) {
+            delete s;
+            return hs;
+        }
+        std::vector<std::vector<uint64_t>> keys;   // symbol-set bitmaps of the classes
+        for (uint32_t c = 0; c < s->nchunks; ++c) {
+            std::vector<uint64_t> key(4, 0);
+            for (int b = 0; b < 256; ++b)
+                if (ch[(size_t)c * 256 + b]) key[b >> 6] |= 1ull << (b & 63);
+            uint32_t k = 0;
+            while (k < keys.size() && keys[k] != key) ++k;
+            if (k == keys.size()) {
+                keys.push_back(key);
+                s->class_hist.emplace_back(256, 0);
+                s->class_n.push_back(0);
+            }
+            for (int b = 0; b < 256; ++b) s->class_hist[k][b] += ch[(size_t)c * 256 + b];
+            s->class_n[k] += (uint64_t)(off[c + 1] - off[c]);
+            s->chunk_class.push_back(k);
+        }
+        for (auto& h : s->class_hist) s->class_text7.push_back(text_is_7bit(h.data()));
+    }
+    s->geo[0] = geometry(ctx, max_m, false);
+    s->geo[1] = geometry(ctx, max_m, true);
     for (auto* b : {&s->buf[0], &s->buf[1], &s->rbuf})
         if (cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
@@ -1051,8 +1142,11 @@ extern "C" uint32_t sm_stepper_chunks(const sm_stepper* s) { return s ? s->nchun
 extern "C" sm_status sm_stepper_admit(sm_stepper* s, uint32_t qid, const uint8_t* h_pat, uint32_t m) {
     if (!s || !h_pat) return sm_fail_internal(SM_EINVAL, "NULL argument");
     if (m < 1 || m > s->max_m) return sm_fail_internal(SM_EINVAL, "pattern length out of range for this stepper");
-    // orders from the whole resident text's frequencies (counts never depend on them)
-    s->queries[qid] = describe(h_pat, m, s->hist, s->n, s->delta, s->text7, qid);
+    // orders under each chunk class's frequencies (counts never depend on them)
+    std::vector<PatDesc>& d = s->queries[qid];
+    d.clear();
+    for (size_t k = 0; k < s->class_hist.size(); ++k)
+        d.push_back(describe(h_pat, m, s->class_hist[k].data(), s->class_n[k], s->delta, s->class_text7[k], qid));
     return SM_OK;
 }
 
@@ -1077,13 +1171,15 @@ extern "C" sm_status sm_stepper_step(sm_stepper* s, const uint32_t* h_qids, uint
     for (uint32_t i = 0; i < nq; ++i) {
         auto it = s->queries.find(h_qids[i]);
         if (it == s->queries.end()) return sm_fail_internal(SM_EINVAL, "query not admitted");
-        if (it->second.zero || it->second.pat.m > nbytes) continue;   // no start in this chunk
-        ds.push_back(&it->second);
+        const PatDesc& d = it->second[s->chunk_class[chunk]];
+        if (d.zero || d.pat.m > nbytes) continue;   // a symbol absent from the chunk, or no start in it
+        ds.push_back(&d);
     }
     if (ds.empty()) return SM_OK;
     Tables T;
     add_text(T, off, nbytes, slimit, ds);
-    finish(T, (uint64_t)sm_ctx_num_sms(s->ctx) * s->geo.occ);
+    const Geometry& geo = s->geo[T.need_index ? 1 : 0];
+    finish(T, (uint64_t)sm_ctx_num_sms(s->ctx) * geo.occ);
     const Layout L = layout_of(T);
     sm_stepper::Buf& b = s->buf[s->cur];
     s->cur ^= 1;
@@ -1092,9 +1188,9 @@ extern "C" sm_status sm_stepper_step(sm_stepper* s, const uint32_t* h_qids, uint
     pack(T, L, b.h);
     cudaError_t e = cudaMemcpyAsync(b.d, b.h, L.total, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) {
-        BatchArgs a = args_for(s->ctx, s->d_text, T, L, b.d, s->geo);
+        BatchArgs a = args_for(s->ctx, s->d_text, T, L, b.d, geo);
         a.d_counts = d_counts;
-        e = launch_batch(smk::kBatchCount, (uint32_t)T.cta_pbase.size(), s->geo.smem(T.nslots), st, a);
+        e = launch_batch(smk::kBatchCount, (uint32_t)T.cta_pbase.size(), geo.smem(T.nslots), st, a);
     }
     if (e == cudaSuccess) e = cudaEventRecord(b.ev, st);
     b.used = true;
@@ -1130,10 +1226,10 @@ extern "C" sm_status sm_stepper_report(sm_stepper* s, const uint8_t* h_pats, con
     const uint64_t ntb = assign_tiles(ms, lens, pt, tb);
     Tables T, W;
     add_text(T, 0, s->n, ~0ull, ptrs, true, &tb);
-    add_text(W, 0, s->n, ~0ull, ptrs, false, &tb);
-    const Geometry g1 = geometry(s->ctx, std::max(T.maxm, 1u), T.need_index);
+    add_text(W, 0, s->n, ~0ull, ptrs, false, &tb, &pt);
+    const Geometry g1 = geometry(s->ctx, std::max(T.maxm, 1u), T.need_index, T.slot_hint());
     finish(T, (uint64_t)sm_ctx_num_sms(s->ctx) * g1.occ);
-    const Geometry g2 = geometry(s->ctx, std::max(W.maxm, 1u), false);
+    const Geometry g2 = geometry(s->ctx, std::max(W.maxm, 1u), false, W.slot_hint());
     finish(W, (uint64_t)sm_ctx_num_sms(s->ctx) * g2.occ);
     const Layout L = layout_of(T), LW = layout_of(W);
     const size_t o_w = L.total, o_pt = o_w + LW.total, o_po = o_pt + ((pt.size() * sizeof(PatTiles) + 255) & ~(size_t)255);
@@ -1153,6 +1249,17 @@ extern "C" sm_status sm_stepper_report(sm_stepper* s, const uint8_t* h_pats, con
         }
         s->rcap = cap;
     }
+    if (s->hcap < std::max<uint64_t>(W.items, 1)) {
+        const uint64_t cap = std::max<uint64_t>(std::max<uint64_t>(W.items, 1), 2 * s->hcap);
+        if (s->d_hit) cudaFree(s->d_hit);
+        s->d_hit = nullptr;
+        s->hcap = 0;
+        if (cudaMalloc(&s->d_hit, cap) != cudaSuccess) {
+            cudaGetLastError();
+            return sm_fail_internal(SM_ENOMEM, "report tile flags");
+        }
+        s->hcap = cap;
+    }
     char* h = s->rbuf.h;
     char* d = s->rbuf.d;
     pack(T, L, h);
@@ -1168,9 +1275,10 @@ extern "C" sm_status sm_stepper_report(sm_stepper* s, const uint8_t* h_pats, con
         a2.toff = s->d_toff;
         a2.d_pos = d_pos ? d_pos + h_pos_off[0] : nullptr;
         a2.pos_off = reinterpret_cast<const int64_t*>(d + o_po);
+        a2.hit = s->d_hit;
         e = run_report(a1, (uint32_t)T.cta_pbase.size(), g1.smem(T.nslots), a2, (uint32_t)W.cta_pbase.size(),
-                       g2.smem(W.nslots), reinterpret_cast<const PatTiles*>(d + o_pt), nq, s->d_tcnt, ntb, d_counts,
-                       nq, st);
+                       g2.smem(W.nslots), reinterpret_cast<const PatTiles*>(d + o_pt), nq, s->d_tcnt, ntb, W.items,
+                       d_counts, nq, st);
     }
     if (e == cudaSuccess) e = cudaEventRecord(s->rbuf.ev, st);
     s->rbuf.used = true;
@@ -1188,5 +1296,6 @@ extern "C" void sm_stepper_destroy(sm_stepper* s) {
     }
     if (s->d_tcnt) cudaFree(s->d_tcnt);
     if (s->d_toff) cudaFree(s->d_toff);
+    if (s->d_hit) cudaFree(s->d_hit);
     delete s;
 }

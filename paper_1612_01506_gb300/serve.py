@@ -5,10 +5,11 @@ the next chunk for all active queries in one batched launch
 (``sm_stepper_step``), so queries in flight share each pass over the text.
 A query is admitted whenever a counter slot is free -- it joins at whatever
 chunk comes next -- and its count is complete after one step on every chunk.
-A report query then needs a position buffer of exactly count x 8 bytes; the
-report queries waiting when no report batch is in flight are admitted up to
-the report memory budget and reported together (``sm_stepper_report``: one
-batched report over the text) on a second stream while the next steps run.
+A report query then needs a position buffer of exactly count x 8 bytes and is
+admitted when the report memory budget has room. Its positions are written on
+a second stream while the next steps run: by ``sm_report`` alone, or, when at
+least ``report_batch_min`` report queries wait, together with them in one
+batched report over the text (``sm_stepper_report``).
 
 Every query's result is the same as when it runs alone (the tests check
 this against single calls and the CPU oracle).
@@ -70,13 +71,14 @@ class Server:
     """Continuous-batching server over the resident uint8 CUDA tensor `text`."""
 
     def __init__(self, text, chunk_bytes: int = 256 << 20, max_m: int = 2048, max_active: int = 1024,
-                 report_budget: int = 8 << 30, burst_below: int = 4):
+                 report_budget: int = 8 << 30, burst_below: int = 4, report_batch_min: int = 32):
         import torch
         self.torch = torch
         self.text = text
         self.dev = text.device
         self.lib = _bind_stepper()
-        self.ctx = sm.sm_create(self.dev.index or 0)           # steps on self.stream, reports on self.rstream
+        self.ctx = sm.sm_create(self.dev.index or 0)           # steps, on self.stream (and batched reports)
+        self.rctx = sm.sm_create(self.dev.index or 0)          # single reports, on self.rstream
         self.stream = torch.cuda.Stream(device=self.dev)
         self.rstream = torch.cuda.Stream(device=self.dev)
         self.hist = sm.sm_histogram(self.ctx, text, stream=self.stream)
@@ -103,6 +105,10 @@ class Server:
         self.report_wait: collections.deque[Query] = collections.deque()
         self.reporting: list = []                 # (event, query, bytes)
         self.report_budget = report_budget
+        # with at least this many report queries waiting they are reported in
+        # one batched pass; fewer run one report each (a batched pass holds
+        # every SM for its whole length, which delays the count steps)
+        self.report_batch_min = report_batch_min
         self.report_reserved = 0
         self.next_chunk = 0
         self.done: list[Query] = []
@@ -201,9 +207,9 @@ class Server:
                     q.done = now
                     self.done.append(q)
         self.finishing = keep
-        # a finished report batch: its queries are done
+        # finished reports (single or batched): their queries are done
         keep = []
-        for ev, qs, need in self.reporting:
+        for ev, qs, need, bt in self.reporting:
             if ev.query():
                 now = self.now()
                 for q in qs:
@@ -211,18 +217,37 @@ class Server:
                     self.done.append(q)
                 self.report_reserved -= need
             else:
-                keep.append((ev, qs, need))
+                keep.append((ev, qs, need, bt))
         self.reporting = keep
-        # the next report batch (one in flight): the waiting report queries
-        # whose position buffers (count x 8 bytes) fit the memory budget,
-        # reported together in one batched pass over the text
-        if self.reporting or not self.report_wait:
-            return
+        if len(self.report_wait) >= self.report_batch_min and not any(bt for _, _, _, bt in self.reporting):
+            self._report_batch()
+        # single reports: admitted by the memory their position buffers need
+        while self.report_wait and len(self.report_wait) < self.report_batch_min:
+            q = self.report_wait[0]
+            need = max(q.count, 1) * 8
+            if self.report_reserved and self.report_reserved + need > self.report_budget:
+                break
+            self.report_wait.popleft()
+            self.report_reserved += need
+            with torch.cuda.stream(self.rstream):
+                pos = torch.empty(max(q.count, 1), dtype=torch.int64, device=self.dev)
+                cnt = torch.empty(1, dtype=torch.int64, device=self.dev)
+            sm.sm_report(self.rctx, self.text, q.pattern, q.count, pi=sm.sm_order(q.pattern, self.hist),
+                         out_pos=pos, out_count=cnt, stream=self.rstream, hist=self.hist)
+            ev = torch.cuda.Event()
+            ev.record(self.rstream)
+            q.positions = pos[: q.count]
+            self.reporting.append((ev, [q], need, False))
+
+    def _report_batch(self):
+        """The waiting report queries whose position buffers (count x 8 bytes)
+        fit the memory budget, reported together in one batched pass."""
+        torch = self.torch
         batch, need = [], 0
         while self.report_wait:
             q = self.report_wait[0]
             b = max(q.count, 1) * 8
-            if batch and need + b > self.report_budget:
+            if batch and self.report_reserved + need + b > self.report_budget:
                 break
             self.report_wait.popleft()
             batch.append(q)
@@ -244,7 +269,7 @@ class Server:
         for k, q in enumerate(batch):
             q.positions = pos[pos_off[k]:pos_off[k + 1]]
         self.report_reserved += need
-        self.reporting.append((ev, batch, need))
+        self.reporting.append((ev, batch, need, True))
 
     # ------------------------------------------------------------ drivers
     def run(self, queries: list[Query], time_scale: float = 1.0, max_steps: int | None = None) -> list[Query]:

@@ -37,11 +37,14 @@ def make_queries(t, k, seed, report_frac=0.2, mmax=2048):
     return qs
 
 
-def test_serving_results_equal_alone(torch):
+# report_batch_min 2: waiting report queries go through batched reports
+@pytest.mark.parametrize("report_batch_min", [32, 2])
+def test_serving_results_equal_alone(torch, report_batch_min):
     from paper_1612_01506_gb300.serve import Server
     t = make_text(3 << 20)
     text = torch.from_numpy(t).cuda()
-    server = Server(text, chunk_bytes=1 << 20, max_m=2048, max_active=16, report_budget=1 << 20, burst_below=4)
+    server = Server(text, chunk_bytes=1 << 20, max_m=2048, max_active=16, report_budget=1 << 20, burst_below=4,
+                    report_batch_min=report_batch_min)
     assert server.nchunks == 6
     qs = make_queries(t, 60, seed=1)
     done = server.run(qs)
@@ -115,3 +118,27 @@ def test_stepper_report_batch(torch):
         for k, p in enumerate(pats):
             w, _ = oracle.report_threads(p, t, want[k])
             assert np.array_equal(allpos[pos_off[k]:pos_off[k + 1]], w[: caps[k]]), (k, len(p))
+
+
+def test_stepper_patterns_across_chunk_classes(torch):
+    # chunks of the ACGT half and of the Markov half have different symbol
+    # sets; a pattern that starts in the last ACGT chunk and ends in the
+    # Markov half holds symbols absent from that chunk, and must still count
+    from paper_1612_01506_gb300.serve import Query, Server
+    half = 1 << 20
+    t = make_text(half)
+    text = torch.from_numpy(t).cuda()
+    server = Server(text, chunk_bytes=1 << 18, max_m=512, max_active=64, burst_below=0)
+    qs = []
+    for m in (2, 3, 8, 40, 300, 512):
+        for back in (1, m // 2, m - 1):
+            if 0 < back < m:
+                s0 = half - back
+                qs.append(Query(pattern=t[s0:s0 + m].tobytes(), kind="count", arrival=0.0))
+    qs.append(Query(pattern=t[half - 5:half + 3].tobytes(), kind="report", arrival=0.0))
+    server.run(qs)
+    for q in qs:
+        assert q.count == oracle.count_threads(q.pattern, t) >= 1, (len(q.pattern), q.pattern[:12])
+    q = qs[-1]
+    pos, _ = oracle.report_threads(q.pattern, t, q.count)
+    assert np.array_equal(q.positions.cpu().numpy().view(np.uint64), pos)

@@ -66,6 +66,10 @@ def parse():
     ap.add_argument("--serve", action="store_true",
                     help="also measure the serving loop (4 GiB resident text, Poisson arrivals)")
     ap.add_argument("--serve-only", action="store_true", help="measure only the serving loop")
+    ap.add_argument("--multi", action="store_true",
+                    help="also measure counts and positions over 20,000 packed texts (~35 GB)")
+    ap.add_argument("--multi-only", action="store_true", help="measure only the packed-texts batch")
+    ap.add_argument("--multi-texts", type=int, default=20000)
     ap.add_argument("--serve-rates", default="200,1000,4000")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     return ap.parse_args()
@@ -437,6 +441,111 @@ def run_batch(args, local, steps=3, warmup=2):
             "counts_agree": agree}
 
 
+def run_multi(args, local, steps=2, warmup=1):
+    """Many packed texts: --multi-texts texts (20,000) with lengths log-uniform
+    in [1 KiB, 16 MiB] (about 35 GB together), each over an alphabet drawn
+    from {4, 20, Markov-95, 256}, each with 1-8 patterns of length
+    log-uniform in [2, 512] (80% copied from the text, 20% random over its
+    alphabet). One step = sm_batch_count (counts) and sm_batch_report
+    (counts and every ascending position list, into exact-size slices).
+    patterns*GB/s = sum over patterns of its text's bytes / time."""
+    import concurrent.futures as cf
+    import torch
+    from paper_1612_01506_gb300 import sm, synth
+    nt = args.multi_texts
+    r = np.random.default_rng(4)
+    lens = np.exp(r.uniform(np.log(1024), np.log(16 << 20), nt)).astype(np.int64)
+    kinds = [(4, 20, "markov95", 256)[i] for i in r.integers(0, 4, nt)]
+    npt = r.integers(1, 9, nt)
+    off = np.zeros(nt + 1, np.int64)
+    off[1:] = np.cumsum(lens)
+    total = int(off[-1])
+    dev = torch.device("cuda", local)
+    d = torch.empty(total, dtype=torch.uint8, device=dev)
+    # texts generated on the host cores in parallel, staged through 1 GiB
+    stage = torch.empty(1 << 30, dtype=torch.uint8).pin_memory()
+    sv = stage.numpy()
+    pats, pat_text = [], []
+
+    def gen(x):
+        return synth.text(kinds[x], int(lens[x]), seed=0, stream=synth.stream_id("multi", x), threads=1)
+
+    x0, used = 0, 0
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        for x, tx in enumerate(ex.map(gen, range(nt))):
+            if used + tx.size > sv.size:
+                d[off[x0]:off[x0] + used].copy_(stage[:used])
+                x0, used = x, 0
+            sv[used:used + tx.size] = tx
+            used += tx.size
+            for _ in range(int(npt[x])):
+                m = min(int(np.exp(r.uniform(np.log(2), np.log(512)))), tx.size)
+                if r.random() < 0.8:
+                    o = int(r.integers(0, tx.size - m + 1))
+                    pats.append(tx[o:o + m].tobytes())
+                else:
+                    a = np.frombuffer(synth.alphabet_of(kinds[x]), np.uint8)
+                    pats.append(a[r.integers(0, a.size, m)].tobytes())
+                pat_text.append(x)
+    d[off[x0]:off[x0] + used].copy_(stage[:used])
+    del stage, sv
+    npat = len(pats)
+    ctx = sm.sm_create(local)
+    t0 = time.perf_counter()
+    b = sm.sm_batch_create(ctx, d, off, pats, np.array(pat_text, np.int32))
+    t_plan = time.perf_counter() - t0
+    counts = sm.sm_batch_count(b)
+    torch.cuda.synchronize()
+    ch = counts.cpu().numpy()[:npat]
+    pos_off = np.zeros(npat + 1, np.int64)
+    pos_off[1:] = np.cumsum(ch)
+    d_off = torch.from_numpy(pos_off).to(dev)
+    d_pos = torch.empty(max(int(pos_off[-1]), 1), dtype=torch.int64, device=dev)
+    rcounts = torch.empty(npat, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        sm.sm_batch_count(b, out=counts)
+        sm.sm_batch_report(b, d_off, d_pos=d_pos, out=rcounts)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    tc, tr = 0.0, 0.0
+    for _ in range(steps):
+        ev[0].record(stream)
+        sm.sm_batch_count(b, out=counts)
+        ev[1].record(stream)
+        sm.sm_batch_report(b, d_off, d_pos=d_pos, out=rcounts)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        tc += ev[0].elapsed_time(ev[1]) / 1e3
+        tr += ev[1].elapsed_time(ev[2]) / 1e3
+    tc, tr = tc / steps, tr / steps
+    status = sm.sm_sync(ctx)
+    # cross-check against single-pattern calls on a sample of patterns
+    rs = np.random.default_rng(5)
+    sample = rs.choice(npat, size=min(npat, 200), replace=False)
+    agree = bool(np.array_equal(rcounts.cpu().numpy()[:npat], ch))
+    allpos = None
+    for k in sample:
+        x = pat_text[k]
+        tx = d[off[x]:off[x + 1]]
+        c = int(ch[k])
+        pos, cnt = sm.sm_report(ctx, tx, pats[k], max(c, 1))
+        if int(cnt.item()) != c:
+            agree = False
+            break
+        got = d_pos[pos_off[k]:pos_off[k + 1]]
+        if not torch.equal(got, pos[:c]):
+            agree = False
+            break
+    pgb = float(sum(int(lens[x]) for x in pat_text)) / 1e9
+    return {"workload": f"{nt} packed texts ({total / 1e9:.1f} GB), lengths log-uniform [1 KiB, 16 MiB], "
+                        f"sigma in {{4,20,markov95,256}}, {npat} patterns (1-8 per text, m log-uniform [2,512])",
+            "texts_bytes": total, "patterns": npat, "positions": int(pos_off[-1]),
+            "plan_s": round(t_plan, 3), "count_ms": round(tc * 1e3, 3), "report_ms": round(tr * 1e3, 3),
+            "count_patterns_gbs": round(pgb / tc, 1), "report_patterns_gbs": round(pgb / tr, 1),
+            "status": status, "sample_agrees_with_single_calls": agree, "sample": int(sample.size)}
+
+
 # ---------------------------------------------------------------- serving
 
 def run_serve(args, local):
@@ -560,6 +669,10 @@ def main():
         if rank == 0:
             print(json.dumps({"serving": run_serve(args, local)}), flush=True)
         return
+    if args.multi_only:
+        if rank == 0:
+            print(json.dumps({"multi": run_multi(args, local)}), flush=True)
+        return
     res = run_gpu(args, world, rank, local)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -575,6 +688,8 @@ def main():
             line["batch"] = run_batch(args, local)
         if args.serve and world == 1:
             line["serving"] = run_serve(args, local)
+        if args.multi and world == 1:
+            line["multi"] = run_multi(args, local)
         print(json.dumps(line), flush=True)
         if args.json_detail:
             with open(args.json_detail, "w") as f:

@@ -122,9 +122,9 @@ struct Plan {
 
 // Compare descriptors (e << 8) | p[q], e = (text address mod 16) + q, in the
 // order pi; the text's symbol frequencies (when the caller passes its
-// histogram) pick the peeled compares and the compare kind: 2-bit codes for
-// texts of at most four symbols, the 7-bit test for texts without bytes
-// >= 0x80, else the general byte test.
+// histogram) pick the peeled compares and the compare kind: 1-bit codes for
+// texts of at most two symbols, 2-bit codes for at most four, the 7-bit test
+// for texts without bytes >= 0x80, else the general byte test.
 sm_status make_plan(const uint8_t* d_text, const uint8_t* p, uint32_t m, const uint32_t* pi,
                     const sm_search_opts* o, uint64_t n, Plan* pl) {
     if (o && (o->flags & ~SM_SEARCH_BYTES)) return fail(SM_EINVAL, "unknown search flags");
@@ -136,7 +136,7 @@ sm_status make_plan(const uint8_t* d_text, const uint8_t* p, uint32_t m, const u
     }
     const uint64_t* h = o ? o->h_hist256 : nullptr;
     std::vector<double> freq;
-    bool packed = false;
+    bool packed = false, binary = false;
     if (h) {
         uint64_t high = 0;
         for (int c = 0x80; c < 256; ++c) high += h[c];
@@ -148,20 +148,22 @@ sm_status make_plan(const uint8_t* d_text, const uint8_t* p, uint32_t m, const u
         pl->kind = (high == 0) && pat7 ? smk::kKindSeven : smk::kKindBytes;
         freq.resize(m);
         for (uint32_t j = 0; j < m; ++j) freq[j] = n ? (double)h[v[j] & 0xFFu] / (double)n : 1.0;
-        packed = !pl->zero && !(o->flags & SM_SEARCH_BYTES) && smk::packed_code_bits(h, &pl->b1, &pl->b2);
+        const bool codes = !pl->zero && !(o->flags & SM_SEARCH_BYTES);
+        binary = codes && smk::binary_code_bit(h, &pl->b1);
+        packed = codes && !binary && smk::packed_code_bits(h, &pl->b1, &pl->b2);
     }
     pl->qc.resize(m);
     uint32_t ng = 0;
-    if (packed) {
+    if (binary || packed) {
         // every pattern symbol occurs in the text, so its code is defined
         for (uint32_t j = 0; j < m; ++j) {
             const uint32_t c = v[j] & 0xFFu;
-            v[j] = (v[j] & ~0xFFu) | ((c >> pl->b1) & 1u) | (((c >> pl->b2) & 1u) << 1);
+            v[j] = (v[j] & ~0xFFu) | ((c >> pl->b1) & 1u) | (binary ? 0u : ((c >> pl->b2) & 1u) << 1);
         }
-        pl->kind = pl->b2 == pl->b1 + 1 ? smk::kKindPackedAdj : smk::kKindPacked;
+        pl->kind = binary ? smk::kKindBinary : pl->b2 == pl->b1 + 1 ? smk::kKindPackedAdj : smk::kKindPacked;
         pl->groups.resize(smk::max_packed_groups_for(m));
         pl->r = smk::plan_packed(v.data(), m, freq.data(), o->peel, pl->qc.data(), pl->groups.data(),
-                                 (uint32_t)pl->groups.size(), &ng);
+                                 (uint32_t)pl->groups.size(), &ng, binary ? 1u : 2u);
     } else {
         pl->groups.resize(smk::max_groups_for(m));
         pl->r = smk::plan_dense(v.data(), m, h ? freq.data() : nullptr, o ? o->peel : 0u, pl->qc.data(),
@@ -228,7 +230,7 @@ smk::ScanArgs scan_args(sm_ctx* c, const uint8_t* d_text, uint64_t n, uint32_t m
     a.b1 = pl.b1;
     a.b2 = pl.b2;
     a.gather = 0x01041040u;
-    a.packed_words = smk::packed_words_for(g.stage_bytes);
+    a.packed_words = smk::packed_words_for(g.stage_bytes, pl.kind);
     a.stage_bytes = g.stage_bytes;
     a.stages = g.stages;
     a.status = c->d_status;

@@ -724,5 +724,168 @@ __device__ __forceinline__ uint2 packed_tiles(const uint32_t* const (&pk)[2], bo
     return make_uint2(n[0], n[1]);
 }
 
+// ------------------------------------------------------------ binary texts
+
+// Texts of at most two distinct symbols are compared on 1-bit codes: a
+// symbol's code is its bit b1, where the two symbols differ. 32 codes fill a
+// word, code k of word u being the symbol at byte 32u + k of the stage buffer,
+// in bit k.
+//
+// Bit b1 of the four bytes of w, in bits 24 + j (byte j): the multiplier
+// 0x01020408 moves byte j's bit (at 8j) to 24 + j; the other partial
+// products land on distinct bits below 24 or beyond 31, so nothing carries
+// into bits 24-31.
+__device__ __forceinline__ uint32_t nib4(uint32_t w, uint32_t b1) { return ((w >> b1) & 0x01010101u) * 0x01020408u; }
+
+// 32 bytes (x0: bytes 0-15, x1: bytes 16-31) -> one word of 1-bit codes.
+// Byte permutes collect the nibbles of the even and the odd 4-byte groups;
+// nibble k lands at bits 4k .. 4k + 3.
+__device__ __forceinline__ uint32_t pack32(const uint4& x0, const uint4& x1, uint32_t b1) {
+    const uint32_t n0 = nib4(x0.x, b1), n1 = nib4(x0.y, b1), n2 = nib4(x0.z, b1), n3 = nib4(x0.w, b1);
+    const uint32_t n4 = nib4(x1.x, b1), n5 = nib4(x1.y, b1), n6 = nib4(x1.z, b1), n7 = nib4(x1.w, b1);
+    const uint32_t lo = __byte_perm(__byte_perm(n0, n2, 0x7373u), __byte_perm(n4, n6, 0x7373u), 0x5410u);
+    const uint32_t hi = __byte_perm(__byte_perm(n1, n3, 0x7373u), __byte_perm(n5, n7, 0x7373u), 0x5410u);
+    return lo | (hi << 4);
+}
+
+// One compare on 1-bit codes for the lane's 64 starts (two words) in each of
+// two tiles: y[t][i] |= window ^ (c..c), X[t] the lane's words 2E' .. 2E' + 3
+// past its first in tile t. v = (e << 8) | code; the caller guarantees
+// E' == e >> 6 and D == (e >> 5) & 1. ALIGNED: e mod 32 == 0 (no shift).
+template <int D, bool ALIGNED>
+__device__ __forceinline__ void acc_bin(const uint32_t (&X)[2][4], uint32_t v, uint32_t (&y)[2][2]) {
+    const uint32_t P = 0u - (v & 1u);
+    const uint32_t sh = (v >> 8) & 31u;
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+            y[t][i] |= (ALIGNED ? X[t][D + i] : __funnelshift_r(X[t][D + i], X[t][D + i + 1], sh)) ^ P;
+}
+
+__device__ __forceinline__ uint32_t valid_bits(int64_t lim) {
+    if (lim >= 32) return ~0u;
+    if (lim <= 0) return 0u;
+    return (1u << lim) - 1u;
+}
+
+// packed_tiles for 1-bit codes: one consumer warp's 2048 starts in each of
+// two staged tiles, on the words pk[t] of tile t (lane l's 64 starts are
+// words 64 warp + 2l and the next). Same phases, results and outputs as
+// packed_tiles; a found bit is a start, so the bitmap of a warp-tile is the
+// found words themselves.
+template <bool WRITE, bool DIRECT, class QC>
+__device__ __forceinline__ uint2 binary_tiles(const uint32_t* const (&pk)[2], bool two, uint32_t warp,
+                                              uint32_t lane, QC qc, uint32_t m, uint32_t r, uint32_t ng,
+                                              uint64_t nstarts, const uint64_t (&s0)[2], const uint64_t (&out)[2],
+                                              uint64_t* __restrict__ d_pos, uint64_t cap,
+                                              uint32_t* const (&bm)[2]) {
+    const uint32_t w0 = warp * 64u + lane * 2u;   // lane's first word
+    uint32_t y[2][2] = {{0u, 0u}, {0u, 0u}};
+    for (uint32_t g = 0, j = 0; g < ng; ++g) {
+        const uint32_t gd = qc.group(g);
+        const uint32_t u = w0 + 2u * (gd & 0x1FFu);
+        uint32_t X[2][4];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const uint2 a = *reinterpret_cast<const uint2*>(pk[t] + u);
+            const uint2 b = *reinterpret_cast<const uint2*>(pk[t] + u + 2);
+            X[t][0] = a.x;
+            X[t][1] = a.y;
+            X[t][2] = b.x;
+            X[t][3] = b.y;
+        }
+        if (gd & (1u << 9)) acc_bin<0, true>(X, qc(j++), y);
+        if (gd & (1u << 10)) acc_bin<1, true>(X, qc(j++), y);
+        for (uint32_t k = (gd >> 13) & 31u; k; --k) acc_bin<0, false>(X, qc(j++), y);
+        for (uint32_t k = (gd >> 18) & 31u; k; --k) acc_bin<1, false>(X, qc(j++), y);
+    }
+    uint32_t f[2][2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) f[t][i] = (t == 0 || two) ? ~y[t][i] : 0u;
+        if (s0[t] + kTile > nstarts) {   // last tile: clear starts beyond n - m
+            const int64_t lim = (int64_t)(nstarts - s0[t]) - (int64_t)(warp * kWarpStarts + lane * 64u);
+#pragma unroll
+            for (int i = 0; i < 2; ++i) f[t][i] &= valid_bits(lim - 32 * i);
+        }
+    }
+    uint32_t any = 0;
+#pragma unroll
+    for (int t = 0; t < 2; ++t) any |= f[t][0] | f[t][1];
+    if (!(DIRECT && r >= m) && __any_sync(kFull, any != 0u)) {
+        const uint32_t jl = min(m, r + kLaneCompares);
+        for (uint32_t j = r; j < jl && any; ++j) {
+            const uint32_t v = qc(j);
+            const uint32_t e = v >> 8;
+            const uint32_t P = 0u - (v & 1u);
+            const uint32_t sh = e & 31u;
+            any = 0;
+#pragma unroll
+            for (int t = 0; t < 2; ++t)
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    if (f[t][i]) {
+                        const uint32_t W = w0 + i + (e >> 5);
+                        f[t][i] &= ~(__funnelshift_r(pk[t][W], pk[t][W + 1], sh) ^ P);
+                    }
+                    any |= f[t][i];
+                }
+        }
+        // words still alive: the whole warp takes the remaining compares of
+        // one word at a time (lane l every 32nd from jl + l) and ANDs
+#pragma unroll
+        for (int t = 0; t < 2; ++t)
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                uint32_t pend = __ballot_sync(kFull, jl < m && f[t][i] != 0u);
+                while (pend) {
+                    const uint32_t src = (uint32_t)__ffs(pend) - 1u;
+                    pend &= pend - 1u;
+                    const uint32_t ws = __shfl_sync(kFull, w0, src) + i;
+                    uint32_t yy = 0;
+                    for (uint32_t j = jl + lane; j < m; j += 32) {
+                        const uint32_t v = qc(j);
+                        const uint32_t e = v >> 8;
+                        const uint32_t W = ws + (e >> 5);
+                        yy |= __funnelshift_r(pk[t][W], pk[t][W + 1], e & 31u) ^ (0u - (v & 1u));
+                    }
+                    uint32_t keep = ~yy;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) keep &= __shfl_xor_sync(kFull, keep, o);
+                    if (lane == src) f[t][i] &= keep;
+                }
+            }
+    }
+    uint32_t n[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) n[t] = __popc(f[t][0]) + __popc(f[t][1]);
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+        if (bm[t] && warp_sum_u32(n[t]))   // lane l's 64 starts are words 2l, 2l + 1 of the bitmap
+            reinterpret_cast<uint2*>(bm[t])[lane] = make_uint2(f[t][0], f[t][1]);
+    if (WRITE) {
+        // positions in order: lanes, then words, then starts
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const uint32_t inc = warp_incl_scan(n[t], lane);
+            uint64_t rk = out[t] + inc - n[t];
+            const uint64_t pos0 = s0[t] + warp * kWarpStarts + 64u * lane;
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                uint32_t fw = f[t][i];
+                while (fw) {
+                    const uint32_t k = (uint32_t)(__ffs(fw) - 1);
+                    if (rk < cap) d_pos[rk] = pos0 + 32u * i + k;
+                    ++rk;
+                    fw &= fw - 1;
+                }
+            }
+        }
+    }
+    return make_uint2(n[0], n[1]);
+}
+
 }  // namespace dev
 }  // namespace smk

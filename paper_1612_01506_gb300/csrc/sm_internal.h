@@ -24,7 +24,14 @@ constexpr uint32_t kStatusTimeout = 2u;
 // Compare variants of the scan kernel: bytes (exact zero-byte test), 7-bit
 // bytes (a cheaper test), and 2-bit codes of texts with at most four
 // distinct symbols (code bits b1, b2 adjacent or not).
-enum ScanKind : int { kKindBytes = 0, kKindSeven = 1, kKindPackedAdj = 2, kKindPacked = 3, kKinds = 4 };
+enum ScanKind : int {
+    kKindBytes = 0,      // byte compares, any text
+    kKindSeven = 1,      // byte compares, text and pattern below 0x80
+    kKindPackedAdj = 2,  // 2-bit codes (<= 4 symbols) from adjacent symbol bits
+    kKindPacked = 3,     // 2-bit codes from any two symbol bits
+    kKindBinary = 4,     // 1-bit codes (<= 2 symbols)
+    kKinds = 5
+};
 inline bool kind_packed(int kind) { return kind >= kKindPackedAdj; }
 
 enum ScanMode : int {
@@ -47,7 +54,7 @@ struct ScanArgs {
     uint32_t stages;         // pipeline depth, 2..kMaxStages
     uint32_t one;            // the value 1 (keeps an add on the multiply-add pipe)
     uint32_t ng;             // window groups of the peeled compares
-    uint32_t b1, b2;         // packed kinds: the symbol bits that form the 2-bit codes
+    uint32_t b1, b2;         // packed kinds: the symbol bits that form the codes (binary: b1)
     uint32_t gather;         // packed kinds: 0x01041040 (see pack16)
     uint32_t packed_words;   // packed kinds: words of one packed tile buffer
     uint32_t test_skip_copy; // test hook: 1 = never issue the first tile's copy
@@ -87,9 +94,12 @@ constexpr uint32_t kQueueCap = kWarpStarts / 16;                           // en
 constexpr uint32_t kQueueBytes = kConsumerWarps * kQueueCap * 4;           // 4 KiB
 
 // Packed kinds: one tile of 2-bit codes takes a word per 16-byte unit of
-// the stage buffer, plus 8 words of load slack; four such buffers (two
-// rounds of two tiles) replace the survivor queues.
-inline uint32_t packed_words_for(uint32_t stage_bytes) { return stage_bytes / 16 + 8; }
+// the stage buffer (1-bit codes: per 32-byte unit), plus 8 words of load
+// slack; four such buffers (two rounds of two tiles) replace the survivor
+// queues.
+inline uint32_t packed_words_for(uint32_t stage_bytes, int kind = kKindPacked) {
+    return stage_bytes / (kind == kKindBinary ? 32u : 16u) + 8;
+}
 
 // Reports: the byte kinds build each warp-tile's found bitmap in shared
 // memory (64 words per warp).
@@ -97,7 +107,7 @@ constexpr uint32_t kBitmapWords = kWarpStarts / 32;
 constexpr uint32_t kBitmapBytes = kConsumerWarps * kBitmapWords * 4;   // 2 KiB
 
 inline size_t scan_smem_bytes(uint32_t stage_bytes, uint32_t stages, int kind = kKindBytes, bool report = false) {
-    const size_t mid = kind_packed(kind) ? (size_t)16 * packed_words_for(stage_bytes)
+    const size_t mid = kind_packed(kind) ? (size_t)16 * packed_words_for(stage_bytes, kind)
                                          : kQueueBytes + (report ? kBitmapBytes : 0u);
     return kScanHeader + mid + (size_t)stage_bytes * stages;
 }

@@ -183,8 +183,10 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
         // rounds later, after every warp has passed the next round's
         // barrier, i.e. finished comparing.
         constexpr bool ADJ = KIND == kKindPackedAdj;
-        const uint32_t units = SB / 16, b1 = A.b1, b2 = A.b2, gather = A.gather, PW = A.packed_words;
-        const uint32_t u0 = warp * (kWarpStarts / 16) + lane;
+        constexpr bool BIN = KIND == kKindBinary;   // 1-bit codes
+        constexpr uint32_t UB = BIN ? 32u : 16u;    // stage bytes per packed word
+        const uint32_t units = SB / UB, b1 = A.b1, b2 = A.b2, gather = A.gather, PW = A.packed_words;
+        const uint32_t u0 = warp * (kWarpStarts / UB) + lane;
         for (uint32_t s = 0, phase = 0, t = 0;; ++t) {
             uint32_t* pw[2] = {pbuf + (t & 1u) * 2u * PW, pbuf + (t & 1u) * 2u * PW + PW};
             StageDesc d[2] = {{kEnd, 0}, {kEnd, 0}};
@@ -196,13 +198,26 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
                 d[k] = desc[ss];
                 if (d[k].tile == kEnd) break;
                 const uint4* b4 = reinterpret_cast<const uint4*>(bufs + (size_t)ss * SB);
-                uint4 x[4];
+                if constexpr (BIN) {
+                    uint4 x[4];
 #pragma unroll
-                for (int c = 0; c < 4; ++c) x[c] = b4[u0 + 32 * c];
+                    for (int c = 0; c < 2; ++c) {
+                        x[2 * c] = b4[2 * (u0 + 32 * c)];
+                        x[2 * c + 1] = b4[2 * (u0 + 32 * c) + 1];
+                    }
 #pragma unroll
-                for (int c = 0; c < 4; ++c) pw[k][u0 + 32 * c] = pack16<ADJ>(x[c], b1, b2, gather);
-                for (uint32_t u = kTile / 16 + tid; u < units; u += kConsumerWarps * 32)
-                    pw[k][u] = pack16<ADJ>(b4[u], b1, b2, gather);
+                    for (int c = 0; c < 2; ++c) pw[k][u0 + 32 * c] = pack32(x[2 * c], x[2 * c + 1], b1);
+                    for (uint32_t u = kTile / 32 + tid; u < units; u += kConsumerWarps * 32)
+                        pw[k][u] = pack32(b4[2 * u], b4[2 * u + 1], b1);
+                } else {
+                    uint4 x[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) x[c] = b4[u0 + 32 * c];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) pw[k][u0 + 32 * c] = pack16<ADJ>(x[c], b1, b2, gather);
+                    for (uint32_t u = kTile / 16 + tid; u < units; u += kConsumerWarps * 32)
+                        pw[k][u] = pack16<ADJ>(b4[u], b1, b2, gather);
+                }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[ss]);
                 if (++ss == S) {
@@ -233,8 +248,13 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
                     ? A.bitmaps + (d[0].tile * kConsumerWarps + warp) * kBitmapWords : nullptr,
                 MODE == kModeTileCount && A.bitmaps && two
                     ? A.bitmaps + (d[1].tile * kConsumerWarps + warp) * kBitmapWords : nullptr};
-            const uint2 c = packed_tiles<MODE == kModeWrite, MODE != kModeWrite>(
-                pk, two, warp, lane, ParamQC<MAXM>{&P}, m, r, A.ng, A.nstarts, s0, out, A.d_pos, A.cap, bm);
+            uint2 c;
+            if constexpr (BIN)
+                c = binary_tiles<MODE == kModeWrite, MODE != kModeWrite>(pk, two, warp, lane, ParamQC<MAXM>{&P}, m, r,
+                                                                         A.ng, A.nstarts, s0, out, A.d_pos, A.cap, bm);
+            else
+                c = packed_tiles<MODE == kModeWrite, MODE != kModeWrite>(pk, two, warp, lane, ParamQC<MAXM>{&P}, m, r,
+                                                                         A.ng, A.nstarts, s0, out, A.d_pos, A.cap, bm);
             if (MODE == kModeTileCount) {
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
@@ -561,6 +581,7 @@ cudaError_t launch_kind(int kind, uint32_t grid, size_t smem, cudaStream_t st, c
         case kKindBytes: return launch_one<MAXM, MODE, kKindBytes>(grid, smem, st, a, qc, groups);
         case kKindSeven: return launch_one<MAXM, MODE, kKindSeven>(grid, smem, st, a, qc, groups);
         case kKindPackedAdj: return launch_one<MAXM, MODE, kKindPackedAdj>(grid, smem, st, a, qc, groups);
+        case kKindBinary: return launch_one<MAXM, MODE, kKindBinary>(grid, smem, st, a, qc, groups);
         default: return launch_one<MAXM, MODE, kKindPacked>(grid, smem, st, a, qc, groups);
     }
 }
@@ -577,6 +598,7 @@ const void* pick_kind(int kind, uint32_t m) {
         case kKindBytes: return kernel_ptr<MODE, kKindBytes>(m);
         case kKindSeven: return kernel_ptr<MODE, kKindSeven>(m);
         case kKindPackedAdj: return kernel_ptr<MODE, kKindPackedAdj>(m);
+        case kKindBinary: return kernel_ptr<MODE, kKindBinary>(m);
         default: return kernel_ptr<MODE, kKindPacked>(m);
     }
 }

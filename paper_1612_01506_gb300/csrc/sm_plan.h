@@ -230,20 +230,42 @@ inline bool packed_code_bits(const uint64_t* hist, uint32_t* b1, uint32_t* b2) {
     return false;
 }
 
-// Packed group descriptor: window E' = e >> 6 (four packed words) in bits
-// 0-8; bit 9 + D set when the group has the compare of class D = (e >> 4) & 3
-// with e mod 16 == 0 (no shift); bits 13 + 4D .. 16 + 4D the number (0..15)
-// of its other compares of class D.
+// Bit b1 at which the text's symbols (at most two; hist has 256 bins)
+// differ, so that it is an injective 1-bit code (0 for a single symbol).
+// False when the text has more than two symbols.
+inline bool binary_code_bit(const uint64_t* hist, uint32_t* b1) {
+    uint32_t sym[2], ns = 0;
+    for (uint32_t c = 0; c < 256; ++c)
+        if (hist[c]) {
+            if (ns == 2) return false;
+            sym[ns++] = c;
+        }
+    if (ns == 0) return false;
+    uint32_t x = 0;
+    if (ns == 2)
+        while (!(((sym[0] ^ sym[1]) >> x) & 1u)) ++x;
+    *b1 = x;
+    return true;
+}
+
+// Packed group descriptor: window E' = e >> 6 (64 starts: four words of
+// 2-bit codes, two of 1-bit codes) in bits 0-8; bit 9 + D set when the group
+// has the compare of word class D (2-bit codes: D = (e >> 4) & 3, 1-bit codes:
+// D = (e >> 5) & 1) that needs no shift (e mod 16 == 0, resp. e mod 32 == 0);
+// then the number of its other compares of class D: 2-bit codes in bits
+// 13 + 4D .. 16 + 4D (at most 15), 1-bit codes in bits 13 + 5D .. 17 + 5D
+// (at most 31).
 constexpr uint32_t max_packed_groups_for(uint32_t m) { return (14 + m) / 64 + 1; }
 
-// Plans the dense phase on 2-bit codes. v[j] = (e << 8) | code in the order
-// pi, freq[j] the text frequency of its symbol (nullptr: unknown). A packed
-// compare costs a few integer instructions per 16 starts, so the first
-// compares of pi are peeled until fewer than 1e-5 of the starts are
-// expected to survive (or all m; r_fixed > 0 peels r_fixed). Output as for
-// plan_dense, with packed group descriptors.
+// Plans the dense phase on 2-bit codes (bits = 2) or 1-bit codes (bits = 1).
+// v[j] = (e << 8) | code in the order pi, freq[j] the text frequency of its
+// symbol (nullptr: unknown). A packed compare costs a few integer
+// instructions per 16 (32) starts, so the first compares of pi are peeled
+// until fewer than 1e-5 of the starts are expected to survive (or all m;
+// r_fixed > 0 peels r_fixed). Output as for plan_dense, with packed group
+// descriptors.
 inline uint32_t plan_packed(const uint32_t* v, uint32_t m, const double* freq, uint32_t r_fixed, uint32_t* qc,
-                            uint32_t* groups, uint32_t max_groups, uint32_t* ng) {
+                            uint32_t* groups, uint32_t max_groups, uint32_t* ng, uint32_t bits = 2) {
     uint32_t r = 0;
     if (r_fixed) {
         r = r_fixed < m ? r_fixed : m;
@@ -253,9 +275,10 @@ inline uint32_t plan_packed(const uint32_t* v, uint32_t m, const double* freq, u
         double alive = 1.0;
         while (r < m && r < 64 && (r < 2 || alive >= 1e-5)) alive *= freq[r++];
     }
+    const uint32_t cb = bits == 1 ? 5u : 4u;                     // log2 of the starts per word
     auto win = [](uint32_t x) { return x >> 14; };               // e >> 6
-    auto cls = [](uint32_t x) { return (x >> 12) & 3u; };        // (e >> 4) & 3
-    auto unshifted = [](uint32_t x) { return ((x >> 8) & 15u) == 0; };
+    auto cls = [cb](uint32_t x) { return (x >> (8 + cb)) & ((64u >> cb) - 1u); };
+    auto unshifted = [cb](uint32_t x) { return ((x >> 8) & ((1u << cb) - 1u)) == 0; };
     uint32_t o = 0, g = 0;
     int64_t prev = -1;
     while (o < r) {
@@ -272,7 +295,7 @@ inline uint32_t plan_packed(const uint32_t* v, uint32_t m, const double* freq, u
                         qc[o++] = v[a];
                         ++cnt;
                     }
-                desc |= pass == 0 ? (cnt << (9 + d)) : (cnt << (13 + 4 * d));
+                desc |= pass == 0 ? (cnt << (9 + d)) : (cnt << (13 + (bits == 1 ? 5u : 4u) * d));
             }
         if (g >= max_groups) return 0;
         groups[g++] = desc;

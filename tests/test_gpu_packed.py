@@ -1,11 +1,12 @@
-"""GPU parity of the 2-bit compare path (texts of at most four symbols).
+"""GPU parity of the coded compare paths (texts of at most four symbols).
 
-With the text histogram, sm_count and sm_report compare 2-bit codes of the
-symbols when the text holds at most four distinct bytes; SM_SEARCH_BYTES
-forces the byte compare on the same input. Both must equal the CPU oracle
-bit for bit: counts and ordered positions, across tile and halo edges,
-misaligned texts, forced peels and both code-bit layouts (adjacent bits, as
-for ACGT, and bits that are not adjacent).
+With the text histogram, sm_count and sm_report compare 1-bit codes of the
+symbols when the text holds at most two distinct bytes and 2-bit codes when
+it holds at most four; SM_SEARCH_BYTES forces the byte compare on the same
+input. Both must equal the CPU oracle bit for bit: counts and ordered
+positions, across tile and halo edges, misaligned texts, forced peels, both
+2-bit code layouts (adjacent bits, as for ACGT, and bits that are not
+adjacent) and 1-bit codes from a low or the top bit.
 """
 import numpy as np
 import pytest
@@ -23,6 +24,7 @@ ALPHABETS = {
     "acgt": b"ACGT",
     "nonadjacent": b"\x00\x01\x04\x05",
     "binary": b"01",
+    "binary_top_bit": b"\x10\x90",
     "three": b"xyz",
     "one": b"a",
 }
@@ -97,7 +99,7 @@ def test_packed_count_edges(torch, ctx, name, n):
                 assert count(ctx, text, p, hist=hist, bytes_only=True) == want, (name, n, offset, m)
 
 
-@pytest.mark.parametrize("name", ["acgt", "nonadjacent", "binary"])
+@pytest.mark.parametrize("name", ["acgt", "nonadjacent", "binary", "binary_top_bit"])
 def test_packed_peel_and_order(torch, ctx, name):
     alpha = ALPHABETS[name]
     n = 5 * TILE + 99

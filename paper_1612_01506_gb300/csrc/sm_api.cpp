@@ -443,7 +443,10 @@ static sm_status search(sm_ctx* c, const uint8_t* d_text, uint64_t n, const uint
     Grid gr;
     st = plan_grid(c, mode1, pl.kind, report, m, nstarts, &gr);
     if (st != SM_OK) return st;
+    const uint64_t wranges = std::max<uint64_t>(1, std::min<uint64_t>(gr.ntiles, 4ull * (uint64_t)c->num_sms));
     if (report) {
+        st = grow(&c->d_partials, &c->partials_cap, std::max<size_t>((size_t)wranges, 256), "partials");
+        if (st != SM_OK) return st;
         st = grow(&c->d_warp_counts, &c->warp_counts_cap, (size_t)gr.ntiles * smk::kConsumerWarps,
                   "per-warp tile counts");
         if (st != SM_OK) return st;
@@ -459,18 +462,22 @@ static sm_status search(sm_ctx* c, const uint8_t* d_text, uint64_t n, const uint
     e = smk::launch_scan(mode1, pl.kind, gr.grid, gr.smem, s, a, pl.qc.data(), pl.groups.data());
     if (e != cudaSuccess) return cuda_fail(e, "scan launch");
     if (report) {
-        e = smk::launch_range_sums(gr.grid, s, c->d_warp_counts, gr.ntiles, gr.per_cta, c->d_partials);
+        // the write pass: ranges of tiles, four blocks per SM (its latency
+        // is hidden by more warps than the scan's grid gives)
+        const uint64_t per = (gr.ntiles + wranges - 1) / wranges;
+        const uint32_t wgrid = (uint32_t)((gr.ntiles + per - 1) / per);
+        e = smk::launch_range_sums(wgrid, s, c->d_warp_counts, gr.ntiles, per, c->d_partials);
         if (e != cudaSuccess) return cuda_fail(e, "range count launch");
         smk::WriteArgs w{};
         w.ntiles = gr.ntiles;
-        w.tiles_per_cta = gr.per_cta;
+        w.tiles_per_cta = per;
         w.partials = c->d_partials;
         w.warp_counts = c->d_warp_counts;
         w.bitmaps = c->d_bitmaps;
         w.d_pos = d_pos;
         w.cap = cap;
         w.status = c->d_status;
-        e = smk::launch_bitmap_write(gr.grid, s, w);
+        e = smk::launch_bitmap_write(wgrid, s, w);
         if (e != cudaSuccess) return cuda_fail(e, "report launch");
     }
     return SM_OK;

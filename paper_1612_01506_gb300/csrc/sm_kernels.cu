@@ -384,10 +384,14 @@ __global__ void __launch_bounds__(kWriteThreads) range_sum_kernel(const uint32_t
 // read again). Its first rank is the sum of the earlier ranges' counts. The
 // range's warp counts are read into shared memory kWalk tiles at a time and
 // scanned there (tile offsets, warp offsets); then every warp turns the
-// bitmaps of its own warp-tiles with matches into positions, staged through
-// shared memory so that the stores are coalesced, loading the next bitmap
-// while it writes the current one.
+// bitmaps of its own warp-tiles with matches into positions: a warp-tile
+// with few matches is handled by one lane (32 at a time, each reading its
+// bitmap and storing its positions in order); one with many by the whole
+// warp, staged through shared memory so that the stores are coalesced, with
+// the bitmaps of the next kAhead such warp-tiles in flight while it writes.
 constexpr uint32_t kWalk = 256;   // tiles per pass over shared memory (one per thread)
+constexpr uint32_t kAhead = 4;    // bitmaps in flight per warp
+constexpr uint32_t kLaneTile = 64; // warp-tiles with at most this many matches are written by one lane
 
 __global__ void __launch_bounds__(kWriteThreads) bitmap_write_kernel(const __grid_constant__ WriteArgs W) {
     static_assert(kWalk == kWriteThreads, "one tile per thread");
@@ -397,6 +401,7 @@ __global__ void __launch_bounds__(kWriteThreads) bitmap_write_kernel(const __gri
     __shared__ uint32_t toff[kWalk];                  // tile offsets within the pass
     __shared__ uint64_t red[kConsumerWarps];
     __shared__ uint64_t base_s;
+    __shared__ uint8_t list[kConsumerWarps][kWalk];   // per warp: its warp-tiles with matches in the pass
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint64_t t0 = (uint64_t)blockIdx.x * W.tiles_per_cta;
     const uint64_t t1 = min(t0 + W.tiles_per_cta, W.ntiles);
@@ -447,54 +452,91 @@ __global__ void __launch_bounds__(kWriteThreads) bitmap_write_kernel(const __gri
         for (int w = 0; w < kConsumerWarps; ++w) pass_tot += red[w];
         __syncthreads();
 
-        // warp w: its warp-tiles with matches, in tile order (the bitmap of
-        // the next one is loaded while the current one is written)
-        uint32_t i = 0;
-        uint32_t w0 = 0, w1 = 0;
+        // warp w: the list of its warp-tiles with matches in the pass, in
+        // tile order (from ballots), then their bitmaps -> positions, the
+        // bitmaps loaded kAhead entries before they are written
         auto own = [&](uint32_t k) -> uint32_t {   // matches of warp-tile (p0 + k, warp)
             return (warp + 1 < kConsumerWarps ? woff[k][warp + 1] : ttot[k]) - woff[k][warp];
         };
-        auto next_from = [&](uint32_t k) -> uint32_t {
-            while (k < np && own(k) == 0) ++k;
-            return k;
-        };
-        i = next_from(0);
-        if (i < np) {
-            const uint2 x = __ldcg(reinterpret_cast<const uint2*>(W.bitmaps + ((p0 + i) * kConsumerWarps + warp) *
-                                                                                  kBitmapWords) + lane);
-            w0 = x.x;
-            w1 = x.y;
+        // warp-tiles with more than kLaneTile matches (front of the list) are
+        // written by the whole warp; the others (back of the list) one per lane
+        uint8_t* lst = list[warp];
+        uint32_t cnt = 0, ns = 0;
+        for (uint32_t c0 = 0; c0 < np; c0 += 32) {
+            const uint32_t k = c0 + lane;
+            const uint32_t o = k < np ? own(k) : 0u;
+            const uint32_t bal = __ballot_sync(kFull, o > kLaneTile);
+            const uint32_t sal = __ballot_sync(kFull, o != 0 && o <= kLaneTile);
+            const uint32_t lt = (1u << lane) - 1u;
+            if (o > kLaneTile) lst[cnt + __popc(bal & lt)] = (uint8_t)k;
+            if (o != 0 && o <= kLaneTile) lst[kWalk - 1 - (ns + __popc(sal & lt))] = (uint8_t)k;
+            cnt += __popc(bal);
+            ns += __popc(sal);
         }
-        while (i < np) {
-            const uint32_t j2 = next_from(i + 1);
-            uint32_t n0 = 0, n1 = 0;
-            if (j2 < np) {
-                const uint2 x = __ldcg(reinterpret_cast<const uint2*>(W.bitmaps + ((p0 + j2) * kConsumerWarps +
-                                                                                     warp) * kBitmapWords) + lane);
-                n0 = x.x;
-                n1 = x.y;
+        __syncwarp();
+        for (uint32_t g = 0; g < ns; g += 32) {
+            if (g + lane < ns) {
+                const uint32_t k = lst[kWalk - 1 - (g + lane)];
+                const uint4* bp = reinterpret_cast<const uint4*>(W.bitmaps + ((p0 + k) * kConsumerWarps + warp) *
+                                                                                 kBitmapWords);
+                const uint64_t s0 = (p0 + k) * kTile + warp * kWarpStarts;
+                uint64_t o = base + toff[k] + woff[k][warp];
+                uint32_t left = own(k);
+                for (uint32_t q0 = 0; q0 < kBitmapWords / 4 && left; q0 += 4) {
+                    uint4 x[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) x[q] = __ldcg(bp + q0 + q);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const uint32_t w[4] = {x[q].x, x[q].y, x[q].z, x[q].w};
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            uint32_t fw = w[i];
+                            while (fw) {
+                                if (o < W.cap) W.d_pos[o] = s0 + 128u * (q0 + q) + 32u * i + (uint32_t)(__ffs(fw) - 1);
+                                ++o;
+                                --left;
+                                fw &= fw - 1;
+                            }
+                        }
+                    }
+                }
             }
-            const uint32_t mine = own(i);
-            const uint32_t n = __popc(w0) + __popc(w1);
+        }
+        auto load = [&](uint32_t j) -> uint2 {
+            return __ldcg(reinterpret_cast<const uint2*>(W.bitmaps + ((p0 + lst[j]) * kConsumerWarps + warp) *
+                                                                         kBitmapWords) + lane);
+        };
+        auto write = [&](uint32_t j, uint2 x) {
+            const uint32_t k = lst[j];
+            const uint32_t n = __popc(x.x) + __popc(x.y);
             const uint32_t inc2 = warp_incl_scan(n, lane);
-            const uint64_t tile = p0 + i;
-            const uint32_t a0 = w0, a1 = w1;
-            staged_write(stg, lane, inc2 - n, n, mine, tile * kTile + warp * kWarpStarts,
-                         base + toff[i] + woff[i][warp], W.d_pos, W.cap, [&](auto&& cb) {
-                             uint32_t kk = 0, fw = a0;
+            staged_write(stg, lane, inc2 - n, n, own(k), (p0 + k) * kTile + warp * kWarpStarts,
+                         base + toff[k] + woff[k][warp], W.d_pos, W.cap, [&](auto&& cb) {
+                             uint32_t kk = 0, fw = x.x;
                              while (fw) {
                                  cb(kk++, 64u * lane + (uint32_t)(__ffs(fw) - 1));
                                  fw &= fw - 1;
                              }
-                             fw = a1;
+                             fw = x.y;
                              while (fw) {
                                  cb(kk++, 64u * lane + 32u + (uint32_t)(__ffs(fw) - 1));
                                  fw &= fw - 1;
                              }
                          });
-            i = j2;
-            w0 = n0;
-            w1 = n1;
+        };
+        uint2 pre[kAhead];
+#pragma unroll
+        for (uint32_t d = 0; d < kAhead; ++d) pre[d] = d < cnt ? load(d) : make_uint2(0u, 0u);
+        for (uint32_t j = 0; j < cnt; j += kAhead) {
+#pragma unroll
+            for (uint32_t d = 0; d < kAhead; ++d) {
+                if (j + d < cnt) {
+                    const uint2 x = pre[d];
+                    if (j + d + kAhead < cnt) pre[d] = load(j + d + kAhead);
+                    write(j + d, x);
+                }
+            }
         }
         base += pass_tot;
         __syncthreads();   // the pass's tables are rewritten by the next one

@@ -632,7 +632,9 @@ def config_block(args, world):
     return {"workload": f"sweep n={args.n} bytes: sigma {args.kinds} x m {args.ms} x {args.patterns} "
                         f"patterns from the text, {args.variants}",
             "n": args.n, "kinds": args.kinds, "ms": args.ms, "patterns": args.patterns,
-            "variants": args.variants, "l2": "inputs larger than L2 (1 GiB texts), no flush",
+            "variants": args.variants,
+            "l2": (f"inputs larger than L2 ({args.n >> 20} MiB texts against 129 MB), no flush"
+                   if args.n > 129_000_000 else f"{args.n >> 20} MiB texts fit in L2: no flush, timings are warm"),
             "parallelism": f"weak: {world} rank(s), independent patterns per rank"}
 
 

@@ -419,6 +419,18 @@ def run_batch(args, local, steps=3, warmup=2):
     torch.cuda.synchronize()
     t_batch = ev0.elapsed_time(ev1) / 1e3 / steps
     batch_counts = out.cpu().numpy().copy()
+    # the autotuner (plan parameters by measurement), then the same timing
+    tuning = sm.sm_batch_tune(b, reps=2)
+    for _ in range(warmup):
+        sm.sm_batch_count(b, out=out)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(steps):
+        sm.sm_batch_count(b, out=out)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_tuned = ev0.elapsed_time(ev1) / 1e3 / steps
+    tuned_agree = bool(np.array_equal(out.cpu().numpy(), batch_counts))
     # one launch per pattern, same orders (rarest first under the text histogram)
     hist = sm.sm_histogram(ctx, d).cpu().numpy().view(np.uint64).copy()
     single = torch.zeros(npat, dtype=torch.int64, device=dev)
@@ -438,7 +450,8 @@ def run_batch(args, local, steps=3, warmup=2):
                         "80% from the text", "batch_ms": round(t_batch * 1e3, 3),
             "batch_patterns_gbs": round(pgb / t_batch, 1), "single_launch_ms": round(t_single * 1e3, 3),
             "single_launch_patterns_gbs": round(pgb / t_single, 1), "speedup": round(t_single / t_batch, 2),
-            "counts_agree": agree}
+            "counts_agree": agree, "tuned": tuning, "tuned_batch_ms": round(t_tuned * 1e3, 3),
+            "tuned_patterns_gbs": round(pgb / t_tuned, 1), "tuned_counts_agree": tuned_agree}
 
 
 def run_multi(args, local, steps=2, warmup=1):
@@ -519,6 +532,17 @@ def run_multi(args, local, steps=2, warmup=1):
         tc += ev[0].elapsed_time(ev[1]) / 1e3
         tr += ev[1].elapsed_time(ev[2]) / 1e3
     tc, tr = tc / steps, tr / steps
+    # the autotuner on this batch, then the counting pass again
+    tuning = sm.sm_batch_tune(b, reps=1)
+    sm.sm_batch_count(b, out=counts)
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for _ in range(steps):
+        sm.sm_batch_count(b, out=counts)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    t_tuned = ev[0].elapsed_time(ev[1]) / 1e3 / steps
+    tuned_agree = bool(np.array_equal(counts.cpu().numpy()[:npat], ch))
     status = sm.sm_sync(ctx)
     # cross-check against single-pattern calls on a sample of patterns
     rs = np.random.default_rng(5)
@@ -543,7 +567,9 @@ def run_multi(args, local, steps=2, warmup=1):
             "texts_bytes": total, "patterns": npat, "positions": int(pos_off[-1]),
             "plan_s": round(t_plan, 3), "count_ms": round(tc * 1e3, 3), "report_ms": round(tr * 1e3, 3),
             "count_patterns_gbs": round(pgb / tc, 1), "report_patterns_gbs": round(pgb / tr, 1),
-            "status": status, "sample_agrees_with_single_calls": agree, "sample": int(sample.size)}
+            "status": status, "sample_agrees_with_single_calls": agree, "sample": int(sample.size),
+            "tuned": tuning, "tuned_count_ms": round(t_tuned * 1e3, 3),
+            "tuned_count_patterns_gbs": round(pgb / t_tuned, 1), "tuned_counts_agree": tuned_agree}
 
 
 # ---------------------------------------------------------------- serving

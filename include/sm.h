@@ -232,6 +232,23 @@ sm_status sm_batch_count(sm_batch* batch, int64_t* d_counts, sm_stream_t stream)
  */
 sm_status sm_batch_report(sm_batch* batch, int64_t* d_counts, uint64_t* d_pos, const int64_t* d_pos_off,
                           sm_stream_t stream);
+/*
+ * sm_batch_tune: the batch's autotuner. Times sm_batch_count (one warm-up
+ * and reps timed launches per plan, on `stream`) for the plan it has and for
+ * every plan over a grid of parameters: the text frequency below which a
+ * pattern's rarest symbol sends it to the candidate path {2, 4, 8, 16, 32 %},
+ * the fewest such patterns of a text that use that path {4, 16, 64}, and the
+ * pipeline stages {2, 3, 4}. Keeps the fastest plan and reports it in *best
+ * (ms = its time per count). Synchronous; allocates a counts buffer and the
+ * trial plans' tables. Counts never depend on the plan.
+ */
+typedef struct sm_batch_tuning {
+    float cand_freq;
+    uint32_t cand_min;
+    uint32_t stages;     /* 0: the context's default */
+    float ms;
+} sm_batch_tuning;
+sm_status sm_batch_tune(sm_batch* batch, uint32_t reps, sm_batch_tuning* best, sm_stream_t stream);
 void sm_batch_destroy(sm_batch* batch);
 
 /*

@@ -476,7 +476,7 @@ struct PatDesc {
 };
 
 PatDesc describe(const uint8_t* p, uint32_t m, const uint64_t* h, uint64_t n, uint32_t delta, bool text7,
-                 uint32_t out) {
+                 uint32_t out, double cand_freq = smk::kCandidateFreq) {
     PatDesc d;
     d.zero = (uint64_t)m > n;
     for (uint32_t q = 0; q < m && !d.zero; ++q) d.zero = h[p[q]] == 0;
@@ -486,7 +486,7 @@ PatDesc describe(const uint8_t* p, uint32_t m, const uint64_t* h, uint64_t n, ui
     std::stable_sort(pi.begin(), pi.end(), [&](uint32_t a, uint32_t b) { return h[p[a]] < h[p[b]]; });
     std::vector<uint32_t> v(m);
     for (uint32_t j = 0; j < m; ++j) v[j] = ((pi[j] + delta) << 8) | p[pi[j]];
-    if ((double)h[p[pi[0]]] / (double)n < smk::kCandidateFreq) {
+    if ((double)h[p[pi[0]]] / (double)n < cand_freq) {
         d.cand = true;
         d.cpat = BatchPat{0, m, 1, 0, out, text7 ? 1u : 0u};   // ng = 0: no peeled compares
         d.cqc = v;
@@ -524,10 +524,10 @@ struct Tables {
 // item.
 void add_text(Tables& T, uint64_t off, uint64_t n, uint64_t slimit, const std::vector<const PatDesc*>& ds,
               bool allow_cand = true, const std::vector<uint64_t>* tb = nullptr,
-              std::vector<PatTiles>* pt = nullptr) {
+              std::vector<PatTiles>* pt = nullptr, uint32_t cand_min = smk::kCandidateMin) {
     uint32_t ncand = 0;
     for (const PatDesc* d : ds) ncand += (!d->zero && d->cand) ? 1u : 0u;
-    const bool use_cand = allow_cand && ncand >= smk::kCandidateMin;
+    const bool use_cand = allow_cand && ncand >= cand_min;
     std::vector<const PatDesc*> order;
     for (const PatDesc* d : ds)
         if (!d->zero && !(use_cand && d->cand)) order.push_back(d);
@@ -617,11 +617,12 @@ struct Geometry {
 // Shared-memory layout and residency of a launch whose patterns have length
 // <= maxm and whose CTAs count at most nslots patterns each: the stage
 // count is lowered while that lets more CTAs reside on an SM.
-Geometry geometry(sm_ctx* ctx, uint32_t maxm, bool need_index, uint32_t nslots = kMaxSlots) {
+Geometry geometry(sm_ctx* ctx, uint32_t maxm, bool need_index, uint32_t nslots = kMaxSlots,
+                  uint32_t stages = 0) {
     Geometry g;
     g.SB = smk::stage_bytes_for(maxm);
     g.index_cap = need_index ? g.SB : 0u;
-    g.stages = sm_ctx_stages(ctx);
+    g.stages = stages ? stages : sm_ctx_stages(ctx);
     nslots = std::max(1u, std::min(nslots, kMaxSlots));
     while (g.stages > 2 && g.smem(nslots) > sm_ctx_max_smem(ctx)) --g.stages;
     const int ms = (int)sm_ctx_max_smem(ctx);
@@ -635,7 +636,7 @@ Geometry geometry(sm_ctx* ctx, uint32_t maxm, bool need_index, uint32_t nslots =
         return o;
     };
     int occ = occ_of(g);
-    while (g.stages > 2) {
+    while (!stages && g.stages > 2) {   // (a tuned stage count is kept)
         Geometry f = g;
         --f.stages;
         const int o2 = occ_of(f);
@@ -793,10 +794,25 @@ sm_status text_histograms(sm_ctx* ctx, const uint8_t* d_texts, const int64_t* be
 
 // ------------------------------------------------------------------ batch
 
+// Plan parameters the autotuner varies (defaults: the constants above and
+// the context's stage count).
+struct BatchParams {
+    double cand_freq = smk::kCandidateFreq;
+    uint32_t cand_min = smk::kCandidateMin;
+    uint32_t stages = 0;
+};
+
 struct sm_batch {
     sm_ctx* ctx = nullptr;
     int device = 0;
     uint32_t npats = 0;      // caller's pattern count (size of d_counts)
+    // the inputs, kept to plan again with other parameters
+    const uint8_t* d_texts = nullptr;
+    std::vector<int64_t> text_off, pat_off;
+    std::vector<int32_t> pat_text;
+    std::vector<uint8_t> pats;
+    std::vector<uint64_t> hist;   // per text, 256 bins
+    BatchParams params;
     uint32_t grid = 0;
     size_t smem = 0;
     BatchArgs args{};
@@ -813,6 +829,89 @@ struct sm_batch {
     uint64_t* d_toff = nullptr;
     uint8_t* d_hit = nullptr;
 };
+
+// Plans (or plans again) a batch from its kept inputs under b->params:
+// descriptions, tables of both passes, device copies, launch shapes.
+sm_status build_plan(sm_batch* b) {
+    using namespace smk;
+    sm_ctx* ctx = b->ctx;
+    const uint32_t npats = b->npats, ntexts = (uint32_t)b->text_off.size() - 1;
+    const int64_t* h_text_off = b->text_off.data();
+    const BatchParams& P = b->params;
+    std::vector<PatDesc> descs(npats);
+    std::vector<uint32_t> ms(npats);
+    std::vector<uint64_t> lens(npats);
+    for (uint32_t k = 0; k < npats; ++k) {
+        const uint32_t x = (uint32_t)b->pat_text[k];
+        const uint64_t n = (uint64_t)(h_text_off[x + 1] - h_text_off[x]);
+        const uint64_t* h = &b->hist[(size_t)x * 256];
+        const uint32_t delta = (uint32_t)((reinterpret_cast<uintptr_t>(b->d_texts) + (uint64_t)h_text_off[x]) & 15u);
+        ms[k] = (uint32_t)(b->pat_off[k + 1] - b->pat_off[k]);
+        lens[k] = n;
+        descs[k] = describe(b->pats.data() + b->pat_off[k], ms[k], h, n, delta, text_is_7bit(h), k, P.cand_freq);
+    }
+    std::vector<PatTiles> pt;
+    std::vector<uint64_t> tb;
+    const uint64_t ntb = assign_tiles(ms, lens, pt, tb);
+    // tables of the counting (and tile-count) pass, and of the write pass
+    std::vector<uint32_t> by_text(npats);
+    std::iota(by_text.begin(), by_text.end(), 0u);
+    std::stable_sort(by_text.begin(), by_text.end(),
+                     [&](uint32_t a, uint32_t c) { return b->pat_text[a] < b->pat_text[c]; });
+    Tables T, W;
+    for (size_t kk = 0, x = 0; x < ntexts; ++x) {
+        std::vector<const PatDesc*> ptrs;
+        for (; kk < npats && (uint32_t)b->pat_text[by_text[kk]] == x; ++kk) ptrs.push_back(&descs[by_text[kk]]);
+        const uint64_t n = (uint64_t)(h_text_off[x + 1] - h_text_off[x]);
+        add_text(T, (uint64_t)h_text_off[x], n, ~0ull, ptrs, true, &tb, nullptr, P.cand_min);
+        add_text(W, (uint64_t)h_text_off[x], n, ~0ull, ptrs, false, &tb, &pt);
+    }
+    const Geometry g = geometry(ctx, T.maxm, T.need_index, T.slot_hint(), P.stages);
+    finish(T, (uint64_t)sm_ctx_num_sms(ctx) * g.occ);
+    const Geometry gw = geometry(ctx, W.maxm, false, W.slot_hint(), P.stages);
+    finish(W, (uint64_t)sm_ctx_num_sms(ctx) * gw.occ);
+
+    // one allocation for each pass's tables (the write pass's also holds the
+    // per-pattern counter ranges); the previous plan's are freed
+    const Layout L = layout_of(T);
+    const Layout LW = layout_of(W);
+    const size_t pt_off = LW.total, wtotal = pt_off + std::max<size_t>(pt.size(), 1) * sizeof(PatTiles);
+    std::vector<char> host(std::max(L.total, wtotal));
+    if (b->d_mem || b->d_wmem) cudaDeviceSynchronize();   // no launch may still read them
+    if (b->d_mem) cudaFree(b->d_mem);
+    if (b->d_wmem) cudaFree(b->d_wmem);
+    b->d_mem = b->d_wmem = nullptr;
+    if (b->d_hit && b->nitems != W.items) {
+        cudaFree(b->d_tcnt);
+        cudaFree(b->d_toff);
+        cudaFree(b->d_hit);
+        b->d_tcnt = nullptr;
+        b->d_toff = nullptr;
+        b->d_hit = nullptr;
+    }
+    b->ntb = ntb;
+    b->nitems = W.items;
+    if (cudaMalloc(&b->d_mem, L.total) != cudaSuccess || cudaMalloc(&b->d_wmem, wtotal) != cudaSuccess) {
+        cudaGetLastError();
+        return sm_fail_internal(SM_ENOMEM, "batch plan tables");
+    }
+    pack(T, L, host.data());
+    cudaError_t e = cudaMemcpy(b->d_mem, host.data(), L.total, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        pack(W, LW, host.data());
+        if (!pt.empty()) std::memcpy(host.data() + pt_off, pt.data(), pt.size() * sizeof(PatTiles));
+        e = cudaMemcpy(b->d_wmem, host.data(), wtotal, cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) return sm_fail_internal(SM_ECUDA, cudaGetErrorString(e));
+    b->args = args_for(ctx, b->d_texts, T, L, static_cast<char*>(b->d_mem), g);
+    b->grid = (uint32_t)T.cta_pbase.size();
+    b->smem = g.smem(T.nslots);
+    b->wargs = args_for(ctx, b->d_texts, W, LW, static_cast<char*>(b->d_wmem), gw);
+    b->wgrid = (uint32_t)W.cta_pbase.size();
+    b->wsmem = gw.smem(W.nslots);
+    b->d_pt = reinterpret_cast<const PatTiles*>(static_cast<char*>(b->d_wmem) + pt_off);
+    return SM_OK;
+}
 
 extern "C" sm_status sm_batch_create(sm_ctx* ctx, const uint8_t* d_texts, const int64_t* h_text_off, uint32_t ntexts,
                                      const uint8_t* h_pats, const int64_t* h_pat_off, const int32_t* h_pat_text,
@@ -841,76 +940,21 @@ extern "C" sm_status sm_batch_create(sm_ctx* ctx, const uint8_t* d_texts, const 
     const sm_status hs = text_histograms(ctx, d_texts, h_text_off, h_text_off + 1, ntexts, st, hist);
     if (hs != SM_OK) return hs;
 
-    // 2. patterns described under their text's frequencies; per-tile
-    // counters for reports
-    std::vector<PatDesc> descs(npats);
-    std::vector<uint32_t> ms(npats);
-    std::vector<uint64_t> lens(npats);
-    for (uint32_t k = 0; k < npats; ++k) {
-        const uint32_t x = (uint32_t)h_pat_text[k];
-        const uint64_t n = (uint64_t)(h_text_off[x + 1] - h_text_off[x]);
-        const uint64_t* h = &hist[(size_t)x * 256];
-        const uint32_t delta = (uint32_t)((reinterpret_cast<uintptr_t>(d_texts) + (uint64_t)h_text_off[x]) & 15u);
-        ms[k] = (uint32_t)(h_pat_off[k + 1] - h_pat_off[k]);
-        lens[k] = n;
-        descs[k] = describe(h_pats + h_pat_off[k], ms[k], h, n, delta, text_is_7bit(h), k);
-    }
-    std::vector<PatTiles> pt;
-    std::vector<uint64_t> tb;
-    const uint64_t ntb = assign_tiles(ms, lens, pt, tb);
-    // tables of the counting (and tile-count) pass, and of the write pass
-    std::vector<uint32_t> by_text(npats);
-    std::iota(by_text.begin(), by_text.end(), 0u);
-    std::stable_sort(by_text.begin(), by_text.end(),
-                     [&](uint32_t a, uint32_t b) { return h_pat_text[a] < h_pat_text[b]; });
-    Tables T, W;
-    for (size_t kk = 0, x = 0; x < ntexts; ++x) {
-        std::vector<const PatDesc*> ptrs;
-        for (; kk < npats && (uint32_t)h_pat_text[by_text[kk]] == x; ++kk) ptrs.push_back(&descs[by_text[kk]]);
-        const uint64_t n = (uint64_t)(h_text_off[x + 1] - h_text_off[x]);
-        add_text(T, (uint64_t)h_text_off[x], n, ~0ull, ptrs, true, &tb);
-        add_text(W, (uint64_t)h_text_off[x], n, ~0ull, ptrs, false, &tb, &pt);
-    }
-    const Geometry g = geometry(ctx, T.maxm, T.need_index, T.slot_hint());
-    finish(T, (uint64_t)sm_ctx_num_sms(ctx) * g.occ);
-    const Geometry gw = geometry(ctx, W.maxm, false, W.slot_hint());
-    finish(W, (uint64_t)sm_ctx_num_sms(ctx) * gw.occ);
-
-    // 3. one allocation for each pass's tables (the write pass's also holds
-    // the per-pattern counter ranges)
-    const Layout L = layout_of(T);
-    const Layout LW = layout_of(W);
-    const size_t pt_off = LW.total, wtotal = pt_off + std::max<size_t>(pt.size(), 1) * sizeof(PatTiles);
-    std::vector<char> host(std::max(L.total, wtotal));
     sm_batch* b = new sm_batch();
     b->ctx = ctx;
     b->device = sm_ctx_device(ctx);
     b->npats = npats;
-    b->ntb = ntb;
-    b->nitems = W.items;
-    if (cudaMalloc(&b->d_mem, L.total) != cudaSuccess || cudaMalloc(&b->d_wmem, wtotal) != cudaSuccess) {
-        cudaGetLastError();
+    b->d_texts = d_texts;
+    b->text_off.assign(h_text_off, h_text_off + ntexts + 1);
+    b->pat_off.assign(h_pat_off, h_pat_off + npats + 1);
+    b->pat_text.assign(h_pat_text, h_pat_text + npats);
+    b->pats.assign(h_pats, h_pats + (npats ? h_pat_off[npats] : 0));
+    b->hist = std::move(hist);
+    const sm_status ps = build_plan(b);
+    if (ps != SM_OK) {
         sm_batch_destroy(b);
-        return sm_fail_internal(SM_ENOMEM, "batch plan tables");
+        return ps;
     }
-    pack(T, L, host.data());
-    cudaError_t e = cudaMemcpy(b->d_mem, host.data(), L.total, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) {
-        pack(W, LW, host.data());
-        if (!pt.empty()) std::memcpy(host.data() + pt_off, pt.data(), pt.size() * sizeof(PatTiles));
-        e = cudaMemcpy(b->d_wmem, host.data(), wtotal, cudaMemcpyHostToDevice);
-    }
-    if (e != cudaSuccess) {
-        sm_batch_destroy(b);
-        return sm_fail_internal(SM_ECUDA, cudaGetErrorString(e));
-    }
-    b->args = args_for(ctx, d_texts, T, L, static_cast<char*>(b->d_mem), g);
-    b->grid = (uint32_t)T.cta_pbase.size();
-    b->smem = g.smem(T.nslots);
-    b->wargs = args_for(ctx, d_texts, W, LW, static_cast<char*>(b->d_wmem), gw);
-    b->wgrid = (uint32_t)W.cta_pbase.size();
-    b->wsmem = gw.smem(W.nslots);
-    b->d_pt = reinterpret_cast<const PatTiles*>(static_cast<char*>(b->d_wmem) + pt_off);
     *out = b;
     return SM_OK;
 }
@@ -959,6 +1003,61 @@ extern "C" sm_status sm_batch_report(sm_batch* b, int64_t* d_counts, uint64_t* d
     const cudaError_t e = run_report(a1, b->grid, b->smem, a2, b->wgrid, b->wsmem, b->d_pt, b->npats, b->d_tcnt,
                                      b->ntb, b->nitems, d_counts, b->npats, st);
     return e == cudaSuccess ? SM_OK : sm_fail_internal(SM_ECUDA, cudaGetErrorString(e));
+}
+
+extern "C" sm_status sm_batch_tune(sm_batch* b, uint32_t reps, sm_batch_tuning* best, sm_stream_t stream) {
+    if (!b || !best) return sm_fail_internal(SM_EINVAL, "NULL argument");
+    if (reps < 1) reps = 1;
+    Guard g(b->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int64_t* d_counts = nullptr;
+    if (cudaMalloc(&d_counts, std::max<size_t>(b->npats, 1) * sizeof(int64_t)) != cudaSuccess) {
+        cudaGetLastError();
+        return sm_fail_internal(SM_ENOMEM, "tuning counts");
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    // ms per count under the current plan: one warm-up launch, then reps
+    auto time_plan = [&](float* ms) -> sm_status {
+        sm_status s = sm_batch_count(b, d_counts, stream);
+        if (s == SM_OK && cudaEventRecord(e0, st) != cudaSuccess) s = SM_ECUDA;
+        for (uint32_t r = 0; s == SM_OK && r < reps; ++r) s = sm_batch_count(b, d_counts, stream);
+        if (s == SM_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                           cudaEventElapsedTime(ms, e0, e1) != cudaSuccess))
+            s = sm_fail_internal(SM_ECUDA, "tuning timer");
+        *ms /= (float)reps;
+        return s;
+    };
+    const BatchParams start = b->params;
+    BatchParams top = start;
+    float top_ms = 0;
+    sm_status s = time_plan(&top_ms);
+    for (const double f : {0.02, 0.04, 0.08, 0.16, 0.32})
+        for (const uint32_t cm : {4u, 16u, 64u})
+            for (const uint32_t stg : {2u, 3u, 4u}) {
+                if (s != SM_OK) break;
+                b->params = BatchParams{f, cm, stg};
+                s = build_plan(b);
+                float ms = 0;
+                if (s == SM_OK) s = time_plan(&ms);
+                if (s == SM_OK && ms < top_ms) {
+                    top_ms = ms;
+                    top = b->params;
+                }
+            }
+    b->params = s == SM_OK ? top : start;
+    const sm_status s2 = build_plan(b);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(d_counts);
+    if (s != SM_OK) return s;
+    if (s2 != SM_OK) return s2;
+    best->cand_freq = (float)top.cand_freq;
+    best->cand_min = top.cand_min;
+    best->stages = top.stages;
+    best->ms = top_ms;
+    return SM_OK;
 }
 
 extern "C" void sm_batch_destroy(sm_batch* b) {

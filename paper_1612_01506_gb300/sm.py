@@ -26,7 +26,7 @@ SM_NOALLOC_MAX_STARTS = 16384 * 16384
 EXPORTS = ("sm_create", "sm_destroy", "sm_last_error", "sm_status_string", "sm_sync", "sm_set_knob",
            "sm_histogram", "sm_order", "sm_order_fixed", "sm_count", "sm_count_ex", "sm_report",
            "sm_report_ex", "sm_report_noalloc", "sm_batch_create", "sm_batch_count", "sm_batch_report",
-           "sm_batch_destroy", "sm_count_batch", "sm_stepper_create", "sm_stepper_chunks", "sm_stepper_admit",
+           "sm_batch_tune", "sm_batch_destroy", "sm_count_batch", "sm_stepper_create", "sm_stepper_chunks", "sm_stepper_admit",
            "sm_stepper_step", "sm_stepper_retire", "sm_stepper_report", "sm_stepper_destroy")
 
 
@@ -37,6 +37,10 @@ class SmError(RuntimeError):
 
 
 SM_SEARCH_BYTES = 1
+
+
+class BatchTuning(C.Structure):
+    _fields_ = [("cand_freq", C.c_float), ("cand_min", C.c_uint32), ("stages", C.c_uint32), ("ms", C.c_float)]
 
 
 class SearchOpts(C.Structure):
@@ -81,6 +85,7 @@ def load():
                                  C.POINTER(C.c_int32), u32, C.POINTER(vp), vp]),
         "sm_batch_count": (st, [vp, vp, vp]),
         "sm_batch_report": (st, [vp, vp, vp, vp, vp]),
+        "sm_batch_tune": (st, [vp, u32, C.POINTER(BatchTuning), vp]),
         "sm_batch_destroy": (None, [vp]),
         "sm_count_batch": (st, [vp, vp, vp, u32, vp, vp, vp, u32, vp, vp, vp, vp]),
     }
@@ -316,6 +321,13 @@ def sm_batch_report(batch: Batch, d_pos_off, d_pos=None, out=None, stream=None):
     _check(load().sm_batch_report(batch.handle, _dev_ptr(out, _WORD64), _dev_ptr(d_pos, _WORD64),
                                   _dev_ptr(d_pos_off, _WORD64), _stream(stream)))
     return out, d_pos
+
+
+def sm_batch_tune(batch: Batch, reps: int = 2, stream=None) -> dict:
+    """Run the batch's autotuner; returns the chosen plan parameters and its ms per count."""
+    t = BatchTuning()
+    _check(load().sm_batch_tune(batch.handle, reps, C.byref(t), _stream(stream)))
+    return {"cand_freq": round(t.cand_freq, 4), "cand_min": t.cand_min, "stages": t.stages, "ms": t.ms}
 
 
 def sm_count_batch(ctx: Ctx, texts, d_text_off, d_pats, d_pat_off, d_pat_text, d_counts, d_pos=None,

@@ -201,3 +201,22 @@ def test_batch_report_dense_matches(torch, ctx):
     allpos = dpos.cpu().numpy().view(np.uint64)
     for k, pos in enumerate(oracle_positions(texts, pats, pt, want)):
         assert np.array_equal(allpos[poff[k]:poff[k + 1]], pos), k
+
+
+def test_batch_tune_keeps_results(torch, ctx):
+    # the autotuner re-plans the batch; counts and positions stay exact
+    texts, flat, off, pats, pt = make_batch(31, [70_000, 3 * 16384 + 5, 9000], ["markov95", 4, 20], 40, 300)
+    want = expected(texts, pats, pt)
+    d = to_dev(torch, flat)
+    b = sm.sm_batch_create(ctx, d, off, pats, pt)
+    best = sm.sm_batch_tune(b, reps=1)
+    assert best["ms"] > 0 and best["cand_min"] in (4, 16, 64) and best["stages"] in (0, 2, 3, 4)
+    assert np.array_equal(sm.sm_batch_count(b).cpu().numpy()[: len(pats)], want)
+    poff = np.zeros(len(pats) + 1, np.int64)
+    poff[1:] = np.cumsum(want)
+    counts, dpos = sm.sm_batch_report(b, torch.from_numpy(poff).cuda())
+    assert sm.sm_sync(ctx) == sm.SM_OK
+    assert np.array_equal(counts.cpu().numpy()[: len(pats)], want)
+    allpos = dpos.cpu().numpy().view(np.uint64)
+    for k, pos in enumerate(oracle_positions(texts, pats, pt, want)):
+        assert np.array_equal(allpos[poff[k]:poff[k + 1]], pos), k

@@ -52,8 +52,9 @@ struct BatchText {        // a text, or one group of <= kMaxSlots of its pattern
     uint32_t pend;        // ... and [pmid, pend) the candidate path
     uint32_t maxm;
     uint32_t mask_idx;    // 8-word mask of the candidate patterns' first symbols
-    uint32_t pad;
+    uint32_t codes;       // 0: byte compares; else 2-bit codes: bits b1 (0-7), b2 (8-15), bit 16 set
 };
+constexpr uint32_t kCoded = 1u << 16;
 
 struct BatchPat {
     uint32_t qc_off;      // first compare descriptor in the qc table
@@ -98,6 +99,7 @@ struct BatchArgs {
     const uint8_t* hit;         // write: 1 for the work items (tiles) where some pattern matches
     uint32_t stage_bytes, stages, one, nslots;
     uint32_t index_cap;         // entries of the per-tile position index (0: no index)
+    uint32_t packed_words;      // words of the packed-tile buffer (0: no entry uses 2-bit codes)
     uint32_t* status;
     uint64_t spin_ns;
 };
@@ -124,7 +126,9 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constan
     uint32_t* istart = icnt + 256;
     uint32_t* icur = icnt + 512;
     uint16_t* ilist = reinterpret_cast<uint16_t*>(icnt + 768);
-    uint8_t* bufs = after_slots + (A.index_cap ? ((3072u + 2u * A.index_cap + 127u) & ~127u) : 0u);
+    uint8_t* after_index = after_slots + (A.index_cap ? ((3072u + 2u * A.index_cap + 127u) & ~127u) : 0u);
+    uint32_t* pbuf = reinterpret_cast<uint32_t*>(after_index);   // 2-bit codes of the staged tile
+    uint8_t* bufs = after_index + ((4u * A.packed_words + 127u) & ~127u);
 
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t SB = A.stage_bytes, S = A.stages, one = A.one;
@@ -215,8 +219,59 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const __grid_constan
             const uint64_t s0 = d.k * kTile;
             const BatchText T = A.tx[d.x];
 
+            if (T.codes) {
+                // a text of at most four symbols: the tile as 2-bit codes
+                // (16 starts per word), built once for all its patterns,
+                // which are all dense and planned on codes
+                consumers_sync();   // the previous coded tile is no longer read
+                const uint32_t b1 = T.codes & 0xFFu, b2 = (T.codes >> 8) & 0xFFu;
+                const uint32_t units = SB / 16u;
+                if (b2 == b1 + 1)
+                    for (uint32_t u = tid; u < units; u += kConsumerWarps * 32) pbuf[u] = pack16<true>(b4[u], b1, b2, 0x01041040u);
+                else
+                    for (uint32_t u = tid; u < units; u += kConsumerWarps * 32) pbuf[u] = pack16<false>(b4[u], b1, b2, 0x01041040u);
+                consumers_sync();
+                const uint32_t* const pk[2] = {pbuf, pbuf};
+                uint32_t* const nobm[2] = {nullptr, nullptr};
+                const uint64_t no_out[2] = {0, 0};
+                for (uint32_t p = T.pbeg; p < T.pmid; ++p) {
+                    const BatchPat P = A.pats[p];
+                    const uint64_t nst = min(T.n - P.m + 1, T.slimit);
+                    if (s0 >= nst) continue;
+                    const GlobalQC qc{A.qc + P.qc_off, P.m};
+                    const uint64_t s0s[2] = {s0, 0};
+                    if constexpr (MODE == kBatchWrite) {
+                        const uint64_t o0 = __ldg(A.toff + P.tb + d.k);
+                        if (__ldg(A.toff + P.tb + d.k + 1) == o0) continue;   // the same for every warp
+                        uint32_t c = packed_tiles<false, true, 1>(pk, false, warp, lane, qc, P.m, P.r, P.ng, nst, s0s,
+                                                               no_out, nullptr, 0, nobm).x;
+                        c = warp_sum_u32(c);
+                        uint32_t* wc = wcnt + wpar * kConsumerWarps;
+                        wpar ^= 1u;
+                        if (lane == 0) wc[warp] = c;
+                        consumers_sync();
+                        const uint32_t before = warp_sum_u32(lane < warp ? wc[lane] : 0u);
+                        if (c) {
+                            const int64_t pb = __ldg(A.pos_off + P.out);
+                            const uint64_t cap = (uint64_t)(__ldg(A.pos_off + P.out + 1) - pb);
+                            const uint64_t outs[2] = {o0 + before, 0};
+                            (void)packed_tiles<true, false, 1>(pk, false, warp, lane, qc, P.m, P.r, P.ng, nst, s0s, outs,
+                                                            A.d_pos + pb, cap, nobm);
+                        }
+                        continue;
+                    }
+                    uint32_t c = packed_tiles<false, true, 1>(pk, false, warp, lane, qc, P.m, P.r, P.ng, nst, s0s, no_out,
+                                                           nullptr, 0, nobm).x;
+                    c = warp_sum_u32(c);
+                    if (lane == 0 && c) {
+                        atomicAdd(&slots[p - pbase], c);
+                        if (MODE == kBatchTileCount) atomicAdd(A.tcnt + P.tb + d.k, c);
+                    }
+                }
+            }
+
             // dense patterns: every warp scans its 2048 starts
-            for (uint32_t p = T.pbeg; p < T.pmid; ++p) {
+            for (uint32_t p = T.pbeg; p < (T.codes ? T.pbeg : T.pmid); ++p) {
                 const BatchPat P = A.pats[p];
                 const uint64_t nst = min(T.n - P.m + 1, T.slimit);   // the plan keeps only m <= n
                 if (s0 >= nst) continue;
@@ -476,7 +531,7 @@ struct PatDesc {
 };
 
 PatDesc describe(const uint8_t* p, uint32_t m, const uint64_t* h, uint64_t n, uint32_t delta, bool text7,
-                 uint32_t out, double cand_freq = smk::kCandidateFreq) {
+                 uint32_t out, double cand_freq = smk::kCandidateFreq, uint32_t codes = 0) {
     PatDesc d;
     d.zero = (uint64_t)m > n;
     for (uint32_t q = 0; q < m && !d.zero; ++q) d.zero = h[p[q]] == 0;
@@ -485,6 +540,23 @@ PatDesc describe(const uint8_t* p, uint32_t m, const uint64_t* h, uint64_t n, ui
     std::iota(pi.begin(), pi.end(), 0u);
     std::stable_sort(pi.begin(), pi.end(), [&](uint32_t a, uint32_t b) { return h[p[a]] < h[p[b]]; });
     std::vector<uint32_t> v(m);
+    if (codes) {
+        // a text of at most four symbols: compares on 2-bit codes, dense
+        const uint32_t b1 = codes & 0xFFu, b2 = (codes >> 8) & 0xFFu;
+        std::vector<double> freq(m);
+        for (uint32_t j = 0; j < m; ++j) {
+            const uint32_t c = p[pi[j]];
+            v[j] = ((pi[j] + delta) << 8) | ((c >> b1) & 1u) | (((c >> b2) & 1u) << 1);
+            freq[j] = (double)h[c] / (double)n;
+        }
+        d.qc.resize(m + smk::max_packed_groups_for(m));
+        uint32_t ng = 0;
+        const uint32_t r = smk::plan_packed(v.data(), m, freq.data(), 0, d.qc.data(), d.qc.data() + m,
+                                            smk::max_packed_groups_for(m), &ng, 2);
+        d.qc.resize(m + ng);
+        d.pat = BatchPat{0, m, r, ng, out, 0u};
+        return d;
+    }
     for (uint32_t j = 0; j < m; ++j) v[j] = ((pi[j] + delta) << 8) | p[pi[j]];
     if ((double)h[p[pi[0]]] / (double)n < cand_freq) {
         d.cand = true;
@@ -513,6 +585,7 @@ struct Tables {
     uint64_t items = 0;
     uint32_t nslots = 1, maxm = 1;
     bool need_index = false;
+    bool need_pack = false;   // some entry compares 2-bit codes
     uint32_t slot_hint() const { return (uint32_t)std::min<size_t>(pats.size(), kMaxSlots); }
 };
 
@@ -524,10 +597,10 @@ struct Tables {
 // item.
 void add_text(Tables& T, uint64_t off, uint64_t n, uint64_t slimit, const std::vector<const PatDesc*>& ds,
               bool allow_cand = true, const std::vector<uint64_t>* tb = nullptr,
-              std::vector<PatTiles>* pt = nullptr, uint32_t cand_min = smk::kCandidateMin) {
+              std::vector<PatTiles>* pt = nullptr, uint32_t cand_min = smk::kCandidateMin, uint32_t codes = 0) {
     uint32_t ncand = 0;
     for (const PatDesc* d : ds) ncand += (!d->zero && d->cand) ? 1u : 0u;
-    const bool use_cand = allow_cand && ncand >= cand_min;
+    const bool use_cand = allow_cand && !codes && ncand >= cand_min;
     std::vector<const PatDesc*> order;
     for (const PatDesc* d : ds)
         if (!d->zero && !(use_cand && d->cand)) order.push_back(d);
@@ -536,7 +609,8 @@ void add_text(Tables& T, uint64_t off, uint64_t n, uint64_t slimit, const std::v
         if (!d->zero && use_cand && d->cand) order.push_back(d);
     for (size_t g0 = 0; g0 < order.size(); g0 += kMaxSlots) {
         const size_t g1 = std::min(order.size(), g0 + kMaxSlots);
-        BatchText e{off, n, 0, slimit, (uint32_t)T.pats.size(), 0, 0, 0, 0, 0};
+        BatchText e{off, n, 0, slimit, (uint32_t)T.pats.size(), 0, 0, 0, 0, codes};
+        T.need_pack |= codes != 0;
         uint32_t mask[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         bool any_cand = false;
         uint32_t mn = ~0u;
@@ -606,11 +680,13 @@ void finish(Tables& T, uint64_t want_ctas) {
 }
 
 struct Geometry {
-    uint32_t SB = 0, stages = 2, index_cap = 0;
+    uint32_t SB = 0, stages = 2, index_cap = 0, packed_words = 0;
     int occ = 1;
     size_t smem(uint32_t nslots) const {
         const size_t ib = index_cap ? ((3072u + 2u * index_cap + 127u) & ~127u) : 0u;
-        return (size_t)smk::kScanHeader + smk::kQueueBytes + ((nslots * 4u + 127u) & ~127u) + ib + (size_t)SB * stages;
+        const size_t pb = (4u * packed_words + 127u) & ~127u;
+        return (size_t)smk::kScanHeader + smk::kQueueBytes + ((nslots * 4u + 127u) & ~127u) + ib + pb +
+               (size_t)SB * stages;
     }
 };
 
@@ -618,10 +694,11 @@ struct Geometry {
 // <= maxm and whose CTAs count at most nslots patterns each: the stage
 // count is lowered while that lets more CTAs reside on an SM.
 Geometry geometry(sm_ctx* ctx, uint32_t maxm, bool need_index, uint32_t nslots = kMaxSlots,
-                  uint32_t stages = 0) {
+                  uint32_t stages = 0, bool need_pack = false) {
     Geometry g;
     g.SB = smk::stage_bytes_for(maxm);
     g.index_cap = need_index ? g.SB : 0u;
+    g.packed_words = need_pack ? smk::packed_words_for(g.SB) : 0u;
     g.stages = stages ? stages : sm_ctx_stages(ctx);
     nslots = std::max(1u, std::min(nslots, kMaxSlots));
     while (g.stages > 2 && g.smem(nslots) > sm_ctx_max_smem(ctx)) --g.stages;
@@ -692,6 +769,7 @@ BatchArgs args_for(sm_ctx* ctx, const uint8_t* d_texts, const Tables& T, const L
     a.one = 1;
     a.nslots = T.nslots;
     a.index_cap = g.index_cap;
+    a.packed_words = g.packed_words;
     a.status = sm_ctx_status(ctx);
     a.spin_ns = sm_ctx_spin_ns(ctx);
     return a;
@@ -701,6 +779,13 @@ bool text_is_7bit(const uint64_t* h) {
     for (int c = 0x80; c < 256; ++c)
         if (h[c]) return false;
     return true;
+}
+
+// BatchText::codes of a text with histogram h: 2-bit codes when it has at
+// most four symbols, else 0 (byte compares).
+uint32_t text_codes(const uint64_t* h) {
+    uint32_t b1 = 0, b2 = 0;
+    return smk::packed_code_bits(h, &b1, &b2) ? (b1 | (b2 << 8) | smk::kCoded) : 0u;
 }
 
 cudaError_t launch_batch(int mode, uint32_t grid, size_t smem, cudaStream_t st, const BatchArgs& a) {
@@ -848,7 +933,8 @@ sm_status build_plan(sm_batch* b) {
         const uint32_t delta = (uint32_t)((reinterpret_cast<uintptr_t>(b->d_texts) + (uint64_t)h_text_off[x]) & 15u);
         ms[k] = (uint32_t)(b->pat_off[k + 1] - b->pat_off[k]);
         lens[k] = n;
-        descs[k] = describe(b->pats.data() + b->pat_off[k], ms[k], h, n, delta, text_is_7bit(h), k, P.cand_freq);
+        descs[k] = describe(b->pats.data() + b->pat_off[k], ms[k], h, n, delta, text_is_7bit(h), k, P.cand_freq,
+                            text_codes(h));
     }
     std::vector<PatTiles> pt;
     std::vector<uint64_t> tb;
@@ -863,12 +949,13 @@ sm_status build_plan(sm_batch* b) {
         std::vector<const PatDesc*> ptrs;
         for (; kk < npats && (uint32_t)b->pat_text[by_text[kk]] == x; ++kk) ptrs.push_back(&descs[by_text[kk]]);
         const uint64_t n = (uint64_t)(h_text_off[x + 1] - h_text_off[x]);
-        add_text(T, (uint64_t)h_text_off[x], n, ~0ull, ptrs, true, &tb, nullptr, P.cand_min);
-        add_text(W, (uint64_t)h_text_off[x], n, ~0ull, ptrs, false, &tb, &pt);
+        const uint32_t codes = text_codes(&b->hist[(size_t)x * 256]);
+        add_text(T, (uint64_t)h_text_off[x], n, ~0ull, ptrs, true, &tb, nullptr, P.cand_min, codes);
+        add_text(W, (uint64_t)h_text_off[x], n, ~0ull, ptrs, false, &tb, &pt, P.cand_min, codes);
     }
-    const Geometry g = geometry(ctx, T.maxm, T.need_index, T.slot_hint(), P.stages);
+    const Geometry g = geometry(ctx, T.maxm, T.need_index, T.slot_hint(), P.stages, T.need_pack);
     finish(T, (uint64_t)sm_ctx_num_sms(ctx) * g.occ);
-    const Geometry gw = geometry(ctx, W.maxm, false, W.slot_hint(), P.stages);
+    const Geometry gw = geometry(ctx, W.maxm, false, W.slot_hint(), P.stages, W.need_pack);
     finish(W, (uint64_t)sm_ctx_num_sms(ctx) * gw.occ);
 
     // one allocation for each pass's tables (the write pass's also holds the
@@ -1131,7 +1218,8 @@ struct sm_stepper {
     std::vector<std::vector<uint64_t>> class_hist;
     std::vector<uint64_t> class_n;
     std::vector<bool> class_text7;
-    Geometry geo[2];   // steps without and with the candidate index (any active set)
+    std::vector<uint32_t> class_codes;   // BatchText::codes of the class (2-bit codes or bytes)
+    Geometry geo[2][2];   // steps [with the candidate index][with 2-bit codes] (any active set)
     std::unordered_map<uint32_t, std::vector<PatDesc>> queries;   // one per class
     struct Buf {
         char* d = nullptr;
@@ -1222,10 +1310,13 @@ extern "C" sm_status sm_stepper_create(sm_ctx* ctx, const uint8_t* d_text, uint6
             s->class_n[k] += (uint64_t)(off[c + 1] - off[c]);
             s->chunk_class.push_back(k);
         }
-        for (auto& h : s->class_hist) s->class_text7.push_back(text_is_7bit(h.data()));
+        for (auto& h : s->class_hist) {
+            s->class_text7.push_back(text_is_7bit(h.data()));
+            s->class_codes.push_back(text_codes(h.data()));
+        }
     }
-    s->geo[0] = geometry(ctx, max_m, false);
-    s->geo[1] = geometry(ctx, max_m, true);
+    for (int ix = 0; ix < 2; ++ix)
+        for (int pk = 0; pk < 2; ++pk) s->geo[ix][pk] = geometry(ctx, max_m, ix == 1, kMaxSlots, 0, pk == 1);
     for (auto* b : {&s->buf[0], &s->buf[1], &s->rbuf})
         if (cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
@@ -1245,7 +1336,8 @@ extern "C" sm_status sm_stepper_admit(sm_stepper* s, uint32_t qid, const uint8_t
     std::vector<PatDesc>& d = s->queries[qid];
     d.clear();
     for (size_t k = 0; k < s->class_hist.size(); ++k)
-        d.push_back(describe(h_pat, m, s->class_hist[k].data(), s->class_n[k], s->delta, s->class_text7[k], qid));
+        d.push_back(describe(h_pat, m, s->class_hist[k].data(), s->class_n[k], s->delta, s->class_text7[k], qid,
+                             smk::kCandidateFreq, s->class_codes[k]));
     return SM_OK;
 }
 
@@ -1276,8 +1368,9 @@ extern "C" sm_status sm_stepper_step(sm_stepper* s, const uint32_t* h_qids, uint
     }
     if (ds.empty()) return SM_OK;
     Tables T;
-    add_text(T, off, nbytes, slimit, ds);
-    const Geometry& geo = s->geo[T.need_index ? 1 : 0];
+    add_text(T, off, nbytes, slimit, ds, true, nullptr, nullptr, smk::kCandidateMin,
+             s->class_codes[s->chunk_class[chunk]]);
+    const Geometry& geo = s->geo[T.need_index ? 1 : 0][T.need_pack ? 1 : 0];
     finish(T, (uint64_t)sm_ctx_num_sms(s->ctx) * geo.occ);
     const Layout L = layout_of(T);
     sm_stepper::Buf& b = s->buf[s->cur];
@@ -1317,18 +1410,20 @@ extern "C" sm_status sm_stepper_report(sm_stepper* s, const uint8_t* h_pats, con
     std::vector<uint64_t> lens(nq, s->n);
     for (uint32_t k = 0; k < nq; ++k) {
         ms[k] = (uint32_t)(h_pat_off[k + 1] - h_pat_off[k]);
-        descs[k] = describe(h_pats + h_pat_off[k], ms[k], s->hist, s->n, s->delta, s->text7, k);
+        descs[k] = describe(h_pats + h_pat_off[k], ms[k], s->hist, s->n, s->delta, s->text7, k,
+                            smk::kCandidateFreq, text_codes(s->hist));
         ptrs[k] = &descs[k];
     }
     std::vector<PatTiles> pt;
     std::vector<uint64_t> tb;
     const uint64_t ntb = assign_tiles(ms, lens, pt, tb);
     Tables T, W;
-    add_text(T, 0, s->n, ~0ull, ptrs, true, &tb);
-    add_text(W, 0, s->n, ~0ull, ptrs, false, &tb, &pt);
-    const Geometry g1 = geometry(s->ctx, std::max(T.maxm, 1u), T.need_index, T.slot_hint());
+    const uint32_t codes = text_codes(s->hist);
+    add_text(T, 0, s->n, ~0ull, ptrs, true, &tb, nullptr, smk::kCandidateMin, codes);
+    add_text(W, 0, s->n, ~0ull, ptrs, false, &tb, &pt, smk::kCandidateMin, codes);
+    const Geometry g1 = geometry(s->ctx, std::max(T.maxm, 1u), T.need_index, T.slot_hint(), 0, T.need_pack);
     finish(T, (uint64_t)sm_ctx_num_sms(s->ctx) * g1.occ);
-    const Geometry g2 = geometry(s->ctx, std::max(W.maxm, 1u), false, W.slot_hint());
+    const Geometry g2 = geometry(s->ctx, std::max(W.maxm, 1u), false, W.slot_hint(), 0, W.need_pack);
     finish(W, (uint64_t)sm_ctx_num_sms(s->ctx) * g2.occ);
     const Layout L = layout_of(T), LW = layout_of(W);
     const size_t o_w = L.total, o_pt = o_w + LW.total, o_po = o_pt + ((pt.size() * sizeof(PatTiles) + 255) & ~(size_t)255);

@@ -558,13 +558,13 @@ __device__ __forceinline__ uint32_t pack16(const uint4& x, uint32_t b1, uint32_t
 // tile t. v = (e << 8) | code with e = text misalignment + pattern position;
 // the caller guarantees E' == e >> 6 and D == (e >> 4) & 3. ALIGNED:
 // e mod 16 == 0 (no shift).
-template <int D, bool ALIGNED>
+template <int D, bool ALIGNED, int NT = 2>
 __device__ __forceinline__ void acc_packed(const uint4 (&a)[2], const uint4 (&b)[2], uint32_t v,
                                            uint32_t (&y)[2][4]) {
     const uint32_t P = (v & 3u) * 0x55555555u;
     const uint32_t sh = ((v >> 8) & 15u) << 1;
 #pragma unroll
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < NT; ++t) {
         const uint32_t X[8] = {a[t].x, a[t].y, a[t].z, a[t].w, b[t].x, b[t].y, b[t].z, b[t].w};
 #pragma unroll
         for (int i = 0; i < 4; ++i)
@@ -602,8 +602,8 @@ __device__ __forceinline__ uint32_t valid_fields(int64_t lim) {
 // with WRITE also writes tile t's positions in ascending order from rank
 // out[t] (first `cap` only). bm[t] (tile-count pass of a report): when the
 // warp-tile of tile t has matches, its found bitmap (64 words, start order)
-// is stored there.
-template <bool WRITE, bool DIRECT, class QC>
+// is stored there. NT = 1 takes tile 0 only (pk[1] is not read).
+template <bool WRITE, bool DIRECT, int NT = 2, class QC>
 __device__ __forceinline__ uint2 packed_tiles(const uint32_t* const (&pk)[2], bool two, uint32_t warp,
                                               uint32_t lane, QC qc, uint32_t m, uint32_t r, uint32_t ng,
                                               uint64_t nstarts, const uint64_t (&s0)[2], const uint64_t (&out)[2],
@@ -616,23 +616,23 @@ __device__ __forceinline__ uint2 packed_tiles(const uint32_t* const (&pk)[2], bo
         const uint32_t u = (w0 >> 2) + (gd & 0x1FFu);
         uint4 a[2], b[2];
 #pragma unroll
-        for (int t = 0; t < 2; ++t) {
+        for (int t = 0; t < NT; ++t) {
             const uint4* p4 = reinterpret_cast<const uint4*>(pk[t]);
             a[t] = p4[u];
             b[t] = p4[u + 1];
         }
-        if (gd & (1u << 9)) acc_packed<0, true>(a, b, qc(j++), y);
-        if (gd & (1u << 10)) acc_packed<1, true>(a, b, qc(j++), y);
-        if (gd & (1u << 11)) acc_packed<2, true>(a, b, qc(j++), y);
-        if (gd & (1u << 12)) acc_packed<3, true>(a, b, qc(j++), y);
-        for (uint32_t k = (gd >> 13) & 15u; k; --k) acc_packed<0, false>(a, b, qc(j++), y);
-        for (uint32_t k = (gd >> 17) & 15u; k; --k) acc_packed<1, false>(a, b, qc(j++), y);
-        for (uint32_t k = (gd >> 21) & 15u; k; --k) acc_packed<2, false>(a, b, qc(j++), y);
-        for (uint32_t k = (gd >> 25) & 15u; k; --k) acc_packed<3, false>(a, b, qc(j++), y);
+        if (gd & (1u << 9)) acc_packed<0, true, NT>(a, b, qc(j++), y);
+        if (gd & (1u << 10)) acc_packed<1, true, NT>(a, b, qc(j++), y);
+        if (gd & (1u << 11)) acc_packed<2, true, NT>(a, b, qc(j++), y);
+        if (gd & (1u << 12)) acc_packed<3, true, NT>(a, b, qc(j++), y);
+        for (uint32_t k = (gd >> 13) & 15u; k; --k) acc_packed<0, false, NT>(a, b, qc(j++), y);
+        for (uint32_t k = (gd >> 17) & 15u; k; --k) acc_packed<1, false, NT>(a, b, qc(j++), y);
+        for (uint32_t k = (gd >> 21) & 15u; k; --k) acc_packed<2, false, NT>(a, b, qc(j++), y);
+        for (uint32_t k = (gd >> 25) & 15u; k; --k) acc_packed<3, false, NT>(a, b, qc(j++), y);
     }
-    uint32_t f[2][4];
+    uint32_t f[2][4] = {{0u, 0u, 0u, 0u}, {0u, 0u, 0u, 0u}};
 #pragma unroll
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < NT; ++t) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) f[t][i] = (t == 0 || two) ? zero_fields(y[t][i]) : 0u;
         if (s0[t] + kTile > nstarts) {   // last tile: clear starts beyond n - m
@@ -644,7 +644,7 @@ __device__ __forceinline__ uint2 packed_tiles(const uint32_t* const (&pk)[2], bo
     // surviving starts continue one compare at a time; rare when r is planned
     uint32_t any = 0;
 #pragma unroll
-    for (int t = 0; t < 2; ++t) any |= (f[t][0] | f[t][1]) | (f[t][2] | f[t][3]);
+    for (int t = 0; t < NT; ++t) any |= (f[t][0] | f[t][1]) | (f[t][2] | f[t][3]);
     if (!(DIRECT && r >= m) && __any_sync(kFull, any != 0u)) {
         const uint32_t jl = min(m, r + kLaneCompares);
         for (uint32_t j = r; j < jl && any; ++j) {
@@ -654,7 +654,7 @@ __device__ __forceinline__ uint2 packed_tiles(const uint32_t* const (&pk)[2], bo
             const uint32_t sh = (e & 15u) << 1;
             any = 0;
 #pragma unroll
-            for (int t = 0; t < 2; ++t)
+            for (int t = 0; t < NT; ++t)
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     if (f[t][i]) {
@@ -667,7 +667,7 @@ __device__ __forceinline__ uint2 packed_tiles(const uint32_t* const (&pk)[2], bo
         // words still alive: the whole warp takes the remaining compares of
         // one word at a time (lane l every 32nd from jl + l) and ANDs
 #pragma unroll
-        for (int t = 0; t < 2; ++t)
+        for (int t = 0; t < NT; ++t)
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 uint32_t pend = __ballot_sync(kFull, jl < m && f[t][i] != 0u);
@@ -689,11 +689,11 @@ __device__ __forceinline__ uint2 packed_tiles(const uint32_t* const (&pk)[2], bo
                 }
             }
     }
-    uint32_t n[2];
+    uint32_t n[2] = {0u, 0u};
 #pragma unroll
-    for (int t = 0; t < 2; ++t) n[t] = __popc(f[t][0] | (f[t][1] << 1)) + __popc(f[t][2] | (f[t][3] << 1));
+    for (int t = 0; t < NT; ++t) n[t] = __popc(f[t][0] | (f[t][1] << 1)) + __popc(f[t][2] | (f[t][3] << 1));
 #pragma unroll
-    for (int t = 0; t < 2; ++t)
+    for (int t = 0; t < NT; ++t)
         if (bm[t] && warp_sum_u32(n[t])) {
             // the warp-tile's found bitmap in start order: lane l's 64 starts
             // are words 2l, 2l + 1 (found bit 2k of a packed word -> bit k)
@@ -705,7 +705,7 @@ __device__ __forceinline__ uint2 packed_tiles(const uint32_t* const (&pk)[2], bo
     if (WRITE) {
         // positions in order: lanes, then words, then starts
 #pragma unroll
-        for (int t = 0; t < 2; ++t) {
+        for (int t = 0; t < NT; ++t) {
             const uint32_t inc = warp_incl_scan(n[t], lane);
             uint64_t rk = out[t] + inc - n[t];
             const uint64_t pos0 = s0[t] + warp * kWarpStarts + 64u * lane;

@@ -206,9 +206,9 @@ sm_status sm_report_ex(sm_ctx* ctx, const uint8_t* d_text, uint64_t n,
  *
  * sm_batch_create plans the batch (synchronous on `stream`, allocates device
  * tables): per-text byte histograms, each pattern's rarest-first order under
- * its own text's frequencies (Sec. 2.2) and peel factor (Sec. 2.3); patterns
- * with a symbol that never occurs in their text, or longer than it, are not
- * scanned (count 0). The plan keeps d_texts and reads it at every count.
+ * its own text's frequencies (Sec. 2.2) and peel factor (Sec. 2.3), 2-bit
+ * codes for texts of at most four symbols; patterns with a symbol that
+ * never occurs in their text, or longer than it, are not scanned (count 0). The plan keeps d_texts and reads it at every count.
  * sm_batch_count enqueues one memset and one persistent kernel that writes
  * d_counts[k] (int64, npats entries) for every pattern; it allocates nothing
  * and may be captured in a CUDA graph. sm_batch_destroy waits for the device

@@ -283,6 +283,10 @@ sm_status sm_count_batch(sm_ctx* ctx, const uint8_t* d_texts, const int64_t* d_t
  *                      the caller zeroes a counter before its first step).
  *                      Asynchronous on `stream`; allocates nothing once its
  *                      two table buffers have grown to the batch size.
+ *   sm_stepper_steps   the same for several chunks in one launch: query
+ *                      h_qids[i] is scanned on chunks chunk, chunk + 1, ...
+ *                      (wrapping) for h_nchunks[i] of them (all queries: 1
+ *                      when h_nchunks is NULL; at most the chunk count).
  *   sm_stepper_retire  forget qid.
  *   sm_stepper_report  report nq patterns (h_pats / h_pat_off packed as for
  *                      sm_batch_create) over the whole text in one batched
@@ -301,6 +305,8 @@ uint32_t sm_stepper_chunks(const sm_stepper* stepper);
 sm_status sm_stepper_admit(sm_stepper* stepper, uint32_t qid, const uint8_t* h_pat, uint32_t m);
 sm_status sm_stepper_step(sm_stepper* stepper, const uint32_t* h_qids, uint32_t nq, uint32_t chunk,
                           int64_t* d_counts, sm_stream_t stream);
+sm_status sm_stepper_steps(sm_stepper* stepper, const uint32_t* h_qids, const uint32_t* h_nchunks, uint32_t nq,
+                           uint32_t chunk, int64_t* d_counts, sm_stream_t stream);
 sm_status sm_stepper_retire(sm_stepper* stepper, uint32_t qid);
 sm_status sm_stepper_report(sm_stepper* stepper, const uint8_t* h_pats, const int64_t* h_pat_off, uint32_t nq,
                             const int64_t* h_pos_off, uint64_t* d_pos, int64_t* d_counts, sm_stream_t stream);

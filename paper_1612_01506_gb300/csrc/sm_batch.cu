@@ -1347,29 +1347,46 @@ extern "C" sm_status sm_stepper_retire(sm_stepper* s, uint32_t qid) {
     return SM_OK;
 }
 
-extern "C" sm_status sm_stepper_step(sm_stepper* s, const uint32_t* h_qids, uint32_t nq, uint32_t chunk,
-                                     int64_t* d_counts, sm_stream_t stream) {
+extern "C" sm_status sm_stepper_steps(sm_stepper* s, const uint32_t* h_qids, const uint32_t* h_nchunks, uint32_t nq,
+                                      uint32_t chunk, int64_t* d_counts, sm_stream_t stream) {
     if (!s || (nq && (!h_qids || !d_counts))) return sm_fail_internal(SM_EINVAL, "NULL argument");
     if (chunk >= s->nchunks) return sm_fail_internal(SM_EINVAL, "chunk out of range");
     Guard g(s->device);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const uint64_t off = (uint64_t)chunk * s->chunk;
-    const uint64_t avail = s->n - off;                          // bytes from the chunk start
-    const uint64_t nbytes = std::min<uint64_t>(avail, s->chunk + s->max_m - 1);
-    const uint64_t slimit = std::min<uint64_t>(avail, s->chunk);
-    std::vector<const PatDesc*> ds;
-    ds.reserve(nq);
+    std::vector<const std::vector<PatDesc>*> qd(nq);
+    uint32_t span = nq ? 1u : 0u;   // chunks scanned: the most any query asks for
     for (uint32_t i = 0; i < nq; ++i) {
         auto it = s->queries.find(h_qids[i]);
         if (it == s->queries.end()) return sm_fail_internal(SM_EINVAL, "query not admitted");
-        const PatDesc& d = it->second[s->chunk_class[chunk]];
-        if (d.zero || d.pat.m > nbytes) continue;   // a symbol absent from the chunk, or no start in it
-        ds.push_back(&d);
+        qd[i] = &it->second;
+        if (h_nchunks) {
+            if (h_nchunks[i] > s->nchunks) return sm_fail_internal(SM_EINVAL, "more chunks than the text has");
+            span = std::max(span, h_nchunks[i]);
+        }
     }
-    if (ds.empty()) return SM_OK;
+    // one entry per chunk (chunk, chunk + 1, ... wrapping), each with the
+    // queries that still want it, described for the chunk's class
     Tables T;
-    add_text(T, off, nbytes, slimit, ds, true, nullptr, nullptr, smk::kCandidateMin,
-             s->class_codes[s->chunk_class[chunk]]);
+    std::vector<const PatDesc*> ds;
+    ds.reserve(nq);
+    for (uint32_t k = 0; k < span; ++k) {
+        const uint32_t c = (chunk + k) % s->nchunks;
+        const uint64_t off = (uint64_t)c * s->chunk;
+        const uint64_t avail = s->n - off;                          // bytes from the chunk start
+        const uint64_t nbytes = std::min<uint64_t>(avail, s->chunk + s->max_m - 1);
+        const uint64_t slimit = std::min<uint64_t>(avail, s->chunk);
+        ds.clear();
+        for (uint32_t i = 0; i < nq; ++i) {
+            if (h_nchunks && h_nchunks[i] <= k) continue;
+            const PatDesc& d = (*qd[i])[s->chunk_class[c]];
+            if (d.zero || d.pat.m > nbytes) continue;   // a symbol absent from the chunk, or no start in it
+            ds.push_back(&d);
+        }
+        if (!ds.empty())
+            add_text(T, off, nbytes, slimit, ds, true, nullptr, nullptr, smk::kCandidateMin,
+                     s->class_codes[s->chunk_class[c]]);
+    }
+    if (T.tx.empty()) return SM_OK;
     const Geometry& geo = s->geo[T.need_index ? 1 : 0][T.need_pack ? 1 : 0];
     finish(T, (uint64_t)sm_ctx_num_sms(s->ctx) * geo.occ);
     const Layout L = layout_of(T);
@@ -1387,6 +1404,11 @@ extern "C" sm_status sm_stepper_step(sm_stepper* s, const uint32_t* h_qids, uint
     if (e == cudaSuccess) e = cudaEventRecord(b.ev, st);
     b.used = true;
     return e == cudaSuccess ? SM_OK : sm_fail_internal(SM_ECUDA, cudaGetErrorString(e));
+}
+
+extern "C" sm_status sm_stepper_step(sm_stepper* s, const uint32_t* h_qids, uint32_t nq, uint32_t chunk,
+                                     int64_t* d_counts, sm_stream_t stream) {
+    return sm_stepper_steps(s, h_qids, nullptr, nq, chunk, d_counts, stream);
 }
 
 extern "C" sm_status sm_stepper_report(sm_stepper* s, const uint8_t* h_pats, const int64_t* h_pat_off, uint32_t nq,

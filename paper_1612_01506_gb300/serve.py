@@ -56,6 +56,8 @@ def _bind_stepper():
     lib.sm_stepper_admit.restype = st
     lib.sm_stepper_step.argtypes = [vp, u32p, C.c_uint32, C.c_uint32, vp, vp]
     lib.sm_stepper_step.restype = st
+    lib.sm_stepper_steps.argtypes = [vp, u32p, u32p, C.c_uint32, C.c_uint32, vp, vp]
+    lib.sm_stepper_steps.restype = st
     lib.sm_stepper_retire.argtypes = [vp, C.c_uint32]
     lib.sm_stepper_retire.restype = st
     i64p = C.POINTER(C.c_int64)
@@ -146,23 +148,32 @@ class Server:
             with torch.cuda.stream(self.stream):
                 self.counters[slot].zero_()
             self.active[slot] = [q, self.nchunks]
-        burst = self.nchunks if len(self.active) <= self.burst_below and not self.pending else 1
-        for _ in range(burst):
-            if not self.active:
-                break
+        if self.active and len(self.active) <= self.burst_below and not self.pending:
+            self._step_chunk(burst=True)   # every active query to its end, one launch
+        elif self.active:
             self._step_chunk()
         self._poll()
 
-    def _step_chunk(self):
+    def _step_chunk(self, burst: bool = False):
+        """One step on the next chunk for every active query; with burst, each
+        active query over all the chunks it still needs, in one launch."""
         torch = self.torch
         slots = np.fromiter(self.active.keys(), dtype=np.uint32, count=len(self.active))
-        sm._check(self.lib.sm_stepper_step(self.stepper, slots.ctypes.data_as(C.POINTER(C.c_uint32)),
-                                           slots.size, self.next_chunk, self.counters.data_ptr(),
-                                           self.stream.cuda_stream))
+        if burst:
+            left = np.array([self.active[int(q)][1] for q in slots], dtype=np.uint32)
+            sm._check(self.lib.sm_stepper_steps(self.stepper, slots.ctypes.data_as(C.POINTER(C.c_uint32)),
+                                                left.ctypes.data_as(C.POINTER(C.c_uint32)), slots.size,
+                                                self.next_chunk, self.counters.data_ptr(), self.stream.cuda_stream))
+            done_chunks = int(left.max())
+        else:
+            sm._check(self.lib.sm_stepper_step(self.stepper, slots.ctypes.data_as(C.POINTER(C.c_uint32)),
+                                               slots.size, self.next_chunk, self.counters.data_ptr(),
+                                               self.stream.cuda_stream))
+            done_chunks = 1
         finished = []
         for slot in list(self.active):
             ent = self.active[slot]
-            ent[1] -= 1
+            ent[1] -= min(ent[1], done_chunks)
             if ent[1] == 0:
                 finished.append(ent[0])
                 del self.active[slot]
@@ -176,7 +187,7 @@ class Server:
             ev = torch.cuda.Event()
             ev.record(self.stream)
             self.finishing.append((ev, finished, host))
-        self.next_chunk = (self.next_chunk + 1) % self.nchunks
+        self.next_chunk = (self.next_chunk + done_chunks) % self.nchunks
         self.steps += 1
 
     def warm_up(self, patterns: list[bytes]):

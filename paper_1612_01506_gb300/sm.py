@@ -27,7 +27,7 @@ EXPORTS = ("sm_create", "sm_destroy", "sm_last_error", "sm_status_string", "sm_s
            "sm_histogram", "sm_order", "sm_order_fixed", "sm_count", "sm_count_ex", "sm_report",
            "sm_report_ex", "sm_report_noalloc", "sm_batch_create", "sm_batch_count", "sm_batch_report",
            "sm_batch_tune", "sm_batch_destroy", "sm_count_batch", "sm_stepper_create", "sm_stepper_chunks", "sm_stepper_admit",
-           "sm_stepper_step", "sm_stepper_retire", "sm_stepper_report", "sm_stepper_destroy")
+           "sm_stepper_step", "sm_stepper_steps", "sm_stepper_retire", "sm_stepper_report", "sm_stepper_destroy")
 
 
 class SmError(RuntimeError):

@@ -41,8 +41,8 @@ inline bool aligned(uint32_t v) { return ((v >> 8) & 3u) == 0; }
 // Modelled time of one 2048-start warp-tile, in consumer-warp cycles measured
 // per phase on GB300 (3 CTAs of 8 consumer warps per SM).
 struct PlanCosts {
-    double base = 550, window = 550, cmp_aligned = 190, cmp_shifted = 375;
-    double zero_test = 380, compact = 480, compact_per_chunk = 10;
+    double base = 550, window = 550, cmp_aligned = 190, cmp_shifted = 450;
+    double zero_test = 120, compact = 480, compact_per_chunk = 10;
     double round = 350, iter = 450, iter_per_lane = 15;
 };
 

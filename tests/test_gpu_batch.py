@@ -220,3 +220,38 @@ def test_batch_tune_keeps_results(torch, ctx):
     allpos = dpos.cpu().numpy().view(np.uint64)
     for k, pos in enumerate(oracle_positions(texts, pats, pt, want)):
         assert np.array_equal(allpos[poff[k]:poff[k + 1]], pos), k
+
+
+def test_batch_coded_texts_long_patterns(torch, ctx):
+    # texts of <= 4 symbols run on 2-bit codes in the batch kernel: long
+    # patterns (up to the 4096 limit), tile and halo edges, a text with
+    # three symbols and one with two, counts and ordered positions
+    t4 = synth.uniform(6 * 16384 + 77, 4, seed=0, stream=41)
+    t3 = np.frombuffer(b"xyz", np.uint8)[np.random.default_rng(42).integers(0, 3, 3 * 16384 + 5)].copy()
+    t2 = synth.uniform(2 * 16384 + 9, 2, seed=0, stream=43)
+    texts = [t4, t3, t2]
+    r = np.random.default_rng(44)
+    pats, pt = [], []
+    for x, t in enumerate(texts):
+        for m in (1, 3, 17, 64, 65, 300, 1500, 4096):
+            for s0 in (0, 16384 - m // 2, t.size - m):
+                if 0 <= s0 <= t.size - m:
+                    pats.append(t[s0:s0 + m].tobytes())
+                    pt.append(x)
+        pats.append(b"ACGN")   # a symbol absent from every text
+        pt.append(x)
+    off = np.zeros(4, np.int64)
+    off[1:] = np.cumsum([t.size for t in texts])
+    want = expected(texts, pats, pt)
+    d = to_dev(torch, np.concatenate(texts), 7)
+    b = sm.sm_batch_create(ctx, d, off, pats, np.array(pt, np.int32))
+    sm.sm_sync(ctx)
+    assert np.array_equal(sm.sm_batch_count(b).cpu().numpy()[: len(pats)], want)
+    poff = np.zeros(len(pats) + 1, np.int64)
+    poff[1:] = np.cumsum(want)
+    counts, dpos = sm.sm_batch_report(b, torch.from_numpy(poff).cuda())
+    assert sm.sm_sync(ctx) == sm.SM_OK
+    assert np.array_equal(counts.cpu().numpy()[: len(pats)], want)
+    allpos = dpos.cpu().numpy().view(np.uint64)
+    for k, pos in enumerate(oracle_positions(texts, pats, pt, want)):
+        assert np.array_equal(allpos[poff[k]:poff[k + 1]], pos), (k, len(pats[k]), pt[k])

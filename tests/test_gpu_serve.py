@@ -142,3 +142,44 @@ def test_stepper_patterns_across_chunk_classes(torch):
     q = qs[-1]
     pos, _ = oracle.report_threads(q.pattern, t, q.count)
     assert np.array_equal(q.positions.cpu().numpy().view(np.uint64), pos)
+
+
+def test_stepper_steps_chunk_ranges(torch):
+    # sm_stepper_steps: each query scanned on its own number of chunks from a
+    # start chunk, wrapping around the text, in one launch; the counts equal
+    # the oracle's over exactly those chunks
+    import ctypes as C
+    from paper_1612_01506_gb300.serve import Server
+    t = make_text(1 << 20)
+    text = torch.from_numpy(t).cuda()
+    chunk = 1 << 18
+    server = Server(text, chunk_bytes=chunk, max_m=512, max_active=8)
+    nch = server.nchunks
+    r = np.random.default_rng(9)
+    pats = []
+    for m in (2, 5, 40, 512):
+        s0 = int(r.integers(0, t.size - m + 1))
+        pats.append(t[s0:s0 + m].tobytes())
+    for first in (0, nch - 3):
+        spans = [nch, 1, 3, nch - 1][: len(pats)]
+        counters = torch.zeros(len(pats), dtype=torch.int64, device="cuda")
+        for q, p in enumerate(pats):
+            a = np.frombuffer(p, np.uint8)
+            assert server.lib.sm_stepper_admit(server.stepper, q, a.ctypes.data_as(C.POINTER(C.c_uint8)), a.size) == 0
+        qids = np.arange(len(pats), dtype=np.uint32)
+        left = np.array(spans, dtype=np.uint32)
+        assert server.lib.sm_stepper_steps(server.stepper, qids.ctypes.data_as(C.POINTER(C.c_uint32)),
+                                           left.ctypes.data_as(C.POINTER(C.c_uint32)), len(pats), first,
+                                           counters.data_ptr(), server.stream.cuda_stream) == 0
+        server.stream.synchronize()
+        got = counters.cpu().numpy()
+        for q, p in enumerate(pats):
+            want = 0
+            for k in range(spans[q]):
+                c = (first + k) % nch
+                lo, hi = c * chunk, min((c + 1) * chunk, t.size)          # starts counted in chunk c
+                seg = t[lo:min(hi + len(p) - 1, t.size)]
+                want += oracle.count_threads(p, seg) if seg.size >= len(p) else 0
+            assert got[q] == want, (q, first, spans[q])
+        for q in range(len(pats)):
+            server.lib.sm_stepper_retire(server.stepper, q)

@@ -316,10 +316,21 @@ __device__ __forceinline__ void staged_write(uint32_t* stg, uint32_t lane, uint3
                 if (rk < kStageCap) stg[rk + (rk >> 5)] = rel;
             });
         __syncwarp();
+        // stores of two positions (16 bytes) per lane, after one lone
+        // position when the slice does not start on a 16-byte boundary
         const uint32_t cnt = min(kStageCap, tot - p0);
-        for (uint32_t o = lane, i = 0; o < cnt; o += 32, ++i) {
-            const uint64_t g = out + p0 + o;
-            if (g < cap) d_pos[g] = base + stg[o + i];
+        const uint64_t g0 = out + p0;
+        const uint32_t lead = (reinterpret_cast<uintptr_t>(d_pos + g0) & 15u) ? 1u : 0u;
+        if (lead && lane == 0 && cnt && g0 < cap) d_pos[g0] = base + stg[0];
+        for (uint32_t o = lead + 2 * lane; o < cnt; o += 64) {
+            const uint64_t g = g0 + o;
+            const uint64_t a = base + stg[o + (o >> 5)];
+            if (o + 1 < cnt && g + 1 < cap) {
+                const uint64_t b = base + stg[o + 1 + ((o + 1) >> 5)];
+                *reinterpret_cast<ulonglong2*>(d_pos + g) = make_ulonglong2(a, b);
+            } else if (g < cap) {
+                d_pos[g] = a;
+            }
         }
         __syncwarp();
     }

@@ -137,13 +137,14 @@ sm_status sm_order_fixed(const uint8_t* h_pat, uint32_t m, int mode, uint32_t* h
  *              0 = choose automatically (then the peeled compares are chosen
  *              by a cost model, see below). Clamped to m. Does not change the
  *              result.
- *   flags      SM_SEARCH_BYTES: compare bytes even when 2-bit codes apply.
- *              Other bits must be 0.
+ *   flags      SM_SEARCH_BYTES: compare bytes even when coded compares
+ *              apply. Other bits must be 0.
  *   h_hist256  optional host histogram of THIS text (from sm_histogram). When
  *              given, it selects the automatic peel and the peeled compares,
  *              allows a faster compare when the text has no byte >= 0x80,
- *              compares 2-bit codes (16 starts per 32-bit word) when the text
- *              has at most four distinct symbols, and returns a zero count
+ *              compares 1-bit codes (32 starts per 32-bit word) when the text
+ *              has at most two distinct symbols and 2-bit codes (16 starts
+ *              per word) when it has at most four, and returns a zero count
  *              without scanning when some pattern symbol never occurs in the
  *              text. A histogram that does not belong to the text gives
  *              undefined results.

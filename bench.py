@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--serve", action="store_true",
                     help="also measure the serving loop (4 GiB resident text, Poisson arrivals)")
     ap.add_argument("--serve-only", action="store_true", help="measure only the serving loop")
+    ap.add_argument("--latency", action="store_true",
+                    help="also measure single-search latency on a 1 MiB ACGT text (m = 8)")
+    ap.add_argument("--latency-only", action="store_true", help="measure only the single-search latency")
     ap.add_argument("--multi", action="store_true",
                     help="also measure counts and positions over 20,000 packed texts (~35 GB)")
     ap.add_argument("--multi-only", action="store_true", help="measure only the packed-texts batch")
@@ -454,6 +457,49 @@ def run_batch(args, local, steps=3, warmup=2):
             "tuned_patterns_gbs": round(pgb / t_tuned, 1), "tuned_counts_agree": tuned_agree}
 
 
+def run_latency(args, local, reps=200):
+    """Latency of one search on a small, L2-resident text: n = 1 MiB of
+    uniform ACGT (seed 0), m = 8 copied from the text. Device time per call
+    (CUDA events around back-to-back calls) and call latency (from the host
+    call to the result on the host, each call synchronised), median over
+    reps, for sm_count and sm_report."""
+    import torch
+    from paper_1612_01506_gb300 import sm, synth
+    n, m = 1 << 20, 8
+    t = synth.uniform(n, 4, seed=0, stream=0)
+    p = t[1000:1000 + m].tobytes()
+    dev = torch.device("cuda", local)
+    ctx = sm.sm_create(local)
+    d = torch.from_numpy(t).to(dev)
+    hist = sm.sm_histogram(ctx, d).cpu().numpy().view(np.uint64).copy()
+    out = torch.zeros(1, dtype=torch.int64, device=dev)
+    cnt = int(sm.sm_count(ctx, d, p, hist=hist, out=out).item())
+    pos = torch.empty(max(cnt, 1), dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream()
+    res = {"workload": "1 MiB uniform ACGT (seed 0), m = 8 from the text, L2-resident", "count": cnt}
+    for name, call in (("count", lambda: sm.sm_count(ctx, d, p, hist=hist, out=out)),
+                       ("report", lambda: sm.sm_report(ctx, d, p, cnt, hist=hist, out_pos=pos, out_count=out))):
+        for _ in range(20):
+            call()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            call()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[f"{name}_device_us"] = round(e0.elapsed_time(e1) * 1e3 / reps, 2)
+        lat = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            call()
+            int(out.item())
+            lat.append(time.perf_counter() - t0)
+        res[f"{name}_call_us_p50"] = round(float(np.percentile(lat, 50)) * 1e6, 1)
+        res[f"{name}_call_us_p99"] = round(float(np.percentile(lat, 99)) * 1e6, 1)
+    return res
+
+
 def run_multi(args, local, steps=2, warmup=1):
     """Many packed texts: --multi-texts texts (20,000) with lengths log-uniform
     in [1 KiB, 16 MiB] (about 35 GB together), each over an alphabet drawn
@@ -701,6 +747,10 @@ def main():
         if rank == 0:
             print(json.dumps({"multi": run_multi(args, local)}), flush=True)
         return
+    if args.latency_only:
+        if rank == 0:
+            print(json.dumps({"latency": run_latency(args, local)}), flush=True)
+        return
     res = run_gpu(args, world, rank, local)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -718,6 +768,8 @@ def main():
             line["serving"] = run_serve(args, local)
         if args.multi and world == 1:
             line["multi"] = run_multi(args, local)
+        if args.latency and world == 1:
+            line["latency"] = run_latency(args, local)
         print(json.dumps(line), flush=True)
         if args.json_detail:
             with open(args.json_detail, "w") as f:

@@ -301,7 +301,9 @@ __device__ __forceinline__ uint32_t chunk_mask16(uint32_t x) {
 // consecutive ranks. Staged rank x sits at word x + x / 32: lanes whose
 // ranks are spaced evenly (by up to 32) then write distinct banks, where the
 // plain layout would put them on two. Ranks at or beyond cap (counted from
-// the batch's first rank `out`) are dropped.
+// the batch's first rank `out`) are dropped. base is a multiple of
+// kWarpStarts and rel < kWarpStarts (a warp-tile's positions), so base + rel
+// is base | rel: no carry into the high word.
 constexpr uint32_t kStageCap = 1024;
 constexpr uint32_t kStageWords = kStageCap + kStageCap / 32;
 
@@ -309,24 +311,29 @@ template <class ForEach>
 __device__ __forceinline__ void staged_write(uint32_t* stg, uint32_t lane, uint32_t excl, uint32_t n, uint32_t tot,
                                              uint64_t base, uint64_t out, uint64_t* __restrict__ d_pos,
                                              uint64_t cap, ForEach for_each) {
+    const uint32_t lo = (uint32_t)base, hi = (uint32_t)(base >> 32);
+    auto pos = [&](uint32_t rel) { return ((uint64_t)hi << 32) | (lo | rel); };
     for (uint32_t p0 = 0; p0 < tot; p0 += kStageCap) {
-        if (n && excl < p0 + kStageCap && excl + n > p0)
+        if (tot <= kStageCap) {   // one slice: every rank of the lane is in it
+            if (n) for_each([&](uint32_t k, uint32_t rel) { stg[excl + k + ((excl + k) >> 5)] = rel; });
+        } else if (n && excl < p0 + kStageCap && excl + n > p0) {
             for_each([&](uint32_t k, uint32_t rel) {
                 const uint32_t rk = excl + k - p0;   // wraps to a large value below the slice
                 if (rk < kStageCap) stg[rk + (rk >> 5)] = rel;
             });
+        }
         __syncwarp();
         // stores of two positions (16 bytes) per lane, after one lone
         // position when the slice does not start on a 16-byte boundary
         const uint32_t cnt = min(kStageCap, tot - p0);
         const uint64_t g0 = out + p0;
         const uint32_t lead = (reinterpret_cast<uintptr_t>(d_pos + g0) & 15u) ? 1u : 0u;
-        if (lead && lane == 0 && cnt && g0 < cap) d_pos[g0] = base + stg[0];
+        if (lead && lane == 0 && cnt && g0 < cap) d_pos[g0] = pos(stg[0]);
         for (uint32_t o = lead + 2 * lane; o < cnt; o += 64) {
             const uint64_t g = g0 + o;
-            const uint64_t a = base + stg[o + (o >> 5)];
+            const uint64_t a = pos(stg[o + (o >> 5)]);
             if (o + 1 < cnt && g + 1 < cap) {
-                const uint64_t b = base + stg[o + 1 + ((o + 1) >> 5)];
+                const uint64_t b = pos(stg[o + 1 + ((o + 1) >> 5)]);
                 *reinterpret_cast<ulonglong2*>(d_pos + g) = make_ulonglong2(a, b);
             } else if (g < cap) {
                 d_pos[g] = a;

@@ -60,14 +60,14 @@ def parse():
     ap.add_argument("--peel", type=int, default=0, help="peeling factor r (0 = automatic)")
     ap.add_argument("--stages", type=int, default=0, help="scan pipeline depth (0 = library default)")
     ap.add_argument("--ctas", type=int, default=0, help="scan CTAs (0 = one resident wave)")
-    ap.add_argument("--batch", action="store_true",
-                    help="also measure batched counting (256 MiB Markov text, 4096 patterns)")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched-counting leg (256 MiB Markov text, 4096 patterns; on by default)")
     ap.add_argument("--batch-only", action="store_true", help="measure only the batched counting")
     ap.add_argument("--serve", action="store_true",
                     help="also measure the serving loop (4 GiB resident text, Poisson arrivals)")
     ap.add_argument("--serve-only", action="store_true", help="measure only the serving loop")
-    ap.add_argument("--latency", action="store_true",
-                    help="also measure single-search latency on a 1 MiB ACGT text (m = 8)")
+    ap.add_argument("--no-latency", action="store_true",
+                    help="skip the single-search latency leg (1 MiB ACGT text, m = 8; on by default)")
     ap.add_argument("--latency-only", action="store_true", help="measure only the single-search latency")
     ap.add_argument("--multi", action="store_true",
                     help="also measure counts and positions over 20,000 packed texts (~35 GB)")
@@ -242,58 +242,60 @@ def run_gpu(args, world, rank, local):
     for i, k in enumerate(kinds):
         hists[k] = hist_dev[i].cpu().numpy().view(np.uint64).copy()
 
-    ev_count = []   # (start, end) events around each count launch of the timed steps
+    # (start, end) events around each count and each report of the timed
+    # steps, per (text, m): the per-(sigma, m) table, the gate and the two
+    # rooflines come from them
+    ev = {}
     launches = {"n": 0}
+    P = args.patterns
 
     def step(timed: bool, text_map):
-        per = {}
         for i, k in enumerate(kinds):
             sm.sm_histogram(ctx, text_map[k], out=hist_dev[i])
             launches["n"] += 1
             h = hists[k]
             for m in ms:
-                slot = 0
-                e0 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                for p in pats[(k, m)]:
-                    pi = sm.sm_order(p, h)
-                    if "count" in variants:
+                pis = [sm.sm_order(p, h) for p in pats[(k, m)]]
+                for var in variants:
+                    lst = ev.setdefault((var, k, m), []) if timed else None
+                    for j, p in enumerate(pats[(k, m)]):
                         if timed:
                             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                             a.record(stream)
-                        sm.sm_count(ctx, text_map[k], p, pi=pi, hist=h, peel=args.peel,
-                                    out=counts[slot:slot + 1])
-                        launches["n"] += 1
+                        if var == "count":
+                            sm.sm_count(ctx, text_map[k], p, pi=pis[j], hist=h, peel=args.peel,
+                                        out=counts[j:j + 1])
+                            launches["n"] += 1
+                        else:
+                            sm.sm_report(ctx, text_map[k], p, max_cap, pi=pis[j], hist=h, peel=args.peel,
+                                         out_pos=d_pos, out_count=counts[P + j:P + j + 1])
+                            launches["n"] += 3
                         if timed:
                             b.record(stream)
-                            ev_count.append((a, b))
-                    slot += 1
-                    if "report" in variants:
-                        sm.sm_report(ctx, text_map[k], p, max_cap, pi=pi, hist=h, peel=args.peel,
-                                     out_pos=d_pos, out_count=counts[slot:slot + 1])
-                        launches["n"] += 2
-                    slot += 1
-                e1 = torch.cuda.Event(enable_timing=True)
-                e1.record(stream)
-                per[(k, m)] = (e0, e1)
-        return per
+                            lst.append((a, b))
+
+    # matches per pattern (for the report's algorithmic bytes n + 8 occ)
+    occ = {}
+    for k in kinds:
+        for m in ms:
+            for j, p in enumerate(pats[(k, m)]):
+                sm.sm_count(ctx, d_texts[k], p, out=counts[j:j + 1])
+            occ[(k, m)] = [int(x) for x in counts[:P].cpu().numpy()]
 
     for _ in range(args.warmup):
         step(False, d_texts)
     if sm.sm_sync(ctx) != sm.SM_OK:
         raise RuntimeError("deferred device status after warm-up")
     launches["n"] = 0
-    ev_count.clear()
 
     barrier(world)
     torch.cuda.synchronize()
-    per_steps = []
     with ClockSampler(local) as clk:
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
         for _ in range(args.steps):
-            per_steps.append(step(True, d_texts))
+            step(True, d_texts)
         t1.record(stream)
         torch.cuda.synchronize()
     barrier(world)
@@ -307,30 +309,63 @@ def run_gpu(args, world, rank, local):
     bytes_per_step = searches_per_step * args.n
     value = world * bytes_per_step * args.steps / elapsed / 1e9
 
-    # per-(sigma, m) breakdown from the events of the timed steps (GB/s)
-    detail = {}
-    for (k, m), _ in per_steps[0].items():
-        ts = [ps[(k, m)][0].elapsed_time(ps[(k, m)][1]) / 1e3 for ps in per_steps]
-        detail[f"{k}/m{m}"] = round(args.patterns * len(variants) * args.n / statistics.median(ts) / 1e9, 1)
-
-    # roofline of the count scan kernel: n algorithmic bytes per launch
-    durs = [a.elapsed_time(b) / 1e3 for a, b in ev_count]
+    # per-(sigma, m) mean launch times; count: n bytes, report: n + 8 occ
     peak, peak_kind = peak_gbs()
-    roof = None
-    if durs:
-        avg = sum(durs) / len(durs)
-        achieved = args.n / avg / 1e9
-        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": scan_traffic(args.n), "peak_source": peak_kind,
-                "kernel": "scan_kernel<count>", "launches": len(durs)}
+    durs = {key: [a.elapsed_time(b) / 1e3 for a, b in v] for key, v in ev.items()}
+    detail, gate_cells = {}, {}
+    for k in kinds:
+        for m in ms:
+            cell = {}
+            if ("count", k, m) in durs:
+                t = statistics.mean(durs[("count", k, m)])
+                cell["count_gbs"] = round(args.n / t / 1e9, 1)
+                cell["count_frac"] = round(args.n / t / 1e9 / peak, 3)
+                if k != 2 and m <= 64:
+                    gate_cells[f"{k}/m{m}"] = cell["count_frac"]
+            if ("report", k, m) in durs:
+                t = statistics.mean(durs[("report", k, m)])
+                ab = args.n + 8 * statistics.mean(occ[(k, m)])
+                cell["report_gbs"] = round(args.n / t / 1e9, 1)
+                cell["report_frac"] = round(ab / t / 1e9 / peak, 3)
+            detail[f"{k}/m{m}"] = cell
+    gate = None
+    if gate_cells:
+        gate = {"rule": "count kernel >= 0.70 of measured HBM peak for m <= 64 on sigma >= 4",
+                "pass": min(gate_cells.values()) >= 0.70, "min_frac": min(gate_cells.values()),
+                "cells": gate_cells}
+
+    def roofline(var, kernel, alg):
+        tot_t = tot_b = 0.0
+        nl = 0
+        for (v, k, m), ds in durs.items():
+            if v != var:
+                continue
+            for j, d in enumerate(ds):
+                tot_t += d
+                tot_b += alg(k, m, j % P)
+                nl += 1
+        if not nl:
+            return None
+        ach = tot_b / tot_t / 1e9
+        return {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
+                "peak_source": peak_kind, "kernel": kernel, "launches": nl}
+
+    roof = roofline("count", "scan_kernel<count>", lambda k, m, j: args.n)
+    if roof:
+        roof["traffic"] = scan_traffic(args.n)
+    roof_rep = roofline("report", "report: scan_kernel<tile count> + range_sum_kernel + bitmap_write_kernel",
+                        lambda k, m, j: args.n + 8 * occ[(k, m)][j])
+    if roof_rep:
+        roof_rep["bytes"] = "n + 8 * matches per report"
+        roof_rep["traffic"] = None
 
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, ctx, kinds, ms, pats, hists, texts, dev, stream, d_texts, variants, world)
 
     return {"value": value, "elapsed": elapsed, "bytes_per_step": bytes_per_step, "detail": detail,
-            "roofline": roof, "clocks": clk.summary(), "e2e": e2e, "launches": launches["n"],
-            "searches_per_step": searches_per_step}
+            "roofline": roof, "report_roofline": roof_rep, "gate": gate, "clocks": clk.summary(), "e2e": e2e,
+            "launches": launches["n"], "searches_per_step": searches_per_step}
 
 
 def run_e2e(args, ctx, kinds, ms, pats, hists, texts, dev, stream, d_texts, variants, world):
@@ -669,33 +704,80 @@ def run_serve(args, local):
 
 # ---------------------------------------------------------------- CPU oracle
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
 def run_cpu_baseline(args, budget_s: float):
-    """The oracle (Algorithm 1, threaded over the host cores) on a bounded
-    sample of the sweep: 64 MiB prefixes of the texts, cycling over
-    (sigma, m) with fresh patterns until the time budget is spent."""
+    """The oracle on a bounded sample of the sweep, on the host cores.
+
+    Threaded leg (three quarters of the budget): Algorithm 1 split over all
+    cores, on 64 MiB prefixes of the sweep texts, cycling over (sigma, m,
+    variant) in the sweep's mix (count and report of every pattern) with
+    fresh patterns until the budget is spent. Single-thread leg (the rest):
+    plain Algorithm 1 on one core, counts on 8 MiB prefixes, same cycle."""
     import oracle
     from paper_1612_01506_gb300 import synth
     kinds, ms = kinds_of(args.kinds), [int(x) for x in args.ms.split(",") if x]
+    variants = [v for v in args.variants.split(",") if v]
     cores = os.cpu_count() or 1
     sample_n = min(args.n, 64 << 20)
-    scanned, spent, searches = 0, 0.0, 0
-    order = [(k, m) for m in ms for k in kinds]
+    single_n = min(args.n, 8 << 20)
     texts = {k: synth.text(k, sample_n, seed=0, stream=synth.stream_id("sweep", k)) for k in kinds}
-    rep = 0
-    while spent < budget_s and rep < 100:
-        for k, m in order:
-            if spent >= budget_s:
-                break
-            p = synth.sample_patterns(texts[k], m, rep + 1, seed=0, stream=synth.stream_id("pat", k, m))[rep]
-            t0 = time.perf_counter()
-            oracle.count_threads(p, texts[k], cores)
-            spent += time.perf_counter() - t0
-            scanned += sample_n
-            searches += 1
-        rep += 1
-    return {"value": round(scanned / spent / 1e9, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
-            "sample": f"{searches} counts over {sample_n >> 20} MiB prefixes of the sweep texts "
-                      f"(sigma {args.kinds}; m {args.ms}), {spent:.1f} s"}
+    order = [(k, m) for m in ms for k in kinds]
+
+    def leg(budget, n, threaded):
+        scanned, spent, searches = {v: 0 for v in variants}, {v: 0.0 for v in variants}, 0
+        rep = 0
+        while sum(spent.values()) < budget and rep < 100:
+            for k, m in order:
+                if sum(spent.values()) >= budget:
+                    break
+                t = texts[k][:n]
+                p = synth.sample_patterns(t, m, rep + 1, seed=0, stream=synth.stream_id("pat", k, m))[rep]
+                for v in (variants if threaded else ["count"]):
+                    t0 = time.perf_counter()
+                    if not threaded:
+                        oracle.naive_count(p, t)
+                    elif v == "count":
+                        oracle.count_threads(p, t, cores)
+                    else:
+                        oracle.report_threads(p, t, n - m + 1, cores)
+                    spent[v] += time.perf_counter() - t0
+                    scanned[v] += n
+                    searches += 1
+            rep += 1
+        tot = sum(spent.values())
+        per = {f"{v}_gbs": round(scanned[v] / spent[v] / 1e9, 3) for v in spent if spent[v] > 0}
+        return round(sum(scanned.values()) / tot / 1e9, 3), searches, tot, per
+
+    v_thr, n_thr, s_thr, per = leg(0.75 * budget_s, sample_n, True)
+    v_one, n_one, s_one, _ = leg(0.25 * budget_s, single_n, False)
+    out = {"value": v_thr, "unit": "GB/s", "cores": cores, "kind": "oracle",
+           "sample": f"{n_thr} searches ({'+'.join(variants)} of each pattern) over {sample_n >> 20} MiB prefixes "
+                     f"of the sweep texts (sigma {args.kinds}; m {args.ms}), {s_thr:.1f} s, threaded over {cores} cores",
+           "cpu_model": cpu_model(),
+           "single_thread": {"value": v_one, "unit": "GB/s", "cores": 1,
+                             "sample": f"{n_one} counts (plain Algorithm 1) over {single_n >> 20} MiB prefixes, "
+                                       f"{s_one:.1f} s"}}
+    out.update(per)
+    return out
 
 
 # ---------------------------------------------------------------- main
@@ -760,15 +842,17 @@ def main():
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(res["elapsed"] / args.steps * 1e3, 2), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-                "config": config_block(args, world), "roofline": res["roofline"], "cpu_baseline": cpu,
-                "e2e": res["e2e"], "gpu_launches": res["launches"], "clocks": res["clocks"]}
-        if args.batch and world == 1:
+                "config": config_block(args, world), "roofline": res["roofline"],
+                "report_roofline": res["report_roofline"], "gate": res["gate"], "cpu_baseline": cpu,
+                "e2e": res["e2e"], "gpu_launches": res["launches"], "clocks": res["clocks"],
+                "sweep": res["detail"]}
+        if not args.no_batch and world == 1:
             line["batch"] = run_batch(args, local)
         if args.serve and world == 1:
             line["serving"] = run_serve(args, local)
         if args.multi and world == 1:
             line["multi"] = run_multi(args, local)
-        if args.latency and world == 1:
+        if not args.no_latency and world == 1:
             line["latency"] = run_latency(args, local)
         print(json.dumps(line), flush=True)
         if args.json_detail:

@@ -386,13 +386,46 @@ struct GlobalQC {
 // the rest of a surviving chunk.
 constexpr uint32_t kLaneCompares = 16;
 
+// Found bits of a warp-tile with matches, as the tile-count pass of a report
+// stores them in the warp-tile's 64-word slot. Chunk k (k = 0..127) is
+// starts 16k .. 16k + 15 of the warp-tile, its mask has bit b for start
+// 16k + b. List form: when at most kListMax chunks have a match, one word
+// (k << 16) | mask per such chunk, ascending k, from word 0 (the slot's
+// other words are not written). Bitmap form otherwise: the 128 masks, chunk
+// k in the low (k even) or high half of word k / 2. The per-(tile, warp)
+// count word tells them apart: matches in bits 0-15, the number of list
+// words in bits 16-23 (0: bitmap form).
+constexpr uint32_t kListMax = kBitmapWords;
+constexpr uint32_t kCountMask = 0xFFFFu;
+
+// Lane l holds the masks of chunks 4l .. 4l + 3 in c[0..3]: store the
+// warp-tile's slot in the form that fits and return the list length (0 for
+// the bitmap form). All lanes take part.
+__device__ __forceinline__ uint32_t store_found_lanes(uint32_t* __restrict__ bm, uint32_t lane,
+                                                      const uint32_t (&c)[4]) {
+    const uint32_t nz = (uint32_t)(c[0] != 0u) + (uint32_t)(c[1] != 0u) + (uint32_t)(c[2] != 0u) +
+                        (uint32_t)(c[3] != 0u);
+    const uint32_t inc = warp_incl_scan(nz, lane);
+    const uint32_t tot = __shfl_sync(kFull, inc, 31);
+    if (tot <= kListMax) {
+        uint32_t o = inc - nz;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (c[i]) bm[o++] = ((4u * lane + (uint32_t)i) << 16) | c[i];
+        return tot;
+    }
+    reinterpret_cast<uint2*>(bm)[lane] = make_uint2(c[0] | (c[1] << 16), c[2] | (c[3] << 16));
+    return 0;
+}
+
 template <bool SEVEN, bool WRITE, bool DIRECT, class QC>
 __device__ __forceinline__ uint32_t warp_tile(const uint4* __restrict__ b4, const uint32_t* __restrict__ b32,
                                               uint32_t c0, uint32_t wq, uint32_t warp, uint32_t lane, QC qc,
                                               uint32_t m, uint32_t r, uint32_t ng, uint32_t one,
                                               uint64_t nstarts, uint64_t s0, uint32_t* q,
                                               uint64_t out, uint64_t* __restrict__ d_pos, uint64_t cap,
-                                              uint32_t* __restrict__ bm = nullptr, uint32_t* sbm = nullptr) {
+                                              uint32_t* __restrict__ bm = nullptr, uint32_t* sbm = nullptr,
+                                              uint32_t* ent = nullptr) {
     uint32_t f[kChunks][4];
 #pragma unroll
     for (int c = 0; c < kChunks; ++c)
@@ -432,15 +465,36 @@ __device__ __forceinline__ uint32_t warp_tile(const uint4* __restrict__ b4, cons
 
     if (DIRECT && r >= m) {
         // every compare peeled: the found bits are final. With bm, store the
-        // bitmap (chunk k = 32c + lane: 16 bits, start order) when the
-        // warp-tile has matches
+        // slot of a warp-tile with matches (chunk k = 32c + lane): the list
+        // of its chunks with matches (ballots in chunk order), or the
+        // bitmap when more than kListMax chunks have one
         const uint32_t cnt = count_flags<kChunks>(f);
-        if (bm && warp_sum_u32(cnt)) {
-            uint16_t* bm16 = reinterpret_cast<uint16_t*>(bm);
+        if (bm && __any_sync(kFull, cnt != 0u)) {
+            uint32_t bal[kChunks], tot = 0;
 #pragma unroll
-            for (int c = 0; c < kChunks; ++c)
-                bm16[32 * c + lane] = (uint16_t)chunk_mask16(((f[c][0] >> 7) | (f[c][1] >> 6)) |
-                                                             ((f[c][2] >> 5) | (f[c][3] >> 4)));
+            for (int c = 0; c < kChunks; ++c) {
+                bal[c] = __ballot_sync(kFull, ((f[c][0] | f[c][1]) | (f[c][2] | f[c][3])) != 0u);
+                tot += __popc(bal[c]);
+            }
+            const uint32_t lt = (1u << lane) - 1u;
+            if (tot <= kListMax) {
+                uint32_t o = 0;
+#pragma unroll
+                for (int c = 0; c < kChunks; ++c) {
+                    if ((bal[c] >> lane) & 1u)
+                        bm[o + __popc(bal[c] & lt)] =
+                            ((32u * c + lane) << 16) | chunk_mask16(((f[c][0] >> 7) | (f[c][1] >> 6)) |
+                                                                    ((f[c][2] >> 5) | (f[c][3] >> 4)));
+                    o += __popc(bal[c]);
+                }
+            } else {
+                uint16_t* bm16 = reinterpret_cast<uint16_t*>(bm);
+#pragma unroll
+                for (int c = 0; c < kChunks; ++c)
+                    bm16[32 * c + lane] = (uint16_t)chunk_mask16(((f[c][0] >> 7) | (f[c][1] >> 6)) |
+                                                                 ((f[c][2] >> 5) | (f[c][3] >> 4)));
+            }
+            if (ent) *ent = tot <= kListMax ? tot : 0u;
         }
         return cnt;
     }
@@ -474,6 +528,7 @@ __device__ __forceinline__ uint32_t warp_tile(const uint4* __restrict__ b4, cons
     __syncwarp();
 
     uint32_t tile_count = 0;   // this lane's share of the warp's matches in the tile
+    uint32_t nlist = 0;        // bm: chunks with matches so far
     for (uint32_t qb = 0; qb < qn; qb += 32) {
         const uint32_t e = qb + lane;
         uint32_t g[4] = {0u, 0u, 0u, 0u}, k = 0;
@@ -512,9 +567,18 @@ __device__ __forceinline__ uint32_t warp_tile(const uint4* __restrict__ b4, cons
             }
         }
         const uint32_t n = (__popc(g[0]) + __popc(g[1])) + (__popc(g[2]) + __popc(g[3]));
-        if (bm && n)   // chunk k's 16 found bits in start order
-            reinterpret_cast<uint16_t*>(sbm)[k] =
-                (uint16_t)chunk_mask16(((g[0] >> 7) | (g[1] >> 6)) | ((g[2] >> 5) | (g[3] >> 4)));
+        if (bm) {
+            // chunk k's 16 found bits in start order: into the list (entries
+            // come in chunk order) while it fits, and into the bitmap
+            const uint32_t bal = __ballot_sync(kFull, n != 0u);
+            if (n) {
+                const uint32_t mk = chunk_mask16(((g[0] >> 7) | (g[1] >> 6)) | ((g[2] >> 5) | (g[3] >> 4)));
+                const uint32_t o = nlist + __popc(bal & ((1u << lane) - 1u));
+                if (o < kListMax) bm[o] = (k << 16) | mk;
+                reinterpret_cast<uint16_t*>(sbm)[k] = (uint16_t)mk;
+            }
+            nlist += __popc(bal);
+        }
         if (WRITE) {
             const uint32_t inc = warp_incl_scan(n, lane);
             uint64_t rk = out + inc - n;
@@ -535,10 +599,11 @@ __device__ __forceinline__ uint32_t warp_tile(const uint4* __restrict__ b4, cons
         }
     }
     __syncwarp();   // the queue is reused by the next tile
-    if (bm && warp_sum_u32(tile_count)) {   // store the bitmap of a warp-tile with matches
+    if (bm && nlist > kListMax) {   // too many chunks with matches for the list: the bitmap
         bm[2 * lane] = sbm[2 * lane];
         bm[2 * lane + 1] = sbm[2 * lane + 1];
     }
+    if (bm && ent) *ent = nlist <= kListMax ? nlist : 0u;
     return tile_count;
 }
 
@@ -626,7 +691,7 @@ __device__ __forceinline__ uint2 packed_tiles(const uint32_t* const (&pk)[2], bo
                                               uint32_t lane, QC qc, uint32_t m, uint32_t r, uint32_t ng,
                                               uint64_t nstarts, const uint64_t (&s0)[2], const uint64_t (&out)[2],
                                               uint64_t* __restrict__ d_pos, uint64_t cap,
-                                              uint32_t* const (&bm)[2]) {
+                                              uint32_t* const (&bm)[2], uint32_t* ent = nullptr) {
     const uint32_t w0 = warp * 128u + lane * 4u;   // lane's first packed word
     uint32_t y[2][4] = {{0u, 0u, 0u, 0u}, {0u, 0u, 0u, 0u}};
     for (uint32_t g = 0, j = 0; g < ng; ++g) {
@@ -712,13 +777,14 @@ __device__ __forceinline__ uint2 packed_tiles(const uint32_t* const (&pk)[2], bo
     for (int t = 0; t < NT; ++t) n[t] = __popc(f[t][0] | (f[t][1] << 1)) + __popc(f[t][2] | (f[t][3] << 1));
 #pragma unroll
     for (int t = 0; t < NT; ++t)
-        if (bm[t] && warp_sum_u32(n[t])) {
-            // the warp-tile's found bitmap in start order: lane l's 64 starts
-            // are words 2l, 2l + 1 (found bit 2k of a packed word -> bit k)
+        if (bm[t] && __any_sync(kFull, n[t] != 0u)) {
+            // the warp-tile's slot: lane l's 64 starts are chunks 4l .. 4l + 3
+            // (found bit 2k of a packed word -> bit k)
             uint32_t c[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) c[i] = compress_even(f[t][i]);
-            reinterpret_cast<uint2*>(bm[t])[lane] = make_uint2(c[0] | (c[1] << 16), c[2] | (c[3] << 16));
+            const uint32_t e = store_found_lanes(bm[t], lane, c);
+            if (ent) ent[t] = e;
         }
     if (WRITE) {
         // positions in order: lanes, then words, then starts
@@ -797,7 +863,7 @@ __device__ __forceinline__ uint2 binary_tiles(const uint32_t* const (&pk)[2], bo
                                               uint32_t lane, QC qc, uint32_t m, uint32_t r, uint32_t ng,
                                               uint64_t nstarts, const uint64_t (&s0)[2], const uint64_t (&out)[2],
                                               uint64_t* __restrict__ d_pos, uint64_t cap,
-                                              uint32_t* const (&bm)[2]) {
+                                              uint32_t* const (&bm)[2], uint32_t* ent = nullptr) {
     const uint32_t w0 = warp * 64u + lane * 2u;   // lane's first word
     uint32_t y[2][2] = {{0u, 0u}, {0u, 0u}};
     for (uint32_t g = 0, j = 0; g < ng; ++g) {
@@ -881,8 +947,11 @@ __device__ __forceinline__ uint2 binary_tiles(const uint32_t* const (&pk)[2], bo
     for (int t = 0; t < 2; ++t) n[t] = __popc(f[t][0]) + __popc(f[t][1]);
 #pragma unroll
     for (int t = 0; t < 2; ++t)
-        if (bm[t] && warp_sum_u32(n[t]))   // lane l's 64 starts are words 2l, 2l + 1 of the bitmap
-            reinterpret_cast<uint2*>(bm[t])[lane] = make_uint2(f[t][0], f[t][1]);
+        if (bm[t] && __any_sync(kFull, n[t] != 0u)) {   // lane l's 64 starts are chunks 4l .. 4l + 3
+            const uint32_t c[4] = {f[t][0] & 0xFFFFu, f[t][0] >> 16, f[t][1] & 0xFFFFu, f[t][1] >> 16};
+            const uint32_t e = store_found_lanes(bm[t], lane, c);
+            if (ent) ent[t] = e;
+        }
     if (WRITE) {
         // positions in order: lanes, then words, then starts
 #pragma unroll

@@ -128,7 +128,8 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
                 // next tile with matches; lanes look at 4 tiles x 8 warp counts per step
                 while (cursor < t_end) {
                     const uint64_t t = cursor + (lane >> 3);
-                    uint32_t c = t < t_end ? __ldcg(A.warp_counts + t * kConsumerWarps + (lane & 7u)) : 0u;
+                    uint32_t c =
+                        t < t_end ? __ldcg(A.warp_counts + t * kConsumerWarps + (lane & 7u)) & kCountMask : 0u;
                     c += __shfl_xor_sync(kFull, c, 1);
                     c += __shfl_xor_sync(kFull, c, 2);
                     c += __shfl_xor_sync(kFull, c, 4);
@@ -238,7 +239,7 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
                 for (int k = 0; k < 2; ++k)
                     if (k == 0 || two) {
                         const uint32_t cw =
-                            lane < warp ? __ldcg(A.warp_counts + d[k].tile * kConsumerWarps + lane) : 0u;
+                            lane < warp ? __ldcg(A.warp_counts + d[k].tile * kConsumerWarps + lane) & kCountMask : 0u;
                         out[k] = d[k].offset + warp_sum_u32(cw);
                     }
             }
@@ -249,18 +250,21 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
                 MODE == kModeTileCount && A.bitmaps && two
                     ? A.bitmaps + (d[1].tile * kConsumerWarps + warp) * kBitmapWords : nullptr};
             uint2 c;
+            uint32_t ent[2] = {0u, 0u};
             if constexpr (BIN)
                 c = binary_tiles<MODE == kModeWrite, MODE != kModeWrite>(pk, two, warp, lane, ParamQC<MAXM>{&P}, m, r,
-                                                                         A.ng, A.nstarts, s0, out, A.d_pos, A.cap, bm);
+                                                                         A.ng, A.nstarts, s0, out, A.d_pos, A.cap, bm,
+                                                                         ent);
             else
                 c = packed_tiles<MODE == kModeWrite, MODE != kModeWrite>(pk, two, warp, lane, ParamQC<MAXM>{&P}, m, r,
-                                                                         A.ng, A.nstarts, s0, out, A.d_pos, A.cap, bm);
+                                                                         A.ng, A.nstarts, s0, out, A.d_pos, A.cap, bm,
+                                                                         ent);
             if (MODE == kModeTileCount) {
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
                     if (k == 1 && !two) break;
                     const uint32_t wsum = warp_sum_u32(k == 0 ? c.x : c.y);
-                    if (lane == 0) A.warp_counts[d[k].tile * kConsumerWarps + warp] = wsum;
+                    if (lane == 0) A.warp_counts[d[k].tile * kConsumerWarps + warp] = wsum | (ent[k] << 16);
                 }
             }
             my_count += c.x + c.y;
@@ -288,18 +292,20 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
 
             uint64_t out = 0;
             if (MODE == kModeWrite) {
-                const uint32_t cw = lane < warp ? __ldcg(A.warp_counts + d.tile * kConsumerWarps + lane) : 0u;
+                const uint32_t cw =
+                    lane < warp ? __ldcg(A.warp_counts + d.tile * kConsumerWarps + lane) & kCountMask : 0u;
                 out = d.offset + warp_sum_u32(cw);
             }
             uint32_t* bm = MODE == kModeTileCount && A.bitmaps
                                ? A.bitmaps + (d.tile * kConsumerWarps + warp) * kBitmapWords : nullptr;
+            uint32_t ent = 0;
             const uint32_t tile_count = warp_tile<SEVEN, MODE == kModeWrite, MODE != kModeWrite>(
                 b4, b32, c0, wq, warp, lane, ParamQC<MAXM>{&P}, m, r, A.ng, one,
-                A.nstarts, s0, q, out, A.d_pos, A.cap, bm, sbms + warp * kBitmapWords);
+                A.nstarts, s0, q, out, A.d_pos, A.cap, bm, sbms + warp * kBitmapWords, &ent);
 
             if (MODE == kModeTileCount) {
                 const uint32_t wsum = warp_sum_u32(tile_count);
-                if (lane == 0) A.warp_counts[d.tile * kConsumerWarps + warp] = wsum;
+                if (lane == 0) A.warp_counts[d.tile * kConsumerWarps + warp] = wsum | (ent << 16);
             }
             my_count += tile_count;
             __syncwarp();
@@ -367,7 +373,7 @@ __global__ void __launch_bounds__(kWriteThreads) range_sum_kernel(const uint32_t
     uint64_t v = 0;
     for (uint64_t i = tid; i < nv; i += kWriteThreads) {
         const uint4 x = __ldcg(src + i);
-        v += (uint64_t)((x.x + x.y) + (x.z + x.w));
+        v += (uint64_t)(((x.x & kCountMask) + (x.y & kCountMask)) + ((x.z & kCountMask) + (x.w & kCountMask)));
     }
     v = warp_sum_u64(v);
     if (lane == 0) red[warp] = v;
@@ -402,6 +408,7 @@ __global__ void __launch_bounds__(kWriteThreads) bitmap_write_kernel(const __gri
     __shared__ uint64_t red[kConsumerWarps];
     __shared__ uint64_t base_s;
     __shared__ uint8_t list[kConsumerWarps][kWalk];   // per warp: its warp-tiles with matches in the pass
+    __shared__ uint8_t nent[kWalk][kConsumerWarps];   // list length of each warp-tile's slot (0: bitmap)
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint64_t t0 = (uint64_t)blockIdx.x * W.tiles_per_cta;
     const uint64_t t1 = min(t0 + W.tiles_per_cta, W.ntiles);
@@ -437,7 +444,8 @@ __global__ void __launch_bounds__(kWriteThreads) bitmap_write_kernel(const __gri
 #pragma unroll
             for (int w = 0; w < kConsumerWarps; ++w) {
                 woff[tid][w] = tot;
-                tot += c[w];
+                tot += c[w] & kCountMask;
+                nent[tid][w] = (uint8_t)(c[w] >> 16);
             }
             ttot[tid] = tot;
         }
@@ -482,6 +490,30 @@ __global__ void __launch_bounds__(kWriteThreads) bitmap_write_kernel(const __gri
                 const uint64_t s0 = (p0 + k) * kTile + warp * kWarpStarts;
                 uint64_t o = base + toff[k] + woff[k][warp];
                 uint32_t left = own(k);
+                const uint32_t ne = nent[k][warp];
+                // list form: one word per chunk with matches, (chunk << 16) | mask
+                for (uint32_t e0 = 0; e0 < ne; e0 += 16) {
+                    uint4 x[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (e0 + 4 * q < ne) x[q] = __ldcg(bp + e0 / 4 + q);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const uint32_t w[4] = {x[q].x, x[q].y, x[q].z, x[q].w};
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            if (e0 + 4 * q + i >= ne) break;
+                            const uint64_t c0 = s0 + 16u * (w[i] >> 16);
+                            uint32_t fw = w[i] & 0xFFFFu;
+                            while (fw) {
+                                if (o < W.cap) W.d_pos[o] = c0 + (uint32_t)(__ffs(fw) - 1);
+                                ++o;
+                                fw &= fw - 1;
+                            }
+                        }
+                    }
+                }
+                if (ne) left = 0;
                 for (uint32_t q0 = 0; q0 < kBitmapWords / 4 && left; q0 += 4) {
                     uint4 x[4];
 #pragma unroll
@@ -509,18 +541,29 @@ __global__ void __launch_bounds__(kWriteThreads) bitmap_write_kernel(const __gri
         };
         auto write = [&](uint32_t j, uint2 x) {
             const uint32_t k = lst[j];
-            const uint32_t n = __popc(x.x) + __popc(x.y);
+            // lane l's two pieces of found bits and the start (relative to
+            // the warp-tile) of each piece's bit 0: bitmap words 2l, 2l + 1,
+            // or list words 2l, 2l + 1 (those below the list length)
+            const uint32_t ne = nent[k][warp];
+            uint32_t m0 = x.x, m1 = x.y, r0 = 64u * lane, r1 = 64u * lane + 32u;
+            if (ne) {
+                m0 = 2u * lane < ne ? x.x & 0xFFFFu : 0u;
+                m1 = 2u * lane + 1u < ne ? x.y & 0xFFFFu : 0u;
+                r0 = 16u * (x.x >> 16);
+                r1 = 16u * (x.y >> 16);
+            }
+            const uint32_t n = __popc(m0) + __popc(m1);
             const uint32_t inc2 = warp_incl_scan(n, lane);
             staged_write(stg, lane, inc2 - n, n, own(k), (p0 + k) * kTile + warp * kWarpStarts,
                          base + toff[k] + woff[k][warp], W.d_pos, W.cap, [&](auto&& cb) {
-                             uint32_t kk = 0, fw = x.x;
+                             uint32_t kk = 0, fw = m0;
                              while (fw) {
-                                 cb(kk++, 64u * lane + (uint32_t)(__ffs(fw) - 1));
+                                 cb(kk++, r0 + (uint32_t)(__ffs(fw) - 1));
                                  fw &= fw - 1;
                              }
-                             fw = x.y;
+                             fw = m1;
                              while (fw) {
-                                 cb(kk++, 64u * lane + 32u + (uint32_t)(__ffs(fw) - 1));
+                                 cb(kk++, r1 + (uint32_t)(__ffs(fw) - 1));
                                  fw &= fw - 1;
                              }
                          });

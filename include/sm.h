@@ -337,14 +337,21 @@ void sm_stepper_destroy(sm_stepper* stepper);
  * All calls share the one array and it keeps the previous call's contents
  * (the call clears what must start at zero): calls whose work overlaps on
  * the GPU -- other streams, other host threads -- race and give wrong
- * results, so order them. A report with more than cap matches writes the
- * first cap positions and the full count; the caller sees this as
- * *d_count > cap (there is no context to hold a deferred status).
+ * results, so order them. There is no context to hold a deferred status,
+ * so device-side conditions show in *d_count once the stream has reached
+ * the call:
+ *   - *d_count > cap: more than cap matches; the first cap positions and the
+ *     full count were written (what sm_sync reports as SM_ETRUNC);
+ *   - *d_count == SM_NOALLOC_TIMEOUT (UINT64_MAX): a bounded device wait
+ *     expired (a tile copy did not arrive within 1 s); the positions are
+ *     invalid (what sm_sync reports as SM_ETIMEOUT).
  * Errors: SM_EINVAL as sm_report, and when the text has more than
  * SM_NOALLOC_MAX_STARTS start positions (n - m + 1), the number of tiles
- * whose per-tile counts the array holds; SM_ECUDA when a CUDA call fails.
+ * whose per-tile counts the array holds; SM_ECUDA when a CUDA call fails
+ * (a failed first-call set-up is tried again by the next call).
  */
 #define SM_NOALLOC_MAX_STARTS 268435456ull   /* 16384 tiles x 16384 starts */
+#define SM_NOALLOC_TIMEOUT 0xFFFFFFFFFFFFFFFFull
 sm_status sm_report_noalloc(const uint8_t* d_text, uint64_t n, const uint8_t* h_pat, uint32_t m,
                             const uint32_t* h_pi, uint64_t* d_pos, uint64_t cap,
                             uint64_t* d_count, sm_stream_t stream);

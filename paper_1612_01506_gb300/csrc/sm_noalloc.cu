@@ -9,7 +9,8 @@
 // host heap. The kernels are the same scan kernels sm_report launches.
 //
 // Scratch layout (bytes of g_noalloc_scratch):
-//   [0, 4)        deferred status bits (written by kernels, not read back)
+//   [0, 4)        deferred status bits; after the passes a one-thread kernel
+//                 turns an expired bounded wait into *d_count = UINT64_MAX
 //   [4, 8)        last-CTA ticket (must be 0 when a call starts)
 //   [8, 16)       tile counter of the tile-count pass (must be 0 when a call starts)
 //   [256, ..)     per-CTA, then per-range partial counts, kMaxCtas x uint64
@@ -19,8 +20,8 @@
 #include "sm_internal.h"
 #include "sm_plan.h"
 
+#include <cstdlib>
 #include <cstring>
-#include <functional>
 #include <mutex>
 
 namespace {
@@ -39,7 +40,8 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 constexpr int kMaxDevices = 64;
 
 struct DeviceSetup {
-    std::once_flag once;
+    std::mutex mu;
+    bool ok = false;                    // set once the set-up succeeded; a failed one is retried
     cudaError_t err = cudaSuccess;
     unsigned char* scratch = nullptr;   // device address of g_noalloc_scratch on this device
     int num_sms = 0;
@@ -62,6 +64,22 @@ void setup_device(DeviceSetup& s, int dev) {
     if ((s.err = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return;
     s.max_smem = (size_t)v;
     s.err = smk::scan_prepare(s.max_smem);
+    s.ok = s.err == cudaSuccess;
+}
+
+// After the passes: a bounded wait that expired leaves the count and the
+// positions invalid; the caller, who has no context to ask, sees it as
+// *d_count == UINT64_MAX (no real count comes near it).
+__global__ void timeout_to_count_kernel(const uint32_t* __restrict__ status, uint64_t* __restrict__ d_count) {
+    if (*status & smk::kStatusTimeout) *d_count = ~0ull;
+}
+
+// Test hook, read at every call: SM_NOALLOC_TEST_TIMEOUT=1 makes the scan
+// never start the copy of tile 0 and gives every wait a 2 ms limit, so the
+// wait expires (without a fault) and the timeout report can be checked.
+bool test_timeout() {
+    const char* v = std::getenv("SM_NOALLOC_TEST_TIMEOUT");
+    return v && v[0] == '1';
 }
 
 }  // namespace
@@ -82,8 +100,11 @@ extern "C" sm_status sm_report_noalloc(const uint8_t* d_text, uint64_t n, const 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SM_ECUDA;
     DeviceSetup& su = g_setup[dev];
-    std::call_once(su.once, setup_device, std::ref(su), dev);
-    if (su.err != cudaSuccess) return SM_ECUDA;
+    {
+        std::lock_guard<std::mutex> lk(su.mu);
+        if (!su.ok) setup_device(su, dev);
+        if (!su.ok) return SM_ECUDA;
+    }
 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if ((uint64_t)m > n) return cudaMemsetAsync(d_count, 0, sizeof(uint64_t), s) == cudaSuccess ? SM_OK : SM_ECUDA;
@@ -129,6 +150,10 @@ extern "C" sm_status sm_report_noalloc(const uint8_t* d_text, uint64_t n, const 
     a.one = 1;
     a.d_count = d_count;
     a.spin_ns = 1000000000ull;
+    if (test_timeout()) {
+        a.test_skip_copy = 1;
+        a.spin_ns = 2000000ull;
+    }
 
     // the array keeps the previous call's contents: clear status, ticket
     // and tile counter
@@ -139,5 +164,7 @@ extern "C" sm_status sm_report_noalloc(const uint8_t* d_text, uint64_t n, const 
     a.d_pos = d_pos;
     a.cap = cap;
     if (smk::launch_scan(smk::kModeWrite, smk::kKindBytes, grid, smem, s, a, qc, groups) != cudaSuccess) return SM_ECUDA;
+    timeout_to_count_kernel<<<1, 1, 0, s>>>(a.status, d_count);
+    if (cudaGetLastError() != cudaSuccess) return SM_ECUDA;
     return SM_OK;
 }

@@ -6,10 +6,16 @@ the next chunk for all active queries in one batched launch
 A query is admitted whenever a counter slot is free -- it joins at whatever
 chunk comes next -- and its count is complete after one step on every chunk.
 A report query then needs a position buffer of exactly count x 8 bytes and is
-admitted when the report memory budget has room. Its positions are written on
+admitted when both the report budget and the device's free memory (what the
+driver reports free plus what torch's allocator holds unused, minus a reserve)
+have room; one that can never fit is answered with an error instead. Its
+positions are written on
 a second stream while the next steps run: by ``sm_report`` alone, or, when at
 least ``report_batch_min`` report queries wait, together with them in one
 batched report over the text (``sm_stepper_report``).
+
+A query that arrives while the server is idle runs at once as one
+single-pattern search over the whole text (``sm_count``), as it would alone.
 
 Every query's result is the same as when it runs alone (the tests check
 this against single calls and the CPU oracle).
@@ -35,6 +41,8 @@ class Query:
     positions: object = None       # device tensor (int64) for reports
     done: float | None = None
     qid: int = -1
+    error: str | None = None       # a report that could not be admitted
+    alone: bool = False            # counted by a single search at an idle server
 
     @property
     def latency(self) -> float:
@@ -73,7 +81,8 @@ class Server:
     """Continuous-batching server over the resident uint8 CUDA tensor `text`."""
 
     def __init__(self, text, chunk_bytes: int = 256 << 20, max_m: int = 2048, max_active: int = 1024,
-                 report_budget: int = 8 << 30, burst_below: int = 4, report_batch_min: int = 32):
+                 report_budget: int = 8 << 30, burst_below: int = 4, report_batch_min: int = 32,
+                 memory_reserve: int = 1 << 30):
         import torch
         self.torch = torch
         self.text = text
@@ -107,6 +116,8 @@ class Server:
         self.report_wait: collections.deque[Query] = collections.deque()
         self.reporting: list = []                 # (event, query, bytes)
         self.report_budget = report_budget
+        # device memory kept free of report buffers (workspace growth, other users)
+        self.memory_reserve = memory_reserve
         # with at least this many report queries waiting they are reported in
         # one batched pass; fewer run one report each (a batched pass holds
         # every SM for its whole length, which delays the count steps)
@@ -137,6 +148,11 @@ class Server:
     # ------------------------------------------------------------ one step
     def step(self):
         torch = self.torch
+        if (len(self.pending) == 1 and not self.active and not self.finishing and self.free_slots
+                and not self.reporting and not self.report_wait):
+            self._run_alone(self.pending.popleft())
+            self._poll()
+            return
         # admission: a free counter slot per query
         while self.pending and self.free_slots:
             q = self.pending.popleft()
@@ -178,16 +194,39 @@ class Server:
                 finished.append(ent[0])
                 del self.active[slot]
         if finished:
-            with torch.cuda.stream(self.stream):
+            self._finish(finished)
+        self.next_chunk = (self.next_chunk + done_chunks) % self.nchunks
+        self.steps += 1
+
+    def _finish(self, finished: list):
+        """Read the final counts of `finished` back to the host (on the step
+        stream, after the work enqueued so far)."""
+        torch = self.torch
+        with torch.cuda.stream(self.stream):
+            if len(finished) <= 4:   # a few copies into the pinned mirror
+                for q in finished:
+                    self.host_counters[q.qid].copy_(self.counters[q.qid], non_blocking=True)
+                host = None
+            else:
                 idx = torch.tensor([q.qid for q in finished], dtype=torch.int64).pin_memory().to(
                     self.dev, non_blocking=True)
                 vals = self.counters.index_select(0, idx)
                 host = torch.empty(len(finished), dtype=torch.int64).pin_memory()
                 host.copy_(vals, non_blocking=True)
-            ev = torch.cuda.Event()
-            ev.record(self.stream)
-            self.finishing.append((ev, finished, host))
-        self.next_chunk = (self.next_chunk + done_chunks) % self.nchunks
+        ev = torch.cuda.Event()
+        ev.record(self.stream)
+        self.finishing.append((ev, finished, host))
+
+    def _run_alone(self, q: Query):
+        """An arrival at an idle server: one single-pattern count over the
+        whole text, planned under the text's own frequencies, as the query
+        would run alone."""
+        slot = self.free_slots.pop()
+        q.qid = slot
+        sm.sm_count(self.ctx, self.text, q.pattern, pi=sm.sm_order(q.pattern, self.hist), hist=self.hist,
+                    out=self.counters[slot:slot + 1], stream=self.stream)
+        q.alone = True
+        self._finish([q])
         self.steps += 1
 
     def warm_up(self, patterns: list[bytes]):
@@ -208,9 +247,11 @@ class Server:
                 keep.append((ev, qs, host))
                 continue
             now = self.now()
-            for q, c in zip(qs, host.tolist()):
+            vals = host.tolist() if host is not None else [int(self.host_counters[q.qid]) for q in qs]
+            for q, c in zip(qs, vals):
                 q.count = int(c)
-                self.lib.sm_stepper_retire(self.stepper, q.qid)
+                if not getattr(q, "alone", False):
+                    self.lib.sm_stepper_retire(self.stepper, q.qid)
                 self.free_slots.append(q.qid)
                 if q.kind == "report":
                     self.report_wait.append(q)
@@ -236,8 +277,10 @@ class Server:
         while self.report_wait and len(self.report_wait) < self.report_batch_min:
             q = self.report_wait[0]
             need = max(q.count, 1) * 8
-            if self.report_reserved and self.report_reserved + need > self.report_budget:
+            if not self._admit(q, need, self._room()):
                 break
+            if q.error:
+                continue
             self.report_wait.popleft()
             self.report_reserved += need
             with torch.cuda.stream(self.rstream):
@@ -250,19 +293,54 @@ class Server:
             q.positions = pos[: q.count]
             self.reporting.append((ev, [q], need, False))
 
+    def _room(self) -> int:
+        """Bytes a new report buffer may take now: what is left of the report
+        budget, and the device memory free for it -- the driver's free bytes
+        plus what torch's caching allocator holds unused, minus the reserve."""
+        torch = self.torch
+        free, _ = torch.cuda.mem_get_info(self.dev)
+        cached = torch.cuda.memory_reserved(self.dev) - torch.cuda.memory_allocated(self.dev)
+        return min(self.report_budget - self.report_reserved, free + cached - self.memory_reserve)
+
+    def _admit(self, q: Query, need: int, room: int) -> bool:
+        """Whether the report at the head of the wait queue may go on: True
+        when it fits `room`; a report that never can (above the budget, or
+        above the free memory with no report in flight to give any back) is
+        answered with an error and taken off the queue (also True); False
+        when it has to wait for reports in flight."""
+        if need <= room:
+            return True
+        if need > self.report_budget or not self.report_reserved:
+            self.report_wait.popleft()
+            q.error = (f"report needs {need} bytes of positions; budget {self.report_budget}, "
+                       f"{max(room, 0)} bytes available")
+            q.done = self.now()
+            self.done.append(q)
+            return True
+        return False
+
     def _report_batch(self):
         """The waiting report queries whose position buffers (count x 8 bytes)
-        fit the memory budget, reported together in one batched pass."""
+        fit the memory budget and the free device memory, reported together
+        in one batched pass."""
         torch = self.torch
         batch, need = [], 0
+        room = self._room()
         while self.report_wait:
             q = self.report_wait[0]
             b = max(q.count, 1) * 8
-            if batch and self.report_reserved + need + b > self.report_budget:
+            if batch and need + b > room:
                 break
+            if not batch:
+                if not self._admit(q, b, room):
+                    break
+                if q.error:
+                    continue
             self.report_wait.popleft()
             batch.append(q)
             need += b
+        if not batch:
+            return
         pos_off = np.zeros(len(batch) + 1, np.int64)
         pos_off[1:] = np.cumsum([q.count for q in batch])
         pat_off = np.zeros(len(batch) + 1, np.int64)

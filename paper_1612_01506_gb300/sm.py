@@ -21,6 +21,7 @@ SM_TILE_STARTS = 16384
 SM_ORDER_H, SM_ORDER_HS = 1, 2
 SM_KNOB_STAGES, SM_KNOB_GRID, SM_KNOB_SPIN_NS, SM_KNOB_TEST_SKIP_COPY = 1, 2, 3, 4
 SM_NOALLOC_MAX_STARTS = 16384 * 16384
+SM_NOALLOC_TIMEOUT = (1 << 64) - 1   # *d_count after an expired bounded wait (int64 view: -1)
 
 # Every symbol the header declares (checked against include/sm.h by the tests).
 EXPORTS = ("sm_create", "sm_destroy", "sm_last_error", "sm_status_string", "sm_sync", "sm_set_knob",

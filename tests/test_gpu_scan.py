@@ -271,3 +271,33 @@ def test_full_size_1gib(torch, ctx, kind):
     assert st == sm.SM_OK and c == want and np.array_equal(pos, want_pos)
     del text
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("kind", [2, 4, 20, "markov95"])
+def test_full_size_dense_report(torch, ctx, kind):
+    """Reports of short patterns at n = 1 GiB, where matches are densest
+    (sigma = 2, m = 2: about n/4 positions), in the launch configuration the
+    sweep uses (text histogram, rarest-first order). Every position is
+    compared with the threaded oracle, streamed over 128 MiB windows of the
+    text (each with its (m - 1)-byte halo)."""
+    n = 1 << 30
+    t = synth.text(kind, n, seed=0, stream=synth.stream_id("sweep", kind))
+    text = torch.from_numpy(t).cuda()
+    hist = oracle.histogram(t)
+    for m in (2, 4):
+        p = synth.sample_patterns(t, m, 1, seed=0, stream=synth.stream_id("pat", kind, m))[0]
+        want = oracle.count_threads(p, t)
+        pos, cnt = sm.sm_report(ctx, text, p, want, pi=sm.sm_order(p, hist), hist=hist)
+        assert sm.sm_sync(ctx) == sm.SM_OK
+        assert int(cnt.item()) == want
+        win, off = 128 << 20, 0
+        for a in range(0, n - m + 1, win):
+            b = min(a + win, n - m + 1)            # starts [a, b)
+            wp, wc = oracle.report_threads(p, t[a:b + m - 1], b - a)
+            got = pos[off:off + wc].cpu().numpy().view(np.uint64)
+            assert np.array_equal(got, wp + np.uint64(a)), (kind, m, a)
+            off += wc
+        assert off == want
+        del pos
+    del text
+    torch.cuda.empty_cache()

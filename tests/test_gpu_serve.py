@@ -43,7 +43,7 @@ def test_serving_results_equal_alone(torch, report_batch_min):
     from paper_1612_01506_gb300.serve import Server
     t = make_text(3 << 20)
     text = torch.from_numpy(t).cuda()
-    server = Server(text, chunk_bytes=1 << 20, max_m=2048, max_active=16, report_budget=1 << 20, burst_below=4,
+    server = Server(text, chunk_bytes=1 << 20, max_m=2048, max_active=16, report_budget=1 << 26, burst_below=4,
                     report_batch_min=report_batch_min)
     assert server.nchunks == 6
     qs = make_queries(t, 60, seed=1)
@@ -183,3 +183,49 @@ def test_stepper_steps_chunk_ranges(torch):
             assert got[q] == want, (q, first, spans[q])
         for q in range(len(pats)):
             server.lib.sm_stepper_retire(server.stepper, q)
+
+
+def test_serving_report_admission(torch):
+    """Report buffers are admitted by the budget and by the device's free
+    memory: a report whose positions exceed the budget, or that cannot fit
+    in free memory with nothing in flight to give memory back, is answered
+    with an error; the other queries are unaffected."""
+    from paper_1612_01506_gb300.serve import Query, Server
+    t = make_text(1 << 20)
+    text = torch.from_numpy(t).cuda()
+    small_p = t[100:124].tobytes()
+    want_small = oracle.naive_report(small_p, t)
+    server = Server(text, chunk_bytes=1 << 20, max_m=64, max_active=8, report_budget=4096)
+    big = Query(pattern=b"AC", kind="report")                 # ~n/32 matches: far above 4096 bytes
+    small = Query(pattern=small_p, kind="report", arrival=0.001)
+    cnt = Query(pattern=b"ACG", kind="count", arrival=0.002)
+    server.run([big, small, cnt])
+    assert big.error and big.positions is None and big.count == oracle.naive_count(b"AC", t)
+    assert small.error is None and small.count == want_small[1]
+    assert np.array_equal(small.positions.cpu().numpy().view(np.uint64), want_small[0])
+    assert cnt.count == oracle.naive_count(b"ACG", t)
+    # no free memory at all for positions: every report is refused, counts still run
+    total = torch.cuda.mem_get_info()[1]
+    starved = Server(text, chunk_bytes=1 << 20, max_m=64, max_active=8, memory_reserve=total)
+    q1, q2 = Query(pattern=small_p, kind="report"), Query(pattern=b"GT", kind="count")
+    starved.run([q1, q2])
+    assert q1.error and "available" in q1.error and q1.count == want_small[1]
+    assert q2.count == oracle.naive_count(b"GT", t)
+
+
+def test_serving_idle_arrival_runs_alone(torch):
+    """A query arriving at an idle server is one single search over the
+    whole text; its count equals the oracle's, and a report follows it."""
+    from paper_1612_01506_gb300.serve import Query, Server
+    t = make_text(1 << 20)
+    text = torch.from_numpy(t).cuda()
+    server = Server(text, chunk_bytes=1 << 20, max_m=64, max_active=8)
+    qs = [Query(pattern=t[i * 1000:i * 1000 + 9].tobytes(), kind=("report" if i % 2 else "count"),
+                arrival=0.02 * i) for i in range(6)]
+    server.run(qs)
+    assert all(q.alone for q in qs)
+    for q in qs:
+        pos, c = oracle.naive_report(q.pattern, t)
+        assert q.count == c
+        if q.kind == "report":
+            assert np.array_equal(q.positions.cpu().numpy().view(np.uint64), pos)

@@ -78,3 +78,49 @@ def test_noalloc_truncation_and_limits(torch):
                                2, None, out_pos.data_ptr(), cap, out_cnt.data_ptr(), None)
     assert st == sm.SM_EINVAL
     assert sm.sm_report_noalloc(text, b"", cap, out_pos, out_cnt) == sm.SM_EINVAL
+
+
+def test_noalloc_largest_text(torch):
+    """The largest text the array covers (exactly SM_NOALLOC_MAX_STARTS start
+    positions) against sm_report; one start more is rejected."""
+    m = 8
+    n = sm.SM_NOALLOC_MAX_STARTS + m - 1
+    t = synth.uniform(n, 4, seed=0, stream=synth.stream_id("noalloc", "max"))
+    text = torch.from_numpy(t).cuda()
+    ctx = sm.sm_create(0)
+    p = t[n - m:].tobytes()                    # the last start matches
+    cap = 1 << 16
+    want_pos, want = _reference(torch, ctx, text, p, cap)
+    out_pos = torch.zeros(cap, dtype=torch.int64, device="cuda")
+    out_cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    assert sm.sm_report_noalloc(text, p, cap, out_pos, out_cnt) == sm.SM_OK
+    torch.cuda.synchronize()
+    got = int(out_cnt.item())
+    assert got == want >= 1
+    assert np.array_equal(out_pos[:min(got, cap)].cpu().numpy(), want_pos)
+    if want <= cap:
+        assert int(out_pos[want - 1].item()) == n - m
+    over = torch.empty(n + 1, dtype=torch.uint8, device="cuda")   # one start over the limit
+    assert sm.sm_report_noalloc(over, p, cap, out_pos, out_cnt) == sm.SM_EINVAL
+
+
+def test_noalloc_timeout_is_reported(torch, monkeypatch):
+    """An expired bounded wait shows as *d_count == SM_NOALLOC_TIMEOUT. The
+    test hook never starts the first tile's copy and gives each wait 2 ms,
+    so the wait runs out without any fault; the next call is correct."""
+    t = synth.uniform(1 << 20, 4, seed=0, stream=7)
+    text = torch.from_numpy(t).cuda()
+    p = t[100:108].tobytes()
+    cap = 1024
+    out_pos = torch.zeros(cap, dtype=torch.int64, device="cuda")
+    out_cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    monkeypatch.setenv("SM_NOALLOC_TEST_TIMEOUT", "1")
+    assert sm.sm_report_noalloc(text, p, cap, out_pos, out_cnt) == sm.SM_OK
+    torch.cuda.synchronize()
+    assert int(out_cnt.item()) & ((1 << 64) - 1) == sm.SM_NOALLOC_TIMEOUT
+    monkeypatch.delenv("SM_NOALLOC_TEST_TIMEOUT")
+    want_pos, want = oracle.naive_report(p, t)
+    assert sm.sm_report_noalloc(text, p, cap, out_pos, out_cnt) == sm.SM_OK
+    torch.cuda.synchronize()
+    assert int(out_cnt.item()) == want
+    assert np.array_equal(out_pos[:want].cpu().numpy().view(np.uint64), want_pos)

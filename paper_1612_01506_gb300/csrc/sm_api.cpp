@@ -35,6 +35,8 @@ struct sm_ctx {
     size_t warp_counts_cap = 0;       // entries
     uint32_t* d_bitmaps = nullptr;    // report: per-(tile, warp) found bitmaps
     size_t bitmaps_cap = 0;           // words
+    uint2* d_tile_list = nullptr;     // rescanning report: tiles with matches, per range
+    size_t tile_list_cap = 0;         // entries
     uint32_t stages = 4;
     bool stages_fixed = false;        // set by SM_KNOB_STAGES; otherwise fewer stages may raise occupancy
     uint32_t grid_override = 0;
@@ -118,6 +120,7 @@ struct Plan {
     int kind = smk::kKindBytes;
     uint32_t b1 = 0, b2 = 0;        // packed kinds: the code bits
     bool zero = false;   // a pattern symbol never occurs in the text
+    double expect = -1;  // expected matches per start from the symbol frequencies (-1: unknown)
 };
 
 // Compare descriptors (e << 8) | p[q], e = (text address mod 16) + q, in the
@@ -147,7 +150,12 @@ sm_status make_plan(const uint8_t* d_text, const uint8_t* p, uint32_t m, const u
         }
         pl->kind = (high == 0) && pat7 ? smk::kKindSeven : smk::kKindBytes;
         freq.resize(m);
-        for (uint32_t j = 0; j < m; ++j) freq[j] = n ? (double)h[v[j] & 0xFFu] / (double)n : 1.0;
+        double lp = 0;
+        for (uint32_t j = 0; j < m; ++j) {
+            freq[j] = n ? (double)h[v[j] & 0xFFu] / (double)n : 1.0;
+            lp += std::log(std::max(freq[j], 1e-300));
+        }
+        pl->expect = std::exp(std::max(lp, -700.0));
         const bool codes = !pl->zero && !(o->flags & SM_SEARCH_BYTES);
         binary = codes && smk::binary_code_bit(h, &pl->b1);
         packed = codes && !binary && smk::packed_code_bits(h, &pl->b1, &pl->b2);
@@ -172,6 +180,22 @@ sm_status make_plan(const uint8_t* d_text, const uint8_t* p, uint32_t m, const u
     if (pl->r == 0) return fail(SM_EINVAL, "internal: dense plan exceeds its group capacity");
     pl->groups.resize(ng);
     return SM_OK;
+}
+
+// Which report to run: the rescan (count, then the tiles with matches again)
+// when the symbol frequencies expect matches in at most one tile in 32 (each
+// such tile is read and compared twice, and the CTA with the most of them
+// sets the second pass's length), else the found-bits passes. SM_REPORT=rescan
+// or SM_REPORT=bits forces one of them.
+bool report_rescans(const Plan& pl, uint64_t nstarts, uint64_t ntiles) {
+    const char* f = std::getenv("SM_REPORT");
+    if (f && std::strcmp(f, "rescan") == 0) return true;
+    if (f && std::strcmp(f, "bits") == 0) return false;
+    if (pl.expect < 0) return false;
+    const double matches = pl.expect * (double)nstarts;
+    // tiles with at least one match, matches spread at random
+    const double tiles = (double)ntiles * -std::expm1(-matches / (double)ntiles);
+    return tiles * 32.0 <= (double)ntiles;
 }
 
 struct Grid {
@@ -324,6 +348,7 @@ void sm_destroy(sm_ctx* c) {
     if (c->d_partials) cudaFree(c->d_partials);
     if (c->d_warp_counts) cudaFree(c->d_warp_counts);
     if (c->d_bitmaps) cudaFree(c->d_bitmaps);
+    if (c->d_tile_list) cudaFree(c->d_tile_list);
     delete c;
 }
 
@@ -439,25 +464,50 @@ static sm_status search(sm_ctx* c, const uint8_t* d_text, uint64_t n, const uint
     if (pl.zero) return zero_count(d_count, s);
 
     const uint64_t nstarts = n - m + 1;
-    const int mode1 = report ? smk::kModeTileCount : smk::kModeCount;
+    const uint64_t ntiles = (nstarts + smk::kTile - 1) / smk::kTile;
+    const bool rescan = report && report_rescans(pl, nstarts, ntiles);
+    const int mode1 = !report ? smk::kModeCount : rescan ? smk::kModeSparse : smk::kModeTileCount;
     Grid gr;
-    st = plan_grid(c, mode1, pl.kind, report, m, nstarts, &gr);
+    st = plan_grid(c, mode1, pl.kind, report && !rescan, m, nstarts, &gr);
     if (st != SM_OK) return st;
     const uint64_t wranges = std::max<uint64_t>(1, std::min<uint64_t>(gr.ntiles, 4ull * (uint64_t)c->num_sms));
     if (report) {
-        st = grow(&c->d_partials, &c->partials_cap, std::max<size_t>((size_t)wranges, 256), "partials");
+        st = grow(&c->d_partials, &c->partials_cap,
+                  std::max<size_t>((size_t)std::max<uint64_t>(wranges, gr.grid), 256), "partials");
         if (st != SM_OK) return st;
         st = grow(&c->d_warp_counts, &c->warp_counts_cap, (size_t)gr.ntiles * smk::kConsumerWarps,
                   "per-warp tile counts");
         if (st != SM_OK) return st;
-        st = grow(&c->d_bitmaps, &c->bitmaps_cap, (size_t)gr.ntiles * smk::kConsumerWarps * smk::kBitmapWords,
-                  "found bitmaps");
-        if (st != SM_OK) return st;
+        if (!rescan) {
+            st = grow(&c->d_bitmaps, &c->bitmaps_cap, (size_t)gr.ntiles * smk::kConsumerWarps * smk::kBitmapWords,
+                      "found bitmaps");
+            if (st != SM_OK) return st;
+        } else {
+            st = grow(&c->d_tile_list, &c->tile_list_cap, (size_t)gr.ntiles, "tile list");
+            if (st != SM_OK) return st;
+        }
     }
     smk::ScanArgs a = scan_args(c, d_text, n, m, pl, gr, d_count);
     cudaError_t e;
-    // a report: the tile-count pass (per-warp-tile counts and found
-    // bitmaps), the per-range counts, then the positions from the bitmaps
+    if (rescan) {
+        // few tiles hold matches: count, noting the warp-tiles with matches,
+        // then scan those tiles again and write their positions
+        e = cudaMemsetAsync(c->d_warp_counts, 0, (size_t)gr.ntiles * smk::kConsumerWarps * sizeof(uint32_t), s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+        e = smk::launch_scan(mode1, pl.kind, gr.grid, gr.smem, s, a, pl.qc.data(), pl.groups.data());
+        if (e != cudaSuccess) return cuda_fail(e, "scan launch");
+        e = smk::launch_range_sums(gr.grid, s, c->d_warp_counts, gr.ntiles, gr.per_cta, c->d_partials,
+                                   c->d_tile_list);
+        if (e != cudaSuccess) return cuda_fail(e, "range count launch");
+        a.d_pos = d_pos;
+        a.cap = cap;
+        a.tile_list = c->d_tile_list;
+        e = smk::launch_scan(smk::kModeWrite, pl.kind, gr.grid, gr.smem, s, a, pl.qc.data(), pl.groups.data());
+        return e == cudaSuccess ? SM_OK : cuda_fail(e, "report launch");
+    }
+    // a report with matches in many tiles: the tile-count pass (per-warp-tile
+    // counts and found bits), the per-range counts, then the positions from
+    // the found bits
     if (report) a.bitmaps = c->d_bitmaps;
     e = smk::launch_scan(mode1, pl.kind, gr.grid, gr.smem, s, a, pl.qc.data(), pl.groups.data());
     if (e != cudaSuccess) return cuda_fail(e, "scan launch");
@@ -477,6 +527,7 @@ static sm_status search(sm_ctx* c, const uint8_t* d_text, uint64_t n, const uint
         w.d_pos = d_pos;
         w.cap = cap;
         w.status = c->d_status;
+        w.folded = smk::kind_packed(pl.kind) ? 0u : 1u;
         e = smk::launch_bitmap_write(wgrid, s, w);
         if (e != cudaSuccess) return cuda_fail(e, "report launch");
     }

@@ -387,35 +387,60 @@ struct GlobalQC {
 constexpr uint32_t kLaneCompares = 16;
 
 // Found bits of a warp-tile with matches, as the tile-count pass of a report
-// stores them in the warp-tile's 64-word slot. Chunk k (k = 0..127) is
-// starts 16k .. 16k + 15 of the warp-tile, its mask has bit b for start
-// 16k + b. List form: when at most kListMax chunks have a match, one word
-// (k << 16) | mask per such chunk, ascending k, from word 0 (the slot's
-// other words are not written). Bitmap form otherwise: the 128 masks, chunk
-// k in the low (k even) or high half of word k / 2. The per-(tile, warp)
-// count word tells them apart: matches in bits 0-15, the number of list
-// words in bits 16-23 (0: bitmap form).
-constexpr uint32_t kListMax = kBitmapWords;
+// stores them in the warp-tile's 64-word slot: one 64-bit entry per lane,
+// lane l's entry in the layout of the compare kind --
+//   byte compares (folded): lane l's chunks 32c + l (c = 0..3, chunk k =
+//     starts 16k .. 16k + 15 of the warp-tile) as the two words the count
+//     folds anyway: word h = c >> 1 has bit 7 - (4 (c & 1) + i) + 8b for
+//     start 16 (32c + l) + 4i + b;
+//   coded compares (contiguous): lane l's starts 64l .. 64l + 63, bit s of
+//     the entry (low word first) for start 64l + s.
+// List form, when at most kListMax lanes have a match: word 0 holds the
+// ballot of the lanes with a match (words 1-3 are zero), and the j-th lane
+// with a match (ascending) has its entry at words 4 + 2j, 5 + 2j; the slot's
+// other words are not written. Bitmap form otherwise: lane l's entry at
+// words 2l, 2l + 1. The per-(tile, warp) count word tells them apart:
+// matches in bits 0-15, the number of list entries in bits 16-23 (0: bitmap
+// form). Pass 1 only stores words it has; pass 2 reorders them into
+// positions.
+constexpr uint32_t kListMax = kBitmapWords / 2 - 2;   // 30
 constexpr uint32_t kCountMask = 0xFFFFu;
 
-// Lane l holds the masks of chunks 4l .. 4l + 3 in c[0..3]: store the
-// warp-tile's slot in the form that fits and return the list length (0 for
-// the bitmap form). All lanes take part.
-__device__ __forceinline__ uint32_t store_found_lanes(uint32_t* __restrict__ bm, uint32_t lane,
-                                                      const uint32_t (&c)[4]) {
-    const uint32_t nz = (uint32_t)(c[0] != 0u) + (uint32_t)(c[1] != 0u) + (uint32_t)(c[2] != 0u) +
-                        (uint32_t)(c[3] != 0u);
-    const uint32_t inc = warp_incl_scan(nz, lane);
-    const uint32_t tot = __shfl_sync(kFull, inc, 31);
-    if (tot <= kListMax) {
-        uint32_t o = inc - nz;
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-            if (c[i]) bm[o++] = ((4u * lane + (uint32_t)i) << 16) | c[i];
-        return tot;
+// Lane entries (x, y) -> the warp-tile's slot in the form that fits; returns
+// the list length (0: bitmap form). All lanes take part.
+__device__ __forceinline__ uint32_t store_slot(uint32_t* __restrict__ bm, uint32_t lane, uint32_t x, uint32_t y) {
+    const bool nz = (x | y) != 0u;
+    const uint32_t bal = __ballot_sync(kFull, nz);
+    const uint32_t nl = __popc(bal);
+    uint2* b2 = reinterpret_cast<uint2*>(bm);
+    if (nl <= kListMax) {
+        if (nz) b2[2 + __popc(bal & ((1u << lane) - 1u))] = make_uint2(x, y);
+        if (lane == 0) reinterpret_cast<uint4*>(bm)[0] = make_uint4(bal, 0u, 0u, 0u);
+        return nl;
     }
-    reinterpret_cast<uint2*>(bm)[lane] = make_uint2(c[0] | (c[1] << 16), c[2] | (c[3] << 16));
+    b2[lane] = make_uint2(x, y);
     return 0;
+}
+
+// The two folded words of a lane's NC = 4 chunks of found flags (bit 7 of
+// each byte): word h ORs f[2h][i] >> i and f[2h + 1][i] >> (4 + i), whose
+// flags land on distinct bits. Their popcounts sum to the lane's matches.
+__device__ __forceinline__ void fold_found(const uint32_t (&f)[kChunks][4], uint32_t& x0, uint32_t& x1) {
+    x0 = ((f[0][0] | (f[0][1] >> 1)) | ((f[0][2] >> 2) | (f[0][3] >> 3))) |
+         (((f[1][0] >> 4) | (f[1][1] >> 5)) | ((f[1][2] >> 6) | (f[1][3] >> 7)));
+    x1 = ((f[2][0] | (f[2][1] >> 1)) | ((f[2][2] >> 2) | (f[2][3] >> 3))) |
+         (((f[3][0] >> 4) | (f[3][1] >> 5)) | ((f[3][2] >> 6) | (f[3][3] >> 7)));
+}
+
+// Chunk c's flags in a folded word x (x is the lane's word c >> 1) -> 16
+// bits in start order (bit 4i + b for start 4i + b of the chunk).
+__device__ __forceinline__ uint32_t unfold_chunk(uint32_t x, uint32_t c) {
+    // nibble of byte b: bit 3 - i for start 4i + b (c odd: low nibbles)
+    const uint32_t n = (c & 1u) ? (x & 0x0F0F0F0Fu) : ((x >> 4) & 0x0F0F0F0Fu);
+    // reverse each nibble: bit i + 8b for start 4i + b, then transpose
+    const uint32_t q = ((n & 0x01010101u) << 3) | ((n & 0x02020202u) << 1) | ((n >> 1) & 0x02020202u) |
+                       ((n >> 3) & 0x01010101u);
+    return chunk_mask16(q);
 }
 
 template <bool SEVEN, bool WRITE, bool DIRECT, class QC>
@@ -464,37 +489,14 @@ __device__ __forceinline__ uint32_t warp_tile(const uint4* __restrict__ b4, cons
     }
 
     if (DIRECT && r >= m) {
-        // every compare peeled: the found bits are final. With bm, store the
-        // slot of a warp-tile with matches (chunk k = 32c + lane): the list
-        // of its chunks with matches (ballots in chunk order), or the
-        // bitmap when more than kListMax chunks have one
-        const uint32_t cnt = count_flags<kChunks>(f);
+        // every compare peeled: the found bits are final. With bm, a
+        // warp-tile with matches stores its lanes' folded words
+        uint32_t x0, x1;
+        fold_found(f, x0, x1);
+        const uint32_t cnt = __popc(x0) + __popc(x1);
         if (bm && __any_sync(kFull, cnt != 0u)) {
-            uint32_t bal[kChunks], tot = 0;
-#pragma unroll
-            for (int c = 0; c < kChunks; ++c) {
-                bal[c] = __ballot_sync(kFull, ((f[c][0] | f[c][1]) | (f[c][2] | f[c][3])) != 0u);
-                tot += __popc(bal[c]);
-            }
-            const uint32_t lt = (1u << lane) - 1u;
-            if (tot <= kListMax) {
-                uint32_t o = 0;
-#pragma unroll
-                for (int c = 0; c < kChunks; ++c) {
-                    if ((bal[c] >> lane) & 1u)
-                        bm[o + __popc(bal[c] & lt)] =
-                            ((32u * c + lane) << 16) | chunk_mask16(((f[c][0] >> 7) | (f[c][1] >> 6)) |
-                                                                    ((f[c][2] >> 5) | (f[c][3] >> 4)));
-                    o += __popc(bal[c]);
-                }
-            } else {
-                uint16_t* bm16 = reinterpret_cast<uint16_t*>(bm);
-#pragma unroll
-                for (int c = 0; c < kChunks; ++c)
-                    bm16[32 * c + lane] = (uint16_t)chunk_mask16(((f[c][0] >> 7) | (f[c][1] >> 6)) |
-                                                                 ((f[c][2] >> 5) | (f[c][3] >> 4)));
-            }
-            if (ent) *ent = tot <= kListMax ? tot : 0u;
+            const uint32_t e = store_slot(bm, lane, x0, x1);
+            if (ent) *ent = e;
         }
         return cnt;
     }
@@ -521,14 +523,13 @@ __device__ __forceinline__ uint32_t warp_tile(const uint4* __restrict__ b4, cons
         }
         qn += (tot >> (8 * c)) & 0xFFu;
     }
-    if (bm) {   // the warp-tile's found bitmap, one 16-bit mask per chunk, starts at zero
+    if (bm) {   // the lanes' folded words of the surviving chunks' final flags, from zero
         sbm[2 * lane] = 0u;
         sbm[2 * lane + 1] = 0u;
     }
     __syncwarp();
 
     uint32_t tile_count = 0;   // this lane's share of the warp's matches in the tile
-    uint32_t nlist = 0;        // bm: chunks with matches so far
     for (uint32_t qb = 0; qb < qn; qb += 32) {
         const uint32_t e = qb + lane;
         uint32_t g[4] = {0u, 0u, 0u, 0u}, k = 0;
@@ -567,17 +568,12 @@ __device__ __forceinline__ uint32_t warp_tile(const uint4* __restrict__ b4, cons
             }
         }
         const uint32_t n = (__popc(g[0]) + __popc(g[1])) + (__popc(g[2]) + __popc(g[3]));
-        if (bm) {
-            // chunk k's 16 found bits in start order: into the list (entries
-            // come in chunk order) while it fits, and into the bitmap
-            const uint32_t bal = __ballot_sync(kFull, n != 0u);
-            if (n) {
-                const uint32_t mk = chunk_mask16(((g[0] >> 7) | (g[1] >> 6)) | ((g[2] >> 5) | (g[3] >> 4)));
-                const uint32_t o = nlist + __popc(bal & ((1u << lane) - 1u));
-                if (o < kListMax) bm[o] = (k << 16) | mk;
-                reinterpret_cast<uint16_t*>(sbm)[k] = (uint16_t)mk;
-            }
-            nlist += __popc(bal);
+        if (bm && n) {
+            // chunk k = 32c + l's flags into lane l's folded word c >> 1 (its
+            // own bits; another lane may set the word's other half)
+            const uint32_t sh = 4u * ((k >> 5) & 1u);
+            atomicOr(&sbm[2u * (k & 31u) + (k >> 6)],
+                     ((g[0] >> sh) | (g[1] >> (sh + 1))) | ((g[2] >> (sh + 2)) | (g[3] >> (sh + 3))));
         }
         if (WRITE) {
             const uint32_t inc = warp_incl_scan(n, lane);
@@ -598,12 +594,11 @@ __device__ __forceinline__ uint32_t warp_tile(const uint4* __restrict__ b4, cons
             tile_count += n;
         }
     }
-    __syncwarp();   // the queue is reused by the next tile
-    if (bm && nlist > kListMax) {   // too many chunks with matches for the list: the bitmap
-        bm[2 * lane] = sbm[2 * lane];
-        bm[2 * lane + 1] = sbm[2 * lane + 1];
+    __syncwarp();   // the queue is reused by the next tile; sbm is complete
+    if (bm && __any_sync(kFull, tile_count != 0u)) {
+        const uint32_t e = store_slot(bm, lane, sbm[2 * lane], sbm[2 * lane + 1]);
+        if (ent) *ent = e;
     }
-    if (bm && ent) *ent = nlist <= kListMax ? nlist : 0u;
     return tile_count;
 }
 
@@ -778,12 +773,12 @@ __device__ __forceinline__ uint2 packed_tiles(const uint32_t* const (&pk)[2], bo
 #pragma unroll
     for (int t = 0; t < NT; ++t)
         if (bm[t] && __any_sync(kFull, n[t] != 0u)) {
-            // the warp-tile's slot: lane l's 64 starts are chunks 4l .. 4l + 3
-            // (found bit 2k of a packed word -> bit k)
+            // the warp-tile's slot: lane l's 64 starts in order (found bit
+            // 2k of a packed word -> bit k)
             uint32_t c[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) c[i] = compress_even(f[t][i]);
-            const uint32_t e = store_found_lanes(bm[t], lane, c);
+            const uint32_t e = store_slot(bm[t], lane, c[0] | (c[1] << 16), c[2] | (c[3] << 16));
             if (ent) ent[t] = e;
         }
     if (WRITE) {
@@ -947,9 +942,8 @@ __device__ __forceinline__ uint2 binary_tiles(const uint32_t* const (&pk)[2], bo
     for (int t = 0; t < 2; ++t) n[t] = __popc(f[t][0]) + __popc(f[t][1]);
 #pragma unroll
     for (int t = 0; t < 2; ++t)
-        if (bm[t] && __any_sync(kFull, n[t] != 0u)) {   // lane l's 64 starts are chunks 4l .. 4l + 3
-            const uint32_t c[4] = {f[t][0] & 0xFFFFu, f[t][0] >> 16, f[t][1] & 0xFFFFu, f[t][1] >> 16};
-            const uint32_t e = store_found_lanes(bm[t], lane, c);
+        if (bm[t] && __any_sync(kFull, n[t] != 0u)) {   // lane l's 64 starts in order: its found words
+            const uint32_t e = store_slot(bm[t], lane, f[t][0], f[t][1]);
             if (ent) ent[t] = e;
         }
     if (WRITE) {

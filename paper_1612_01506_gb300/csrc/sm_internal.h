@@ -38,8 +38,12 @@ enum ScanMode : int {
     kModeCount = 0,      // count only: per-CTA partial counts, last CTA writes *d_count
     kModeTileCount = 1,  // as kModeCount, and per-(tile, warp) counts (and found bitmaps) for a
                          // report
-    kModeWrite = 2       // report: write ascending positions of tiles with matches; CTA b owns
+    kModeWrite = 2,      // report: write ascending positions of tiles with matches; CTA b owns
                          // tile range b (partials: per-range counts from launch_range_sums)
+    kModeSparse = 3,     // as kModeCount, and the per-(tile, warp) counts that are not zero
+                         // (the array is zeroed first): the first pass of a report whose
+                         // matches fall in few tiles, which kModeWrite then scans again
+    kModes = 4
 };
 
 struct ScanArgs {
@@ -64,10 +68,11 @@ struct ScanArgs {
     unsigned long long* tile_next;  // next unclaimed tile of the counting modes (scratch, zero between launches)
     uint64_t* d_count;       // result count
     uint32_t* warp_counts;   // per-(tile, warp) counts (scratch, ntiles x 8; report only)
-    uint32_t* bitmaps;       // report: per-(tile, warp) found bitmaps (ntiles x 8 x 64 words) or null
+    uint32_t* bitmaps;       // report: per-(tile, warp) slots of found bits (ntiles x 8 x 64 words) or null
     uint64_t* d_pos;         // report output
     uint64_t cap;            // report capacity
     uint64_t spin_ns;        // limit of every bounded wait, in ns
+    const uint2* tile_list;  // write mode: per range, its tiles with matches (range_sum_kernel) or null
 };
 
 struct HistArgs {
@@ -131,15 +136,17 @@ struct WriteArgs {
     uint64_t tiles_per_cta;       // CTA b writes the tiles of range b
     const uint64_t* partials;     // per-range match counts of the first pass
     const uint32_t* warp_counts;  // per-(tile, warp) counts
-    const uint32_t* bitmaps;      // per-(tile, warp) found bitmaps
+    const uint32_t* bitmaps;      // per-(tile, warp) slots of found bits (list or bitmap form)
     uint64_t* d_pos;
     uint64_t cap;
     uint32_t* status;
+    uint32_t folded;              // 1: byte-compare slots (folded lane entries); 0: coded (contiguous)
 };
 constexpr int kWriteThreads = 32 * kConsumerWarps;
 cudaError_t launch_bitmap_write(uint32_t grid, cudaStream_t s, const WriteArgs& a);
-// Between the passes: partials[b] = matches in tiles [b T, (b + 1) T), one block per range.
+// Between the passes: partials[b] = matches in tiles [b T, (b + 1) T), one block per range;
+// with tile_list (ntiles entries), also the list of each range's tiles with matches.
 cudaError_t launch_range_sums(uint32_t grid, cudaStream_t s, const uint32_t* warp_counts, uint64_t ntiles,
-                              uint64_t tiles_per_range, uint64_t* partials);
+                              uint64_t tiles_per_range, uint64_t* partials, uint2* tile_list = nullptr);
 
 }  // namespace smk

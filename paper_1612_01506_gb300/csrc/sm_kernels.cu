@@ -91,6 +91,7 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
     if (warp == kConsumerWarps) {
         // ---------------------------------------------------------- producer
         uint64_t cursor = t_begin, running = 0;
+        uint2 lst = make_uint2(~0u, 0u);   // write mode with a tile list: 32 of its entries
         if (MODE == kModeWrite) {
             uint64_t b = 0;
             for (uint32_t i = lane; i < blockIdx.x; i += 32) b += __ldcg(A.partials + i);
@@ -123,6 +124,24 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
                 if (t < A.ntiles) {
                     tile = t;
                     if (lane == 0) claim = atomicAdd(A.tile_next, 1ull);
+                }
+            } else if (A.tile_list) {
+                // next entry of the range's list of tiles with matches; the
+                // lanes hold 32 entries at a time
+                if (cursor < t_end) {
+                    const uint32_t i = (uint32_t)(cursor - t_begin);
+                    if ((i & 31u) == 0) {
+                        const uint64_t x = cursor + lane;
+                        lst = x < t_end ? __ldcg(A.tile_list + x) : make_uint2(~0u, 0u);
+                    }
+                    const uint32_t tt = __shfl_sync(kFull, lst.x, i & 31u);
+                    if (tt != ~0u) {
+                        tile = tt;
+                        tcount = __shfl_sync(kFull, lst.y, i & 31u);
+                        ++cursor;
+                    } else {
+                        cursor = t_end;
+                    }
                 }
             } else {
                 // next tile with matches; lanes look at 4 tiles x 8 warp counts per step
@@ -259,12 +278,13 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
                 c = packed_tiles<MODE == kModeWrite, MODE != kModeWrite>(pk, two, warp, lane, ParamQC<MAXM>{&P}, m, r,
                                                                          A.ng, A.nstarts, s0, out, A.d_pos, A.cap, bm,
                                                                          ent);
-            if (MODE == kModeTileCount) {
+            if (MODE == kModeTileCount || MODE == kModeSparse) {
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
                     if (k == 1 && !two) break;
                     const uint32_t wsum = warp_sum_u32(k == 0 ? c.x : c.y);
-                    if (lane == 0) A.warp_counts[d[k].tile * kConsumerWarps + warp] = wsum | (ent[k] << 16);
+                    if (lane == 0 && (MODE == kModeTileCount || wsum))
+                        A.warp_counts[d[k].tile * kConsumerWarps + warp] = wsum | (ent[k] << 16);
                 }
             }
             my_count += c.x + c.y;
@@ -306,6 +326,11 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
             if (MODE == kModeTileCount) {
                 const uint32_t wsum = warp_sum_u32(tile_count);
                 if (lane == 0) A.warp_counts[d.tile * kConsumerWarps + warp] = wsum | (ent << 16);
+            } else if (MODE == kModeSparse) {
+                if (__any_sync(kFull, tile_count != 0u)) {
+                    const uint32_t wsum = warp_sum_u32(tile_count);
+                    if (lane == 0) A.warp_counts[d.tile * kConsumerWarps + warp] = wsum;
+                }
             }
             my_count += tile_count;
             __syncwarp();
@@ -359,28 +384,63 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
 // counts of range b (tiles [b T, (b + 1) T), T = tiles_per_range) into
 // partials[b]. The tile-count pass writes only per-warp-tile counts; a
 // per-range atomic there put every warp of the GPU on the same few
-// addresses (tiles are claimed in order) and cost up to 2x the scan.
+// addresses (tiles are claimed in order) and cost up to 2x the scan. With
+// tile_list (the rescanning report), the block also lists the range's tiles
+// with matches in order, (tile, matches) from tile_list[b T], ended by a
+// tile of ~0u when the list is shorter than the range.
 __global__ void __launch_bounds__(kWriteThreads) range_sum_kernel(const uint32_t* __restrict__ warp_counts,
                                                                   uint64_t ntiles, uint64_t tiles_per_range,
-                                                                  uint64_t* __restrict__ partials) {
-    __shared__ uint64_t red[kWriteThreads / 32];
+                                                                  uint64_t* __restrict__ partials,
+                                                                  uint2* __restrict__ tile_list) {
+    __shared__ uint32_t red[kWriteThreads / 32];
+    __shared__ uint64_t redl[kWriteThreads / 32];
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint64_t t0 = (uint64_t)blockIdx.x * tiles_per_range;
     const uint64_t t1 = min(t0 + tiles_per_range, ntiles);
-    // a tile's 8 counts are two 16-byte words
-    const uint4* src = reinterpret_cast<const uint4*>(warp_counts + t0 * kConsumerWarps);
-    const uint64_t nv = t1 > t0 ? 2 * (t1 - t0) : 0;
     uint64_t v = 0;
-    for (uint64_t i = tid; i < nv; i += kWriteThreads) {
-        const uint4 x = __ldcg(src + i);
-        v += (uint64_t)(((x.x & kCountMask) + (x.y & kCountMask)) + ((x.z & kCountMask) + (x.w & kCountMask)));
+    if (!tile_list) {
+        // a tile's 8 counts are two 16-byte words
+        const uint4* src = reinterpret_cast<const uint4*>(warp_counts + t0 * kConsumerWarps);
+        const uint64_t nv = t1 > t0 ? 2 * (t1 - t0) : 0;
+        for (uint64_t i = tid; i < nv; i += kWriteThreads) {
+            const uint4 x = __ldcg(src + i);
+            v += (uint64_t)(((x.x & kCountMask) + (x.y & kCountMask)) + ((x.z & kCountMask) + (x.w & kCountMask)));
+        }
+    } else {
+        // thread i: tile c + i of each step of kWriteThreads tiles; the tiles
+        // with matches are compacted in order (warp ballots, then the warps'
+        // counts through shared memory)
+        uint32_t listed = 0;
+        for (uint64_t c = t0; c < t1; c += kWriteThreads) {
+            const uint64_t t = c + tid;
+            uint32_t tot = 0;
+            if (t < t1) {
+                const uint4* src = reinterpret_cast<const uint4*>(warp_counts + t * kConsumerWarps);
+                const uint4 x = __ldcg(src), y = __ldcg(src + 1);
+                tot = ((x.x & kCountMask) + (x.y & kCountMask)) + ((x.z & kCountMask) + (x.w & kCountMask)) +
+                      ((y.x & kCountMask) + (y.y & kCountMask)) + ((y.z & kCountMask) + (y.w & kCountMask));
+            }
+            v += tot;
+            const uint32_t bal = __ballot_sync(kFull, tot != 0u);
+            if (lane == 0) red[warp] = __popc(bal);
+            __syncthreads();
+            uint32_t before = listed, all = 0;
+            for (uint32_t w = 0; w < kWriteThreads / 32; ++w) {
+                before += w < warp ? red[w] : 0u;
+                all += red[w];
+            }
+            if (tot) tile_list[t0 + before + __popc(bal & ((1u << lane) - 1u))] = make_uint2((uint32_t)t, tot);
+            listed += all;
+            __syncthreads();   // red is rewritten by the next step
+        }
+        if (tid == 0 && t0 + listed < t1) tile_list[t0 + listed] = make_uint2(~0u, 0u);
     }
     v = warp_sum_u64(v);
-    if (lane == 0) red[warp] = v;
+    if (lane == 0) redl[warp] = v;
     __syncthreads();
     if (tid == 0) {
         uint64_t t = 0;
-        for (int w = 0; w < kWriteThreads / 32; ++w) t += red[w];
+        for (int w = 0; w < kWriteThreads / 32; ++w) t += redl[w];
         partials[blockIdx.x] = t;
     }
 }
@@ -398,6 +458,7 @@ __global__ void __launch_bounds__(kWriteThreads) range_sum_kernel(const uint32_t
 constexpr uint32_t kWalk = 256;   // tiles per pass over shared memory (one per thread)
 constexpr uint32_t kAhead = 4;    // bitmaps in flight per warp
 constexpr uint32_t kLaneTile = 64; // warp-tiles with at most this many matches are written by one lane
+constexpr uint32_t kLaneList = 14; // ... when their slot is a list of at most this many entries (32 words)
 
 __global__ void __launch_bounds__(kWriteThreads) bitmap_write_kernel(const __grid_constant__ WriteArgs W) {
     static_assert(kWalk == kWriteThreads, "one tile per thread");
@@ -466,94 +527,144 @@ __global__ void __launch_bounds__(kWriteThreads) bitmap_write_kernel(const __gri
         auto own = [&](uint32_t k) -> uint32_t {   // matches of warp-tile (p0 + k, warp)
             return (warp + 1 < kConsumerWarps ? woff[k][warp + 1] : ttot[k]) - woff[k][warp];
         };
-        // warp-tiles with more than kLaneTile matches (front of the list) are
-        // written by the whole warp; the others (back of the list) one per lane
+        // warp-tiles in list form with at most kLaneTile matches (back of the
+        // list) are written by one lane each; the others (front of the list)
+        // by the whole warp
+        auto by_lane = [&](uint32_t k, uint32_t o) {
+            return nent[k][warp] != 0 && nent[k][warp] <= kLaneList && o <= kLaneTile;
+        };
         uint8_t* lst = list[warp];
         uint32_t cnt = 0, ns = 0;
         for (uint32_t c0 = 0; c0 < np; c0 += 32) {
             const uint32_t k = c0 + lane;
             const uint32_t o = k < np ? own(k) : 0u;
-            const uint32_t bal = __ballot_sync(kFull, o > kLaneTile);
-            const uint32_t sal = __ballot_sync(kFull, o != 0 && o <= kLaneTile);
+            const bool wl = o != 0 && !by_lane(k, o), ll = o != 0 && by_lane(k, o);
+            const uint32_t bal = __ballot_sync(kFull, wl);
+            const uint32_t sal = __ballot_sync(kFull, ll);
             const uint32_t lt = (1u << lane) - 1u;
-            if (o > kLaneTile) lst[cnt + __popc(bal & lt)] = (uint8_t)k;
-            if (o != 0 && o <= kLaneTile) lst[kWalk - 1 - (ns + __popc(sal & lt))] = (uint8_t)k;
+            if (wl) lst[cnt + __popc(bal & lt)] = (uint8_t)k;
+            if (ll) lst[kWalk - 1 - (ns + __popc(sal & lt))] = (uint8_t)k;
             cnt += __popc(bal);
             ns += __popc(sal);
         }
         __syncwarp();
         for (uint32_t g = 0; g < ns; g += 32) {
-            if (g + lane < ns) {
-                const uint32_t k = lst[kWalk - 1 - (g + lane)];
-                const uint4* bp = reinterpret_cast<const uint4*>(W.bitmaps + ((p0 + k) * kConsumerWarps + warp) *
-                                                                                 kBitmapWords);
-                const uint64_t s0 = (p0 + k) * kTile + warp * kWarpStarts;
-                uint64_t o = base + toff[k] + woff[k][warp];
-                uint32_t left = own(k);
-                const uint32_t ne = nent[k][warp];
-                // list form: one word per chunk with matches, (chunk << 16) | mask
-                for (uint32_t e0 = 0; e0 < ne; e0 += 16) {
-                    uint4 x[4];
+            // the lists (at most 32 words) of the next 32 warp-tiles into the
+            // staging area, row i (33 words) for warp-tile i: lane 8u + q
+            // copies words 4q .. 4q + 3 of warp-tile 4 st + u, so that each
+            // step covers four lists and the loads of four steps are in
+            // flight together; then lane i writes warp-tile i from there
+            const uint32_t nb = min(32u, ns - g);
+            const uint32_t q = lane & 7u;
 #pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        if (e0 + 4 * q < ne) x[q] = __ldcg(bp + e0 / 4 + q);
+            for (uint32_t h = 0; h < 8; h += 4) {
+                uint4 v[4];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const uint32_t w[4] = {x[q].x, x[q].y, x[q].z, x[q].w};
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            if (e0 + 4 * q + i >= ne) break;
-                            const uint64_t c0 = s0 + 16u * (w[i] >> 16);
-                            uint32_t fw = w[i] & 0xFFFFu;
-                            while (fw) {
-                                if (o < W.cap) W.d_pos[o] = c0 + (uint32_t)(__ffs(fw) - 1);
-                                ++o;
-                                fw &= fw - 1;
-                            }
-                        }
+                for (uint32_t st = 0; st < 4; ++st) {
+                    const uint32_t i = 4u * (h + st) + (lane >> 3);
+                    v[st] = make_uint4(0u, 0u, 0u, 0u);
+                    if (i < nb) {
+                        const uint32_t k = lst[kWalk - 1 - (g + i)];
+                        if (q < 1u + (nent[k][warp] + 1u) / 2u)
+                            v[st] = __ldcg(reinterpret_cast<const uint4*>(
+                                               W.bitmaps + ((p0 + k) * kConsumerWarps + warp) * kBitmapWords) + q);
                     }
                 }
-                if (ne) left = 0;
-                for (uint32_t q0 = 0; q0 < kBitmapWords / 4 && left; q0 += 4) {
-                    uint4 x[4];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) x[q] = __ldcg(bp + q0 + q);
+                for (uint32_t st = 0; st < 4; ++st) {
+                    uint32_t* row = stg + 33u * (4u * (h + st) + (lane >> 3)) + 4u * q;
+                    row[0] = v[st].x;
+                    row[1] = v[st].y;
+                    row[2] = v[st].z;
+                    row[3] = v[st].w;
+                }
+            }
+            __syncwarp();
+            if (lane < nb) {
+                const uint32_t k = lst[kWalk - 1 - (g + lane)];
+                const uint32_t* slot = stg + 33u * lane;
+                const uint64_t s0 = (p0 + k) * kTile + warp * kWarpStarts;
+                uint64_t o = base + toff[k] + woff[k][warp];
+                const uint32_t ne = nent[k][warp];
+                const uint4 h = make_uint4(slot[0], slot[1], slot[2], slot[3]);
+                auto put = [&](uint64_t p0s, uint32_t fw) {
+                    while (fw) {
+                        if (o < W.cap) W.d_pos[o] = p0s + (uint32_t)(__ffs(fw) - 1);
+                        ++o;
+                        fw &= fw - 1;
+                    }
+                };
+                if (W.folded) {
+                    // ascending is chunk row c, then lane, then start in the
+                    // chunk: rows[c] = the lanes with a match in row c; a
+                    // lane's entry is its rank among the lanes with a match
+                    const uint32_t M = h.x;
+                    uint32_t rows[4] = {0u, 0u, 0u, 0u};
+                    for (uint32_t j = 0, mm = M; j < ne; ++j, mm &= mm - 1u) {
+                        const uint32_t bit = mm & (0u - mm);
+                        const uint32_t x = slot[4 + 2 * j], y = slot[5 + 2 * j];
+                        rows[0] |= (x & 0xF0F0F0F0u) ? bit : 0u;
+                        rows[1] |= (x & 0x0F0F0F0Fu) ? bit : 0u;
+                        rows[2] |= (y & 0xF0F0F0F0u) ? bit : 0u;
+                        rows[3] |= (y & 0x0F0F0F0Fu) ? bit : 0u;
+                    }
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const uint32_t w[4] = {x[q].x, x[q].y, x[q].z, x[q].w};
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            uint32_t fw = w[i];
-                            while (fw) {
-                                if (o < W.cap) W.d_pos[o] = s0 + 128u * (q0 + q) + 32u * i + (uint32_t)(__ffs(fw) - 1);
-                                ++o;
-                                --left;
-                                fw &= fw - 1;
-                            }
+                    for (uint32_t c = 0; c < 4; ++c) {
+                        for (uint32_t mm = rows[c]; mm; mm &= mm - 1u) {
+                            const uint32_t sl = (uint32_t)__ffs(mm) - 1u;
+                            const uint32_t j = __popc(M & ((1u << sl) - 1u));
+                            const uint32_t x = slot[4 + 2 * j + (c >> 1)];
+                            put(s0 + 16u * (32u * c + sl), unfold_chunk(x, c));
                         }
+                    }
+                } else {
+                    uint32_t mm = h.x;
+                    for (uint32_t j = 0; j < ne; ++j) {
+                        const uint32_t sl = (uint32_t)__ffs(mm) - 1u;
+                        mm &= mm - 1u;
+                        put(s0 + 64u * sl, slot[4 + 2 * j]);
+                        put(s0 + 64u * sl + 32u, slot[5 + 2 * j]);
                     }
                 }
             }
+            __syncwarp();   // the staging area is refilled by the next group
         }
+        // whole warp: lane l loads words 2l, 2l + 1 of the slot; a list is
+        // spread back to its lanes by shuffles, folded entries are turned
+        // into lane l's 64 starts 64l .. 64l + 63 in order
         auto load = [&](uint32_t j) -> uint2 {
             return __ldcg(reinterpret_cast<const uint2*>(W.bitmaps + ((p0 + lst[j]) * kConsumerWarps + warp) *
                                                                          kBitmapWords) + lane);
         };
-        auto write = [&](uint32_t j, uint2 x) {
+        auto write = [&](uint32_t j, uint2 raw) {
             const uint32_t k = lst[j];
-            // lane l's two pieces of found bits and the start (relative to
-            // the warp-tile) of each piece's bit 0: bitmap words 2l, 2l + 1,
-            // or list words 2l, 2l + 1 (those below the list length)
             const uint32_t ne = nent[k][warp];
-            uint32_t m0 = x.x, m1 = x.y, r0 = 64u * lane, r1 = 64u * lane + 32u;
+            uint32_t ex = raw.x, ey = raw.y;
             if (ne) {
-                m0 = 2u * lane < ne ? x.x & 0xFFFFu : 0u;
-                m1 = 2u * lane + 1u < ne ? x.y & 0xFFFFu : 0u;
-                r0 = 16u * (x.x >> 16);
-                r1 = 16u * (x.y >> 16);
+                const uint32_t M = __shfl_sync(kFull, raw.x, 0);
+                const uint32_t src = 2u + __popc(M & ((1u << lane) - 1u));
+                const uint32_t tx = __shfl_sync(kFull, raw.x, src & 31u), ty = __shfl_sync(kFull, raw.y, src & 31u);
+                const bool has = (M >> lane) & 1u;
+                ex = has ? tx : 0u;
+                ey = has ? ty : 0u;
+            }
+            uint32_t m0 = ex, m1 = ey;
+            if (W.folded) {
+                // lane l's chunks 4l + i sit in entry lane (4l + i) mod 32, chunk row l / 8
+                const uint32_t c = lane >> 3;
+                uint32_t mk[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const uint32_t src = (4u * lane + (uint32_t)i) & 31u;
+                    const uint32_t xs = __shfl_sync(kFull, ex, src), ys = __shfl_sync(kFull, ey, src);
+                    mk[i] = unfold_chunk((c >> 1) ? ys : xs, c);
+                }
+                m0 = mk[0] | (mk[1] << 16);
+                m1 = mk[2] | (mk[3] << 16);
             }
             const uint32_t n = __popc(m0) + __popc(m1);
             const uint32_t inc2 = warp_incl_scan(n, lane);
+            const uint32_t r0 = 64u * lane, r1 = 64u * lane + 32u;
             staged_write(stg, lane, inc2 - n, n, own(k), (p0 + k) * kTile + warp * kWarpStarts,
                          base + toff[k] + woff[k][warp], W.d_pos, W.cap, [&](auto&& cb) {
                              uint32_t kk = 0, fw = m0;
@@ -692,6 +803,7 @@ const void* pick(int mode, int kind, uint32_t m) {
     switch (mode) {
         case kModeCount: return pick_kind<kModeCount>(kind, m);
         case kModeTileCount: return pick_kind<kModeTileCount>(kind, m);
+        case kModeSparse: return pick_kind<kModeSparse>(kind, m);
         default: return pick_kind<kModeWrite>(kind, m);
     }
 }
@@ -708,6 +820,9 @@ cudaError_t launch_scan(int mode, int kind, uint32_t grid, size_t smem, cudaStre
         case kModeTileCount:
             return small ? launch_kind<kSmallM, kModeTileCount>(kind, grid, smem, s, a, qc, groups)
                          : launch_kind<kLargeM, kModeTileCount>(kind, grid, smem, s, a, qc, groups);
+        case kModeSparse:
+            return small ? launch_kind<kSmallM, kModeSparse>(kind, grid, smem, s, a, qc, groups)
+                         : launch_kind<kLargeM, kModeSparse>(kind, grid, smem, s, a, qc, groups);
         default:
             return small ? launch_kind<kSmallM, kModeWrite>(kind, grid, smem, s, a, qc, groups)
                          : launch_kind<kLargeM, kModeWrite>(kind, grid, smem, s, a, qc, groups);
@@ -722,7 +837,7 @@ int scan_occupancy(int mode, int kind, uint32_t m, size_t smem) {
 }
 
 cudaError_t scan_prepare(size_t max_smem) {
-    for (int mode = 0; mode < 3; ++mode)
+    for (int mode = 0; mode < kModes; ++mode)
         for (int kind = 0; kind < kKinds; ++kind)
             for (uint32_t m : {1u, (uint32_t)kLargeM}) {
                 cudaError_t e = cudaFuncSetAttribute(pick(mode, kind, m),
@@ -733,8 +848,8 @@ cudaError_t scan_prepare(size_t max_smem) {
 }
 
 cudaError_t launch_range_sums(uint32_t grid, cudaStream_t s, const uint32_t* warp_counts, uint64_t ntiles,
-                              uint64_t tiles_per_range, uint64_t* partials) {
-    range_sum_kernel<<<grid, kWriteThreads, 0, s>>>(warp_counts, ntiles, tiles_per_range, partials);
+                              uint64_t tiles_per_range, uint64_t* partials, uint2* tile_list) {
+    range_sum_kernel<<<grid, kWriteThreads, 0, s>>>(warp_counts, ntiles, tiles_per_range, partials, tile_list);
     return cudaGetLastError();
 }
 

@@ -115,8 +115,16 @@ def test_packed_peel_and_order(torch, ctx, name):
                     assert count(ctx, text, p, pi=pi, peel=peel, hist=hist) == want, (m, peel)
 
 
+@pytest.fixture(params=["auto", "rescan", "bits"])
+def report_mode(request, monkeypatch):
+    """Both report designs (SM_REPORT forces one; auto is the library's choice)."""
+    if request.param != "auto":
+        monkeypatch.setenv("SM_REPORT", request.param)
+    return request.param
+
+
 @pytest.mark.parametrize("name", list(ALPHABETS))
-def test_packed_report(torch, ctx, name):
+def test_packed_report(torch, ctx, name, report_mode):
     alpha = ALPHABETS[name]
     n = 4 * TILE + 1234
     t = text_over(alpha, n, 31)
@@ -131,7 +139,7 @@ def test_packed_report(torch, ctx, name):
                 assert st == sm.SM_OK and c == want and np.array_equal(pos, want_pos), (name, m, kw)
 
 
-def test_packed_absent_symbol_and_truncation(torch, ctx):
+def test_packed_absent_symbol_and_truncation(torch, ctx, report_mode):
     t = text_over(b"ACGT", 3 * TILE + 5, 41)
     hist = oracle.histogram(t)
     text = to_dev(torch, t, 0)

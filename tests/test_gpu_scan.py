@@ -190,8 +190,17 @@ def test_seven_bit_and_absent_symbol(torch, ctx):
 
 # ------------------------------------------------------------------ report
 
+@pytest.fixture(params=["auto", "rescan", "bits"])
+def report_mode(request, monkeypatch):
+    """Both report designs: the library's choice, the rescan of the tiles with
+    matches, and the passes over found bits (SM_REPORT forces one)."""
+    if request.param != "auto":
+        monkeypatch.setenv("SM_REPORT", request.param)
+    return request.param
+
+
 @pytest.mark.parametrize("kind", ["ones", 2, 4, 20, "markov95", 256])
-def test_report_parity(torch, ctx, kind):
+def test_report_parity(torch, ctx, kind, report_mode):
     n = 9 * TILE + 1234
     t = host_text(kind, n, 21)
     text = to_dev(torch, t, 9)
@@ -205,7 +214,7 @@ def test_report_parity(torch, ctx, kind):
                 assert st == sm.SM_OK and c == want and np.array_equal(pos, want_pos), (kind, m)
 
 
-def test_report_truncation(torch, ctx):
+def test_report_truncation(torch, ctx, report_mode):
     t = synth.uniform(5 * TILE + 17, 2, seed=0, stream=2)
     text = to_dev(torch, t, 0)
     p = b"01"

@@ -73,6 +73,14 @@ def parse():
                     help="also measure counts and positions over 20,000 packed texts (~35 GB)")
     ap.add_argument("--multi-only", action="store_true", help="measure only the packed-texts batch")
     ap.add_argument("--multi-texts", type=int, default=20000)
+    ap.add_argument("--tune-only", action="store_true",
+                    help="autotune every (sigma, m) bucket of the sweep and compare tuned with untuned counts")
+    ap.add_argument("--tune-save", default="", help="--tune-only: merge the plans into this JSON cache")
+    ap.add_argument("--orders-only", action="store_true",
+                    help="measure only the comparison orders of Sec. 2.2 / 2.4 (pi_freq, pi_h, pi_hs)")
+    ap.add_argument("--orders-kinds", default="markov95,20,4")
+    ap.add_argument("--orders-ms", default=",".join(str(m) for m in range(4, 65, 4)))
+    ap.add_argument("--orders-peels", default="0,2,3,5")
     ap.add_argument("--serve-rates", default="200,1000,4000")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     return ap.parse_args()
@@ -653,6 +661,119 @@ def run_multi(args, local, steps=2, warmup=1):
             "tuned_count_patterns_gbs": round(pgb / t_tuned, 1), "tuned_counts_agree": tuned_agree}
 
 
+def run_tune(args, local, reps=3):
+    """Autotuner per (m, sigma) bucket on the sweep's texts: for each text and
+    m, the count GB/s of --patterns patterns under the library's defaults,
+    then sm_tune_search on 24 other patterns of the bucket (seed 1), then the
+    same timed patterns under the tuned plan. The counts must not change."""
+    import torch
+    from paper_1612_01506_gb300 import sm, synth, tune
+    kinds, ms = kinds_of(args.kinds), [int(x) for x in args.ms.split(",") if x]
+    dev = torch.device("cuda", local)
+    ctx = sm.sm_create(local)
+    stream = torch.cuda.current_stream()
+    counts = torch.zeros(args.patterns, dtype=torch.int64, device=dev)
+    out = {"workload": f"tune: n={args.n}, sigma {args.kinds} x m {args.ms}, {args.patterns} timed patterns",
+           "cells": {}, "counts_agree": True, "entries": []}
+
+    def gbs(d, pats, pis, hist):
+        def one():
+            for j, p in enumerate(pats):
+                sm.sm_count(ctx, d, p, pi=pis[j], hist=hist, out=counts[j:j + 1])
+        one()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            one()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        return round(len(pats) * args.n / min(ts) / 1e9, 1), counts.cpu().numpy().copy()
+
+    for kind in kinds:
+        t = np.empty(args.n, dtype=np.uint8)
+        synth.text(kind, args.n, seed=0, stream=synth.stream_id("sweep", kind), out=t)
+        d = torch.from_numpy(t).to(dev)
+        hist = sm.sm_histogram(ctx, d).cpu().numpy().view(np.uint64).copy()
+        for m in ms:
+            pats = synth.sample_patterns(t, m, args.patterns, seed=0, stream=synth.stream_id("pat", kind, m))
+            pis = [sm.sm_order(p, hist) for p in pats]
+            mb, sb = sm.sm_tune_bucket(hist, m)
+            sm.sm_tune_set(ctx, mb, sb, None)
+            base, c0 = gbs(d, pats, pis, hist)
+            ent = tune.autotune(ctx, d, hist, t, [m], patterns=24, reps=reps)[0]
+            tuned, c1 = gbs(d, pats, pis, hist)
+            if not np.array_equal(c0, c1):
+                out["counts_agree"] = False
+            out["entries"].append(ent)
+            out["cells"][f"{kind}/m{m}"] = {"default_gbs": base, "tuned_gbs": tuned,
+                                            "plan": {k: ent[k] for k in tune.FIELDS}}
+        del d
+    out["tuned_not_slower_cells"] = sum(1 for c in out["cells"].values() if c["tuned_gbs"] >= 0.99 * c["default_gbs"])
+    out["cells_total"] = len(out["cells"])
+    if args.tune_save:
+        tune.write_entries(args.tune_save, tune.gpu_key(local), out["entries"])
+    return out
+
+
+def run_orders(args, local, reps=2):
+    """The comparison orders of Sec. 2.2 and 2.4 on the sweep's texts (n =
+    --n): rarest first under the text's histogram (pi_freq), and the fixed
+    orders pi_h and pi_hs, each with the peel r fixed (Algorithm 4) or chosen
+    by the planner (0). Per (text, m): --patterns patterns copied from the
+    text; GB/s = patterns x n / time of their count launches (median of reps
+    timed passes over the patterns). The counts must not depend on the order."""
+    import torch
+    from paper_1612_01506_gb300 import sm, synth
+    kinds = kinds_of(args.orders_kinds)
+    ms = [int(x) for x in args.orders_ms.split(",") if x]
+    peels = [int(x) for x in args.orders_peels.split(",") if x]
+    dev = torch.device("cuda", local)
+    ctx = sm.sm_create(local)
+    stream = torch.cuda.current_stream()
+    out = {"workload": f"orders: n={args.n}, texts {args.orders_kinds}, m {args.orders_ms}, "
+                       f"{args.patterns} patterns from the text, peel {args.orders_peels} (0 = planner)",
+           "gbs": {}, "counts_agree": True}
+    counts = torch.zeros(args.patterns, dtype=torch.int64, device=dev)
+    for kind in kinds:
+        t = np.empty(args.n, dtype=np.uint8)
+        synth.text(kind, args.n, seed=0, stream=synth.stream_id("sweep", kind), out=t)
+        d = torch.from_numpy(t).to(dev)
+        hist = sm.sm_histogram(ctx, d).cpu().numpy().view(np.uint64).copy()
+        res = {}
+        for m in ms:
+            pats = synth.sample_patterns(t, m, args.patterns, seed=0, stream=synth.stream_id("orders", kind, m))
+            orders = {"freq": [sm.sm_order(p, hist) for p in pats],
+                      "h": [sm.sm_order_fixed(p, sm.SM_ORDER_H) for p in pats],
+                      "hs": [sm.sm_order_fixed(p, sm.SM_ORDER_HS) for p in pats]}
+            cell, ref = {}, None
+            for name, pis in orders.items():
+                for peel in peels:
+                    def one():
+                        for j, p in enumerate(pats):
+                            sm.sm_count(ctx, d, p, pi=pis[j], hist=hist, peel=peel, out=counts[j:j + 1])
+                    one()
+                    got = counts.cpu().numpy().copy()
+                    if ref is None:
+                        ref = got
+                    elif not np.array_equal(ref, got):
+                        out["counts_agree"] = False
+                    ts = []
+                    for _ in range(reps):
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        one()
+                        e1.record(stream)
+                        torch.cuda.synchronize()
+                        ts.append(e0.elapsed_time(e1) / 1e3)
+                    cell[f"{name}/r{peel}"] = round(len(pats) * args.n / statistics.median(ts) / 1e9, 1)
+            res[str(m)] = cell
+        out["gbs"][str(kind)] = res
+        del d
+    return out
+
+
 # ---------------------------------------------------------------- serving
 
 def run_serve(args, local):
@@ -828,6 +949,14 @@ def main():
     if args.multi_only:
         if rank == 0:
             print(json.dumps({"multi": run_multi(args, local)}), flush=True)
+        return
+    if args.tune_only:
+        if rank == 0:
+            print(json.dumps({"tune": run_tune(args, local)}), flush=True)
+        return
+    if args.orders_only:
+        if rank == 0:
+            print(json.dumps({"orders": run_orders(args, local)}), flush=True)
         return
     if args.latency_only:
         if rank == 0:

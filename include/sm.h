@@ -193,6 +193,59 @@ sm_status sm_report_ex(sm_ctx* ctx, const uint8_t* d_text, uint64_t n,
                        const sm_search_opts* opts, uint64_t* d_pos, uint64_t cap,
                        uint64_t* d_count, sm_stream_t stream);
 
+/* ------------------------------------------------------------- tuning */
+/*
+ * Autotuned plans of the single-pattern scan. Sec. 2.3 leaves the peeling
+ * factor r to tuning (and Sec. 3 finds r = 2, 3 or 5 best per text type); on
+ * the GPU the pipeline depth and the CTAs per SM also change the speed
+ * (never the result). A context keeps one plan per bucket:
+ *   m bucket      ceil(log2 m): 0 for m = 1, 1 for m = 2, 2 for m = 3..4, ...,
+ *                 12 for m = 2049..4096
+ *   sigma bucket  from the text's histogram: 0 at most two distinct symbols
+ *                 (1-bit codes), 1 at most four (2-bit codes), then by the
+ *                 effective alphabet 1 / sum(p_c^2) of the symbol
+ *                 frequencies p_c: 2 below 12, 3 below 48, 4 from 48 up
+ * sm_count_ex and sm_report_ex use the plan of their bucket when they are
+ * given the text's histogram; fields left 0 keep the defaults, and an
+ * explicit opts->peel or sm_set_knob(SM_KNOB_STAGES / SM_KNOB_GRID) wins
+ * over the plan. The environment variables SM_R (peel), SM_STAGES and
+ * SM_CTAS_PER_SM override plans and defaults for every search of the
+ * process. Tile size (SM_TILE_STARTS) and starts per thread (64) are fixed
+ * by the kernels' warp geometry: sm_create fails with SM_ENOTSUP when
+ * SM_TILE or SM_STARTS asks for other values.
+ */
+#define SM_TUNE_M_BUCKETS 13u
+#define SM_TUNE_SIGMA_BUCKETS 5u
+typedef struct sm_tuning {
+    uint32_t peel;          /* peeling factor r, 0 = the planner's choice */
+    uint32_t stages;        /* pipeline depth 2..8, 0 = default */
+    uint32_t ctas_per_sm;   /* resident scan CTAs per SM to launch, 0 = all that fit */
+    float ms;               /* sm_tune_search: mean time per search of the plan */
+} sm_tuning;
+
+/* The buckets of a search for a pattern of length m (1..SM_MAX_M) in a text
+ * with host histogram h_hist256. Host only. */
+sm_status sm_tune_bucket(const uint64_t* h_hist256, uint32_t m, uint32_t* m_bucket, uint32_t* sigma_bucket);
+
+/* Install (NULL: clear) or read the plan of a bucket of this context. */
+sm_status sm_tune_set(sm_ctx* ctx, uint32_t m_bucket, uint32_t sigma_bucket, const sm_tuning* plan);
+sm_status sm_tune_get(sm_ctx* ctx, uint32_t m_bucket, uint32_t sigma_bucket, sm_tuning* plan);
+
+/*
+ * Time sm_count_ex over npats patterns (packed in h_pats by h_pat_off, all
+ * in one m bucket) in the text d_text (n bytes, device) with histogram
+ * h_hist256, each in rarest-first order: the current plan of their bucket,
+ * then by coordinate descent the peel (planner, 1..8), the stages (2, 3, 4,
+ * 6) and the CTAs per SM (1, 2, 3) -- a candidate replaces the best only
+ * when it is at least 2 % faster. Each plan: one warm-up pass, then reps
+ * timed passes over the patterns (the fastest counts). Installs the best
+ * plan for the bucket and returns it in *best. Synchronous on `stream`;
+ * allocates one count word.
+ */
+sm_status sm_tune_search(sm_ctx* ctx, const uint8_t* d_text, uint64_t n, const uint64_t* h_hist256,
+                         const uint8_t* h_pats, const int64_t* h_pat_off, uint32_t npats, uint32_t reps,
+                         sm_tuning* best, sm_stream_t stream);
+
 /* ---------------------------------------------------------------- batch */
 /*
  * Batched counting: many patterns of uneven lengths over many texts, with

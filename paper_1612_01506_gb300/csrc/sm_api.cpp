@@ -43,6 +43,8 @@ struct sm_ctx {
     uint64_t spin_ns = 1000000000ull;
     uint32_t test_skip_copy = 0;
     std::unordered_map<uint64_t, int> occ;   // (mode, kind, large m, smem) -> resident CTAs per SM
+    // autotuned plans per (m bucket, sigma bucket); all-zero = the defaults
+    sm_tuning tune[SM_TUNE_M_BUCKETS][SM_TUNE_SIGMA_BUCKETS] = {};
 };
 
 namespace {
@@ -111,6 +113,40 @@ sm_status check_pattern(const uint8_t* h_pat, uint32_t m, const uint32_t* h_pi) 
         }
     }
     return SM_OK;
+}
+
+// Autotuning buckets (include/sm.h): ceil(log2 m), and the text's alphabet.
+uint32_t m_bucket_of(uint32_t m) {
+    uint32_t b = 0;
+    while ((1u << b) < m) ++b;
+    return b;
+}
+
+uint32_t sigma_bucket_of(const uint64_t* h) {
+    uint64_t n = 0;
+    uint32_t distinct = 0;
+    for (int c = 0; c < 256; ++c) {
+        n += h[c];
+        distinct += h[c] ? 1u : 0u;
+    }
+    if (distinct <= 2) return 0;
+    if (distinct <= 4) return 1;
+    double s2 = 0;
+    for (int c = 0; c < 256; ++c) {
+        const double p = (double)h[c] / (double)n;
+        s2 += p * p;
+    }
+    const double eff = 1.0 / s2;
+    return eff < 12.0 ? 2u : eff < 48.0 ? 3u : 4u;
+}
+
+// A non-negative integer from the environment, or -1.
+long env_uint(const char* name) {
+    const char* v = std::getenv(name);
+    if (!v || !*v) return -1;
+    char* end = nullptr;
+    const long x = std::strtol(v, &end, 10);
+    return (end && *end == 0 && x >= 0) ? x : -1;
 }
 
 struct Plan {
@@ -214,17 +250,19 @@ int occupancy(sm_ctx* c, int mode, int kind, uint32_t m, size_t smem) {
     return o;
 }
 
-sm_status plan_grid(sm_ctx* c, int mode, int kind, bool report, uint32_t m, uint64_t nstarts, Grid* g) {
+sm_status plan_grid(sm_ctx* c, int mode, int kind, bool report, uint32_t m, uint64_t nstarts, Grid* g,
+                    const sm_tuning* t = nullptr) {
     g->ntiles = (nstarts + smk::kTile - 1) / smk::kTile;
     g->stage_bytes = smk::stage_bytes_for(m);
-    g->stages = c->stages;
+    const bool tuned_stages = t && t->stages >= 2;
+    g->stages = tuned_stages ? std::min<uint32_t>(t->stages, smk::kMaxStages) : c->stages;
     while (g->stages > 2 && smk::scan_smem_bytes(g->stage_bytes, g->stages, kind, report) > c->max_smem) --g->stages;
     g->smem = smk::scan_smem_bytes(g->stage_bytes, g->stages, kind, report);
     if (g->smem > c->max_smem) return fail(SM_ENOTSUP, "pattern too long for shared memory");
     int occ = occupancy(c, mode, kind, m, g->smem);
     if (occ <= 0) return fail(SM_ECUDA, "scan kernel cannot be resident (smem %zu)", g->smem);
     // one stage fewer is worth it when it lets another CTA reside on each SM
-    while (!c->stages_fixed && g->stages > 2) {
+    while (!c->stages_fixed && !tuned_stages && g->stages > 2) {
         const size_t sm2 = smk::scan_smem_bytes(g->stage_bytes, g->stages - 1, kind, report);
         const int o2 = occupancy(c, mode, kind, m, sm2);
         if (o2 <= occ) break;
@@ -233,7 +271,8 @@ sm_status plan_grid(sm_ctx* c, int mode, int kind, bool report, uint32_t m, uint
         occ = o2;
     }
     uint64_t want = c->grid_override;
-    if (!want) want = (uint64_t)c->num_sms * (uint64_t)occ;
+    if (!want) want = (uint64_t)c->num_sms * (uint64_t)(t && t->ctas_per_sm ? std::min<int>(occ, (int)t->ctas_per_sm)
+                                                                             : occ);
     want = std::max<uint64_t>(1, std::min<uint64_t>(want, g->ntiles));
     g->per_cta = (g->ntiles + want - 1) / want;
     g->grid = (uint32_t)((g->ntiles + g->per_cta - 1) / g->per_cta);
@@ -312,6 +351,12 @@ sm_status sm_create(sm_ctx** out, int device) {
     DeviceGuard g(device);
     if (!g.ok) return fail(SM_ECUDA, "cudaSetDevice(%d) failed", device);
     if (fault_alloc()) return fail(SM_ENOMEM, "injected allocation failure (context)");
+    const long tile = env_uint("SM_TILE"), starts = env_uint("SM_STARTS");
+    if (tile >= 0 && tile != (long)smk::kTile)
+        return fail(SM_ENOTSUP, "SM_TILE=%ld: the tile is fixed at %u starts by the warp geometry", tile, smk::kTile);
+    if (starts >= 0 && starts != 16 * smk::kChunks)
+        return fail(SM_ENOTSUP, "SM_STARTS=%ld: each thread takes %d starts (fixed by the warp geometry)", starts,
+                    16 * smk::kChunks);
     sm_ctx* c = new sm_ctx();
     c->device = device;
     int v = 0;
@@ -458,6 +503,20 @@ static sm_status search(sm_ctx* c, const uint8_t* d_text, uint64_t n, const uint
     if (!g.ok) return fail(SM_ECUDA, "cudaSetDevice(%d) failed", c->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if ((uint64_t)m > n) return zero_count(d_count, s);
+    // the autotuned plan of the search's bucket (needs the text histogram),
+    // then the environment's overrides; an explicit peel or knob wins
+    sm_tuning tu{};
+    if (opts && opts->h_hist256) tu = c->tune[m_bucket_of(m)][sigma_bucket_of(opts->h_hist256)];
+    if (env_uint("SM_R") > 0) tu.peel = (uint32_t)env_uint("SM_R");
+    if (env_uint("SM_STAGES") >= 2) tu.stages = (uint32_t)env_uint("SM_STAGES");
+    if (env_uint("SM_CTAS_PER_SM") > 0) tu.ctas_per_sm = (uint32_t)env_uint("SM_CTAS_PER_SM");
+    if (c->stages_fixed) tu.stages = 0;
+    sm_search_opts o2{};
+    if (tu.peel && !(opts && opts->peel)) {
+        if (opts) o2 = *opts;
+        o2.peel = tu.peel;
+        opts = &o2;
+    }
     Plan pl;
     st = make_plan(d_text, h_pat, m, h_pi, opts, n, &pl);
     if (st != SM_OK) return st;
@@ -468,7 +527,7 @@ static sm_status search(sm_ctx* c, const uint8_t* d_text, uint64_t n, const uint
     const bool rescan = report && report_rescans(pl, nstarts, ntiles);
     const int mode1 = !report ? smk::kModeCount : rescan ? smk::kModeSparse : smk::kModeTileCount;
     Grid gr;
-    st = plan_grid(c, mode1, pl.kind, report && !rescan, m, nstarts, &gr);
+    st = plan_grid(c, mode1, pl.kind, report && !rescan, m, nstarts, &gr, &tu);
     if (st != SM_OK) return st;
     const uint64_t wranges = std::max<uint64_t>(1, std::min<uint64_t>(gr.ntiles, 4ull * (uint64_t)c->num_sms));
     if (report) {
@@ -553,6 +612,134 @@ sm_status sm_report_ex(sm_ctx* c, const uint8_t* d_text, uint64_t n, const uint8
                        const uint32_t* h_pi, const sm_search_opts* opts, uint64_t* d_pos, uint64_t cap,
                        uint64_t* d_count, sm_stream_t stream) {
     return search(c, d_text, n, h_pat, m, h_pi, opts, d_pos, cap, d_count, stream, true);
+}
+
+sm_status sm_tune_bucket(const uint64_t* h_hist256, uint32_t m, uint32_t* m_bucket, uint32_t* sigma_bucket) {
+    if (!h_hist256 || !m_bucket || !sigma_bucket) return fail(SM_EINVAL, "NULL argument");
+    if (m == 0 || m > SM_MAX_M) return fail(SM_EINVAL, "pattern length %u out of range", m);
+    *m_bucket = m_bucket_of(m);
+    *sigma_bucket = sigma_bucket_of(h_hist256);
+    return SM_OK;
+}
+
+sm_status sm_tune_set(sm_ctx* c, uint32_t m_bucket, uint32_t sigma_bucket, const sm_tuning* plan) {
+    if (!c) return fail(SM_EINVAL, "ctx is NULL");
+    if (m_bucket >= SM_TUNE_M_BUCKETS || sigma_bucket >= SM_TUNE_SIGMA_BUCKETS)
+        return fail(SM_EINVAL, "bucket (%u, %u) out of range", m_bucket, sigma_bucket);
+    if (plan && (plan->peel > SM_MAX_M || (plan->stages && (plan->stages < 2 || plan->stages > smk::kMaxStages)) ||
+                 plan->ctas_per_sm > 64))
+        return fail(SM_EINVAL, "plan out of range");
+    c->tune[m_bucket][sigma_bucket] = plan ? *plan : sm_tuning{};
+    return SM_OK;
+}
+
+sm_status sm_tune_get(sm_ctx* c, uint32_t m_bucket, uint32_t sigma_bucket, sm_tuning* plan) {
+    if (!c || !plan) return fail(SM_EINVAL, "NULL argument");
+    if (m_bucket >= SM_TUNE_M_BUCKETS || sigma_bucket >= SM_TUNE_SIGMA_BUCKETS)
+        return fail(SM_EINVAL, "bucket (%u, %u) out of range", m_bucket, sigma_bucket);
+    *plan = c->tune[m_bucket][sigma_bucket];
+    return SM_OK;
+}
+
+sm_status sm_tune_search(sm_ctx* c, const uint8_t* d_text, uint64_t n, const uint64_t* h_hist256,
+                         const uint8_t* h_pats, const int64_t* h_pat_off, uint32_t npats, uint32_t reps,
+                         sm_tuning* best, sm_stream_t stream) {
+    if (!c || !d_text || !h_hist256 || !h_pats || !h_pat_off || !best || npats == 0)
+        return fail(SM_EINVAL, "NULL argument or no patterns");
+    if (reps < 1) reps = 1;
+    uint32_t mb = 0;
+    for (uint32_t k = 0; k < npats; ++k) {
+        const int64_t m = h_pat_off[k + 1] - h_pat_off[k];
+        if (m < 1 || m > (int64_t)SM_MAX_M || (uint64_t)m > n) return fail(SM_EINVAL, "pattern %u length", k);
+        if (k == 0) mb = m_bucket_of((uint32_t)m);
+        if (m_bucket_of((uint32_t)m) != mb) return fail(SM_EINVAL, "patterns of different m buckets");
+    }
+    const uint32_t sb = sigma_bucket_of(h_hist256);
+    DeviceGuard g(c->device);
+    if (!g.ok) return fail(SM_ECUDA, "cudaSetDevice(%d) failed", c->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    std::vector<std::vector<uint32_t>> pis(npats);
+    for (uint32_t k = 0; k < npats; ++k) {
+        const uint32_t m = (uint32_t)(h_pat_off[k + 1] - h_pat_off[k]);
+        pis[k].resize(m);
+        sm_order(h_pats + h_pat_off[k], m, h_hist256, pis[k].data());
+    }
+    uint64_t* d_count = nullptr;
+    if (cudaMalloc(&d_count, sizeof(uint64_t)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SM_ENOMEM, "tuning count word");
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const sm_search_opts o{0u, 0u, h_hist256};
+    auto pass = [&]() -> sm_status {
+        for (uint32_t k = 0; k < npats; ++k) {
+            const sm_status s = sm_count_ex(c, d_text, n, h_pats + h_pat_off[k],
+                                            (uint32_t)(h_pat_off[k + 1] - h_pat_off[k]), pis[k].data(), &o,
+                                            d_count, stream);
+            if (s != SM_OK) return s;
+        }
+        return SM_OK;
+    };
+    // mean ms per search of a plan: a warm-up pass, then the fastest of reps
+    auto time_plan = [&](const sm_tuning& t, float* ms) -> sm_status {
+        c->tune[mb][sb] = t;
+        sm_status s = pass();
+        float bestp = 1e30f;
+        for (uint32_t r = 0; s == SM_OK && r < reps; ++r) {
+            float x = 0;
+            if (cudaEventRecord(e0, st) != cudaSuccess) s = fail(SM_ECUDA, "tuning timer");
+            if (s == SM_OK) s = pass();
+            if (s == SM_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                               cudaEventElapsedTime(&x, e0, e1) != cudaSuccess))
+                s = fail(SM_ECUDA, "tuning timer");
+            bestp = std::min(bestp, x);
+        }
+        *ms = bestp / (float)npats;
+        return s;
+    };
+    auto same = [](const sm_tuning& a, const sm_tuning& b) {
+        return a.peel == b.peel && a.stages == b.stages && a.ctas_per_sm == b.ctas_per_sm;
+    };
+    sm_tuning cur = c->tune[mb][sb];
+    cur.ms = 0;
+    const sm_tuning start = cur;
+    float cur_ms = 0;
+    sm_status s = time_plan(cur, &cur_ms);
+    auto consider = [&](sm_tuning cand) {
+        if (s != SM_OK || same(cand, cur)) return;
+        float ms = 0;
+        s = time_plan(cand, &ms);
+        if (s == SM_OK && ms < 0.98f * cur_ms) {
+            cur = cand;
+            cur_ms = ms;
+        }
+    };
+    for (uint32_t r : {0u, 1u, 2u, 3u, 4u, 5u, 6u, 7u, 8u}) {
+        sm_tuning t = cur;
+        t.peel = r;
+        consider(t);
+    }
+    for (uint32_t stg : {0u, 2u, 3u, 4u, 6u}) {
+        sm_tuning t = cur;
+        t.stages = stg;
+        consider(t);
+    }
+    for (uint32_t k : {0u, 1u, 2u, 3u}) {
+        sm_tuning t = cur;
+        t.ctas_per_sm = k;
+        consider(t);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(d_count);
+    c->tune[mb][sb] = s == SM_OK ? cur : start;
+    if (s != SM_OK) return s;
+    cur.ms = cur_ms;
+    c->tune[mb][sb].ms = cur_ms;
+    *best = cur;
+    return SM_OK;
 }
 
 }  // extern "C"

@@ -28,7 +28,9 @@ EXPORTS = ("sm_create", "sm_destroy", "sm_last_error", "sm_status_string", "sm_s
            "sm_histogram", "sm_order", "sm_order_fixed", "sm_count", "sm_count_ex", "sm_report",
            "sm_report_ex", "sm_report_noalloc", "sm_batch_create", "sm_batch_count", "sm_batch_report",
            "sm_batch_tune", "sm_batch_destroy", "sm_count_batch", "sm_stepper_create", "sm_stepper_chunks", "sm_stepper_admit",
-           "sm_stepper_step", "sm_stepper_steps", "sm_stepper_retire", "sm_stepper_report", "sm_stepper_destroy")
+           "sm_stepper_step", "sm_stepper_steps", "sm_stepper_retire", "sm_stepper_report", "sm_stepper_destroy",
+           "sm_tune_bucket", "sm_tune_set", "sm_tune_get", "sm_tune_search")
+SM_TUNE_M_BUCKETS, SM_TUNE_SIGMA_BUCKETS = 13, 5
 
 
 class SmError(RuntimeError):
@@ -42,6 +44,10 @@ SM_SEARCH_BYTES = 1
 
 class BatchTuning(C.Structure):
     _fields_ = [("cand_freq", C.c_float), ("cand_min", C.c_uint32), ("stages", C.c_uint32), ("ms", C.c_float)]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("peel", C.c_uint32), ("stages", C.c_uint32), ("ctas_per_sm", C.c_uint32), ("ms", C.c_float)]
 
 
 class SearchOpts(C.Structure):
@@ -89,6 +95,10 @@ def load():
         "sm_batch_tune": (st, [vp, u32, C.POINTER(BatchTuning), vp]),
         "sm_batch_destroy": (None, [vp]),
         "sm_count_batch": (st, [vp, vp, vp, u32, vp, vp, vp, u32, vp, vp, vp, vp]),
+        "sm_tune_bucket": (st, [u64p, u32, u32p, u32p]),
+        "sm_tune_set": (st, [vp, u32, u32, C.POINTER(Tuning)]),
+        "sm_tune_get": (st, [vp, u32, u32, C.POINTER(Tuning)]),
+        "sm_tune_search": (st, [vp, vp, u64, u64p, u8p, C.POINTER(C.c_int64), u32, u32, C.POINTER(Tuning), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -341,3 +351,44 @@ def sm_count_batch(ctx: Ctx, texts, d_text_off, d_pats, d_pat_off, d_pat_text, d
                                  _dev_ptr(d_pos, _WORD64) if d_pos is not None else None,
                                  _dev_ptr(d_pos_off, _WORD64) if d_pos_off is not None else None, _stream(stream)))
     return d_counts
+
+
+# ------------------------------------------------------------------ tuning
+
+def _tuning_dict(t: Tuning) -> dict:
+    return {"peel": t.peel, "stages": t.stages, "ctas_per_sm": t.ctas_per_sm, "ms": round(float(t.ms), 6)}
+
+
+def sm_tune_bucket(hist, m: int) -> tuple[int, int]:
+    """(m bucket, sigma bucket) of a search for a pattern of length m in a text with this histogram."""
+    h = np.ascontiguousarray(hist, dtype=np.uint64)
+    mb, sb = C.c_uint32(), C.c_uint32()
+    _check(load().sm_tune_bucket(h.ctypes.data_as(C.POINTER(C.c_uint64)), m, C.byref(mb), C.byref(sb)))
+    return mb.value, sb.value
+
+
+def sm_tune_set(ctx: Ctx, m_bucket: int, sigma_bucket: int, plan: dict | None):
+    """Install a plan ({"peel", "stages", "ctas_per_sm"}; None clears) for a bucket."""
+    t = None if plan is None else Tuning(int(plan.get("peel", 0)), int(plan.get("stages", 0)),
+                                         int(plan.get("ctas_per_sm", 0)), float(plan.get("ms", 0.0)))
+    _check(load().sm_tune_set(ctx.handle, m_bucket, sigma_bucket, C.byref(t) if t is not None else None))
+
+
+def sm_tune_get(ctx: Ctx, m_bucket: int, sigma_bucket: int) -> dict:
+    t = Tuning()
+    _check(load().sm_tune_get(ctx.handle, m_bucket, sigma_bucket, C.byref(t)))
+    return _tuning_dict(t)
+
+
+def sm_tune_search(ctx: Ctx, text, hist, patterns: list, reps: int = 3, stream=None) -> dict:
+    """Autotune the bucket of `patterns` (one m bucket) on `text`; installs and returns the best plan."""
+    h = np.ascontiguousarray(hist, dtype=np.uint64)
+    flat = np.frombuffer(b"".join(bytes(p) for p in patterns), dtype=np.uint8)
+    off = np.zeros(len(patterns) + 1, dtype=np.int64)
+    off[1:] = np.cumsum([len(p) for p in patterns])
+    t = Tuning()
+    _check(load().sm_tune_search(ctx.handle, _dev_ptr(text, ("torch.uint8",)), text.numel(),
+                                 h.ctypes.data_as(C.POINTER(C.c_uint64)), _u8p(flat),
+                                 off.ctypes.data_as(C.POINTER(C.c_int64)), len(patterns), reps, C.byref(t),
+                                 _stream(stream)))
+    return _tuning_dict(t)

@@ -310,3 +310,27 @@ def test_full_size_dense_report(torch, ctx, kind):
         del pos
     del text
     torch.cuda.empty_cache()
+
+
+def test_injected_alloc_failure(torch, monkeypatch):
+    """Host-side fault injection: with SM_FAULT=alloc every workspace
+    allocation fails, so the first call that must grow the workspace (a
+    report's per-tile tables) returns SM_ENOMEM and enqueues nothing; without
+    it the same context then gives the oracle's result."""
+    import __graft_entry__
+    __graft_entry__.build()
+    fresh = sm.sm_create(0)
+    t = synth.uniform(6 * TILE + 77, 20, seed=0, stream=61)
+    text = to_dev(torch, t, 3)
+    p = t[5000:5002].tobytes()
+    want_pos, want = oracle.naive_report(p, t)
+    monkeypatch.setenv("SM_FAULT", "alloc")
+    with pytest.raises(sm.SmError) as e:
+        sm.sm_report(fresh, text, p, want)
+    assert e.value.status == sm.SM_ENOMEM
+    with pytest.raises(sm.SmError) as e:
+        sm.sm_create(0)
+    assert e.value.status == sm.SM_ENOMEM
+    monkeypatch.delenv("SM_FAULT")
+    pos, c, st = gpu_report(fresh, text, p, want)
+    assert st == sm.SM_OK and c == want and np.array_equal(pos, want_pos)

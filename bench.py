@@ -76,6 +76,9 @@ def parse():
     ap.add_argument("--tune-only", action="store_true",
                     help="autotune every (sigma, m) bucket of the sweep and compare tuned with untuned counts")
     ap.add_argument("--tune-save", default="", help="--tune-only: merge the plans into this JSON cache")
+    ap.add_argument("--compare-stats", action="store_true",
+                    help="early-exit counters: compares per 16-start chunk (builds and uses a profiling "
+                         "library with -DSMK_COUNT_COMPARES=1)")
     ap.add_argument("--orders-only", action="store_true",
                     help="measure only the comparison orders of Sec. 2.2 / 2.4 (pi_freq, pi_h, pi_hs)")
     ap.add_argument("--orders-kinds", default="markov95,20,4")
@@ -193,12 +196,13 @@ def make_workload(args, rank):
     return kinds, ms, texts, pats
 
 
-def scan_traffic(n):
-    """DRAM bytes per count launch at text size n from the committed ncu
-    capture, if the scan kernel's sources are unchanged since (else None)."""
+def scan_traffic(n, record="scan_traffic.json"):
+    """DRAM bytes per launch (count) or per report (its kernels together) at
+    text size n from a committed ncu capture under profiles/, if the kernels'
+    sources are unchanged since (else None)."""
     import hashlib
     try:
-        with open(os.path.join(ROOT, "profiles", "scan_traffic.json")) as f:
+        with open(os.path.join(ROOT, "profiles", record)) as f:
             rec = json.load(f)
         h = hashlib.sha256()
         for src in rec["sources"]:
@@ -365,7 +369,10 @@ def run_gpu(args, world, rank, local):
                         lambda k, m, j: args.n + 8 * occ[(k, m)][j])
     if roof_rep:
         roof_rep["bytes"] = "n + 8 * matches per report"
-        roof_rep["traffic"] = None
+        roof_rep["traffic"] = scan_traffic(args.n, "report_traffic.json")
+        if roof_rep["traffic"]:
+            mean_alg = statistics.mean(args.n + 8 * statistics.mean(occ[(k, m)]) for k in kinds for m in ms)
+            roof_rep["traffic_over_bytes"] = round(roof_rep["traffic"] / mean_alg, 4)
 
     e2e = None
     if not args.no_e2e:
@@ -717,6 +724,46 @@ def run_tune(args, local, reps=3):
     return out
 
 
+def run_compare_stats(args, local):
+    """Early-exit counters from a profiling build of the library (its scan
+    kernels count, per 16-start chunk, the compares of the dense phase and,
+    for chunks that survive it, of the sparse phase). Per (text, m): the
+    --patterns count searches of the sweep (text histogram, rarest-first
+    order). Texts sigma = 4 run on 2-bit codes (a chunk is one 16-start word)."""
+    import ctypes as C
+    import torch
+    from paper_1612_01506_gb300 import build, sm, synth
+    os.environ["SM_LIBRARY"] = build.build_lib(out=os.path.join(build.PKG, "_build", "cmpstats"),
+                                               defines=("SMK_COUNT_COMPARES=1",))
+    lib = sm.load()
+    f = lib.sm_debug_compare_stats
+    f.restype, f.argtypes = C.c_int, [C.POINTER(C.c_ulonglong), C.c_int]
+    stats = (C.c_ulonglong * 4)()
+    dev = torch.device("cuda", local)
+    ctx = sm.sm_create(local)
+    out = {"workload": f"early exit: n={args.n}, sigma {args.kinds} x m {args.ms}, {args.patterns} patterns "
+                       "from the text, counts", "cells": {}}
+    for kind in kinds_of(args.kinds):
+        t = np.empty(args.n, dtype=np.uint8)
+        synth.text(kind, args.n, seed=0, stream=synth.stream_id("sweep", kind), out=t)
+        d = torch.from_numpy(t).to(dev)
+        hist = sm.sm_histogram(ctx, d).cpu().numpy().view(np.uint64).copy()
+        for m in [int(x) for x in args.ms.split(",") if x]:
+            pats = synth.sample_patterns(t, m, args.patterns, seed=0, stream=synth.stream_id("pat", kind, m))
+            f(stats, 1)
+            for p in pats:
+                sm.sm_count(ctx, d, p, pi=sm.sm_order(p, hist), hist=hist)
+            if f(stats, 1) != 0:
+                raise RuntimeError("reading the compare counters failed")
+            ch, dense, alive, sparse = (int(x) for x in stats)
+            out["cells"][f"{kind}/m{m}"] = {
+                "compares_per_chunk": round((dense + sparse) / ch, 3), "dense_per_chunk": round(dense / ch, 3),
+                "surviving_chunks": round(alive / ch, 5),
+                "sparse_per_surviving_chunk": round(sparse / alive, 3) if alive else 0.0}
+        del d
+    return out
+
+
 def run_orders(args, local, reps=2):
     """The comparison orders of Sec. 2.2 and 2.4 on the sweep's texts (n =
     --n): rarest first under the text's histogram (pi_freq), and the fixed
@@ -949,6 +996,10 @@ def main():
     if args.multi_only:
         if rank == 0:
             print(json.dumps({"multi": run_multi(args, local)}), flush=True)
+        return
+    if args.compare_stats:
+        if rank == 0:
+            print(json.dumps({"compare_stats": run_compare_stats(args, local)}), flush=True)
         return
     if args.tune_only:
         if rank == 0:

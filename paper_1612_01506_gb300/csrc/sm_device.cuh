@@ -11,6 +11,30 @@ namespace dev {
 constexpr uint32_t kFull = 0xffffffffu;
 constexpr uint64_t kEnd = ~0ull;
 
+// Early-exit counters of a profiling build (-DSMK_COUNT_COMPARES=1; off in
+// the library): per 16-start chunk (2-bit codes: per 16-start word) the
+// compares run in the dense phase and, for the chunks that survive it, in the
+// sparse phase. [0] chunks, [1] dense compares, [2] surviving chunks, [3]
+// sparse compares (cooperative ones included), summed over all launches of
+// the translation unit's scan kernels until read.
+#ifndef SMK_COUNT_COMPARES
+#define SMK_COUNT_COMPARES 0
+#endif
+#if SMK_COUNT_COMPARES
+static __device__ unsigned long long g_cmp_stats[4];
+__device__ __forceinline__ void cmp_stats_add(uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    const uint32_t v[4] = {a, b, c, d};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const uint32_t w = __reduce_add_sync(kFull, v[i]);
+        if ((threadIdx.x & 31u) == 0 && w) atomicAdd(&g_cmp_stats[i], (unsigned long long)w);
+    }
+}
+#define SMK_STATS(...) __VA_ARGS__
+#else
+#define SMK_STATS(...)
+#endif
+
 // ------------------------------------------------------------ PTX helpers
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -488,7 +512,9 @@ __device__ __forceinline__ uint32_t warp_tile(const uint4* __restrict__ b4, cons
             for (int i = 0; i < 4; ++i) f[c][i] &= valid_mask(lim - (512 * c + 4 * i));
     }
 
+    SMK_STATS(uint32_t st_sparse = 0, st_alive = 0;)
     if (DIRECT && r >= m) {
+        SMK_STATS(cmp_stats_add(kChunks, kChunks * r, 0, 0);)
         // every compare peeled: the found bits are final. With bm, a
         // warp-tile with matches stores its lanes' folded words
         uint32_t x0, x1;
@@ -506,7 +532,10 @@ __device__ __forceinline__ uint32_t warp_tile(const uint4* __restrict__ b4, cons
 #pragma unroll
     for (int c = 0; c < kChunks; ++c)
         alive |= (uint32_t)(((f[c][0] | f[c][1]) | (f[c][2] | f[c][3])) != 0u) << (8 * c);
-    if (!__any_sync(kFull, alive != 0u)) return 0;
+    if (!__any_sync(kFull, alive != 0u)) {
+        SMK_STATS(cmp_stats_add(kChunks, kChunks * r, 0, 0);)
+        return 0;
+    }
 
     // queue in position order: chunk 0 of all lanes, then chunk 1, ...; an
     // entry packs the chunk's 16 found bits (word i's bit 7 + 8b at bit
@@ -541,7 +570,9 @@ __device__ __forceinline__ uint32_t warp_tile(const uint4* __restrict__ b4, cons
         }
         const uint32_t W = wq + 4u * k;   // word index of the chunk's first start
         const uint32_t jl = min(m, r + kLaneCompares);
+        SMK_STATS(st_alive += e < qn ? 1u : 0u;)
         for (uint32_t j = r; j < jl && ((g[0] | g[1]) | (g[2] | g[3])); j += 2) {
+            SMK_STATS(st_sparse += min(2u, m - j);)
             uint32_t y[4] = {0u, 0u, 0u, 0u};
             acc_window(b32, W, qc(j), y);
             acc_window(b32, W, qc(min(j + 1, m - 1)), y);   // an odd tail repeats compare j
@@ -557,6 +588,7 @@ __device__ __forceinline__ uint32_t warp_tile(const uint4* __restrict__ b4, cons
             const uint32_t src = (uint32_t)__ffs(pend) - 1u;
             pend &= pend - 1u;
             const uint32_t Ws = __shfl_sync(kFull, W, src);
+            SMK_STATS(if (lane == src) st_sparse += m - jl;)
             uint32_t y[4] = {0u, 0u, 0u, 0u};
             for (uint32_t j = jl + lane; j < m; j += 32) acc_window(b32, Ws, qc(j), y);
 #pragma unroll
@@ -594,6 +626,7 @@ __device__ __forceinline__ uint32_t warp_tile(const uint4* __restrict__ b4, cons
             tile_count += n;
         }
     }
+    SMK_STATS(cmp_stats_add(kChunks, kChunks * r, st_alive, st_sparse);)
     __syncwarp();   // the queue is reused by the next tile; sbm is complete
     if (bm && __any_sync(kFull, tile_count != 0u)) {
         const uint32_t e = store_slot(bm, lane, sbm[2 * lane], sbm[2 * lane + 1]);
@@ -723,6 +756,11 @@ __device__ __forceinline__ uint2 packed_tiles(const uint32_t* const (&pk)[2], bo
     uint32_t any = 0;
 #pragma unroll
     for (int t = 0; t < NT; ++t) any |= (f[t][0] | f[t][1]) | (f[t][2] | f[t][3]);
+    SMK_STATS(uint32_t st_words = 0, st_alive = 0, st_sparse = 0;)
+    SMK_STATS(for (int t = 0; t < NT; ++t) if (t == 0 || two) {
+        st_words += 4;
+        for (int i = 0; i < 4; ++i) st_alive += f[t][i] ? 1u : 0u;
+    })
     if (!(DIRECT && r >= m) && __any_sync(kFull, any != 0u)) {
         const uint32_t jl = min(m, r + kLaneCompares);
         for (uint32_t j = r; j < jl && any; ++j) {
@@ -736,6 +774,7 @@ __device__ __forceinline__ uint2 packed_tiles(const uint32_t* const (&pk)[2], bo
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     if (f[t][i]) {
+                        SMK_STATS(++st_sparse;)
                         const uint32_t W = w0 + i + (e >> 4);
                         f[t][i] &= zero_fields(__funnelshift_r(pk[t][W], pk[t][W + 1], sh) ^ P);
                     }
@@ -753,6 +792,7 @@ __device__ __forceinline__ uint2 packed_tiles(const uint32_t* const (&pk)[2], bo
                     const uint32_t src = (uint32_t)__ffs(pend) - 1u;
                     pend &= pend - 1u;
                     const uint32_t ws = __shfl_sync(kFull, w0, src) + i;
+                    SMK_STATS(if (lane == src) st_sparse += m - jl;)
                     uint32_t y = 0;
                     for (uint32_t j = jl + lane; j < m; j += 32) {
                         const uint32_t v = qc(j);
@@ -767,6 +807,7 @@ __device__ __forceinline__ uint2 packed_tiles(const uint32_t* const (&pk)[2], bo
                 }
             }
     }
+    SMK_STATS(cmp_stats_add(st_words, st_words * r, (DIRECT && r >= m) ? 0u : st_alive, st_sparse);)
     uint32_t n[2] = {0u, 0u};
 #pragma unroll
     for (int t = 0; t < NT; ++t) n[t] = __popc(f[t][0] | (f[t][1] << 1)) + __popc(f[t][2] | (f[t][3] << 1));

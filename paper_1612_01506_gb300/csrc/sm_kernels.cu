@@ -864,3 +864,18 @@ cudaError_t launch_hist(uint32_t grid, cudaStream_t s, const HistArgs& a) {
 }
 
 }  // namespace smk
+
+#if SMK_COUNT_COMPARES
+// Profiling builds only: the early-exit counters of the scan kernels (see
+// sm_device.cuh), read into out[0..3] and, with reset, cleared. Not part of
+// the library's interface.
+extern "C" int sm_debug_compare_stats(unsigned long long* out, int reset) {
+    if (cudaDeviceSynchronize() != cudaSuccess) return 1;
+    if (cudaMemcpyFromSymbol(out, smk::dev::g_cmp_stats, 4 * sizeof(unsigned long long)) != cudaSuccess) return 1;
+    if (reset) {
+        const unsigned long long z[4] = {0, 0, 0, 0};
+        if (cudaMemcpyToSymbol(smk::dev::g_cmp_stats, z, sizeof z) != cudaSuccess) return 1;
+    }
+    return 0;
+}
+#endif

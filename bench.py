@@ -86,6 +86,11 @@ def parse():
     ap.add_argument("--orders-peels", default="0,2,3,5")
     ap.add_argument("--serve-rates", default="200,1000,4000")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
+    ap.add_argument("--serve-chunk-mib", type=int, default=256, help="serving: text chunk per step (MiB)")
+    ap.add_argument("--serve-report-batch-min", type=int, default=32,
+                    help="serving: waiting reports that trigger one batched report")
+    ap.add_argument("--serve-burst-below", type=int, default=4,
+                    help="serving: at most this many queries in flight and none waiting: all chunks in one launch")
     return ap.parse_args()
 
 
@@ -838,8 +843,11 @@ def run_serve(args, local):
     synth.markov95(half, seed=0, stream=synth.stream_id("serve", "markov95"), out=t[half:])
     text = torch.from_numpy(t).to(torch.device("cuda", local))
     out = {"workload": "serving: 4 GiB resident text (2 GiB ACGT + 2 GiB Markov-95), Poisson arrivals, "
-                       "m log-uniform [2,2048], 80/20 count/report", "chunk_bytes": 256 << 20, "rates": {}}
-    server = Server(text, chunk_bytes=256 << 20, max_m=2048, max_active=4096, report_budget=24 << 30)
+                       "m log-uniform [2,2048], 80/20 count/report", "chunk_bytes": args.serve_chunk_mib << 20,
+           "report_batch_min": args.serve_report_batch_min, "burst_below": args.serve_burst_below, "rates": {}}
+    server = Server(text, chunk_bytes=args.serve_chunk_mib << 20, max_m=2048, max_active=4096,
+                    report_budget=24 << 30, report_batch_min=args.serve_report_batch_min,
+                    burst_below=args.serve_burst_below)
     server.warm_up([t[1000:1000 + m].tobytes() for m in (3, 40, 700, 2048)])
     one_at_a_time(text, [Query(pattern=t[5:12].tobytes(), kind="report"), Query(pattern=t[9:30].tobytes())],
                   hist=server.hist)

@@ -199,23 +199,18 @@ class Server:
         self.steps += 1
 
     def _finish(self, finished: list):
-        """Read the final counts of `finished` back to the host (on the step
-        stream, after the work enqueued so far)."""
+        """Read the final counts of `finished` back to the host: one copy of
+        the whole counter array into the pinned mirror allocated at start-up
+        (on the step stream, after the work enqueued so far). Nothing is
+        allocated here: a pinned allocation in the loop took seconds on first
+        use. A later copy rewrites the mirror, but a finished query's counter
+        does not change until its slot is freed, after it has been read."""
         torch = self.torch
         with torch.cuda.stream(self.stream):
-            if len(finished) <= 4:   # a few copies into the pinned mirror
-                for q in finished:
-                    self.host_counters[q.qid].copy_(self.counters[q.qid], non_blocking=True)
-                host = None
-            else:
-                idx = torch.tensor([q.qid for q in finished], dtype=torch.int64).pin_memory().to(
-                    self.dev, non_blocking=True)
-                vals = self.counters.index_select(0, idx)
-                host = torch.empty(len(finished), dtype=torch.int64).pin_memory()
-                host.copy_(vals, non_blocking=True)
+            self.host_counters.copy_(self.counters, non_blocking=True)
         ev = torch.cuda.Event()
         ev.record(self.stream)
-        self.finishing.append((ev, finished, host))
+        self.finishing.append((ev, finished, None))
 
     def _run_alone(self, q: Query):
         """An arrival at an idle server: one single-pattern count over the
@@ -247,8 +242,9 @@ class Server:
                 keep.append((ev, qs, host))
                 continue
             now = self.now()
-            vals = host.tolist() if host is not None else [int(self.host_counters[q.qid]) for q in qs]
-            for q, c in zip(qs, vals):
+            hc = self.host_counters.numpy()
+            for q in qs:
+                c = hc[q.qid]
                 q.count = int(c)
                 if not getattr(q, "alone", False):
                     self.lib.sm_stepper_retire(self.stepper, q.qid)
@@ -375,13 +371,30 @@ class Server:
                 self.submit(order[i])
                 i += 1
             if not self.busy and i < len(order):
-                time.sleep(max(0.0, min(order[i].arrival - now, 0.001)))
+                wait = order[i].arrival - now
+                if wait > 0.0005:   # sleep most of the gap, spin the rest (sleep overshoots)
+                    time.sleep(wait - 0.0003)
                 continue
+            if not self.pending and not self.active and not self.report_wait and (self.finishing or self.reporting):
+                # only results in flight and nothing to step: wait for the oldest
+                # instead of polling (an arrival meanwhile joins right after)
+                (self.finishing or self.reporting)[0][0].synchronize()
             self.step()
             if max_steps is not None and self.steps >= max_steps:
                 break
         self.torch.cuda.synchronize()
         return order
+
+
+def _wait_until(t0: float, t: float) -> None:
+    """Return at time t0 + t (perf_counter seconds): sleep most of the gap,
+    spin the rest (a sleep overshoots by tens of microseconds)."""
+    while True:
+        left = t0 + t - time.perf_counter()
+        if left <= 0:
+            return
+        if left > 0.0005:
+            time.sleep(left - 0.0003)
 
 
 def one_at_a_time(text, queries: list[Query], hist=None) -> list[Query]:
@@ -393,9 +406,7 @@ def one_at_a_time(text, queries: list[Query], hist=None) -> list[Query]:
     order = sorted(queries, key=lambda q: q.arrival)
     t0 = time.perf_counter()
     for q in order:
-        now = time.perf_counter() - t0
-        if q.arrival > now:
-            time.sleep(q.arrival - now)
+        _wait_until(t0, q.arrival)
         pi = sm.sm_order(q.pattern, hist)
         c = sm.sm_count(ctx, text, q.pattern, pi=pi, hist=hist)
         q.count = int(c.item())
@@ -408,7 +419,15 @@ def one_at_a_time(text, queries: list[Query], hist=None) -> list[Query]:
 
 
 def latency_stats(qs: list[Query]) -> dict:
-    lat = np.array([q.latency for q in qs]) * 1e3
+    """p50 / p99 latency (ms) and throughput of answered queries, also per kind."""
+    def pct(sel):
+        lat = np.array([q.latency for q in sel]) * 1e3
+        return {"queries": len(sel), "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                "p99_ms": round(float(np.percentile(lat, 99)), 3)}
     span = max(q.done for q in qs) - min(q.arrival for q in qs)
-    return {"queries": len(qs), "p50_ms": round(float(np.percentile(lat, 50)), 3),
-            "p99_ms": round(float(np.percentile(lat, 99)), 3), "qps": round(len(qs) / span, 1)}
+    out = {**pct(qs), "qps": round(len(qs) / span, 1)}
+    for kind in ("count", "report"):
+        sel = [q for q in qs if q.kind == kind]
+        if sel:
+            out[kind] = pct(sel)
+    return out

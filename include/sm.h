@@ -237,8 +237,10 @@ sm_status sm_tune_get(sm_ctx* ctx, uint32_t m_bucket, uint32_t sigma_bucket, sm_
  * h_hist256, each in rarest-first order: the current plan of their bucket,
  * then by coordinate descent the peel (planner, 1..8), the stages (2, 3, 4,
  * 6) and the CTAs per SM (1, 2, 3) -- a candidate replaces the best only
- * when it is at least 2 % faster. Each plan: one warm-up pass, then reps
- * timed passes over the patterns (the fastest counts). Installs the best
+ * when it is at least 2 % faster on each half of the patterns (the first
+ * npats / 2 and the rest), so that a plan that helps a few patterns and
+ * hurts the others of the bucket is not kept. Each plan: one warm-up pass,
+ * then per half reps timed passes (the fastest counts). Installs the best
  * plan for the bucket and returns it in *best. Synchronous on `stream`;
  * allocates one count word.
  */

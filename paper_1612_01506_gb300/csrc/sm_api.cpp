@@ -40,6 +40,7 @@ struct sm_ctx {
     uint32_t stages = 4;
     bool stages_fixed = false;        // set by SM_KNOB_STAGES; otherwise fewer stages may raise occupancy
     uint32_t grid_override = 0;
+    int write_occ = 1;                // resident blocks per SM of the report's second pass
     uint64_t spin_ns = 1000000000ull;
     uint32_t test_skip_copy = 0;
     std::unordered_map<uint64_t, int> occ;   // (mode, kind, large m, smem) -> resident CTAs per SM
@@ -375,6 +376,7 @@ sm_status sm_create(sm_ctx** out, int device) {
         sm_destroy(c);
         return cuda_fail(e, "cudaFuncSetAttribute");
     }
+    c->write_occ = std::max(1, smk::bitmap_write_occupancy());
     sm_status st = grow(&c->d_partials, &c->partials_cap, (size_t)c->num_sms * 16 * 256, "partials");
     if (st != SM_OK) {
         sm_destroy(c);
@@ -529,7 +531,9 @@ static sm_status search(sm_ctx* c, const uint8_t* d_text, uint64_t n, const uint
     Grid gr;
     st = plan_grid(c, mode1, pl.kind, report && !rescan, m, nstarts, &gr, &tu);
     if (st != SM_OK) return st;
-    const uint64_t wranges = std::max<uint64_t>(1, std::min<uint64_t>(gr.ntiles, 4ull * (uint64_t)c->num_sms));
+    // ranges of the report's second pass: one resident wave of its blocks
+    const uint64_t wranges = std::max<uint64_t>(
+        1, std::min<uint64_t>(gr.ntiles, (uint64_t)c->write_occ * (uint64_t)c->num_sms));
     if (report) {
         st = grow(&c->d_partials, &c->partials_cap,
                   std::max<size_t>((size_t)std::max<uint64_t>(wranges, gr.grid), 256), "partials");
@@ -571,8 +575,7 @@ static sm_status search(sm_ctx* c, const uint8_t* d_text, uint64_t n, const uint
     e = smk::launch_scan(mode1, pl.kind, gr.grid, gr.smem, s, a, pl.qc.data(), pl.groups.data());
     if (e != cudaSuccess) return cuda_fail(e, "scan launch");
     if (report) {
-        // the write pass: ranges of tiles, four blocks per SM (its latency
-        // is hidden by more warps than the scan's grid gives)
+        // the write pass: one range of tiles per block, one resident wave
         const uint64_t per = (gr.ntiles + wranges - 1) / wranges;
         const uint32_t wgrid = (uint32_t)((gr.ntiles + per - 1) / per);
         e = smk::launch_range_sums(wgrid, s, c->d_warp_counts, gr.ntiles, per, c->d_partials);
@@ -673,8 +676,11 @@ sm_status sm_tune_search(sm_ctx* c, const uint8_t* d_text, uint64_t n, const uin
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const sm_search_opts o{0u, 0u, h_hist256};
-    auto pass = [&]() -> sm_status {
-        for (uint32_t k = 0; k < npats; ++k) {
+    // the patterns in two halves [0, half) and [half, npats): a candidate
+    // must win on both (with one pattern, the one half is all of them)
+    const uint32_t half = npats >= 2 ? npats / 2 : npats;
+    auto pass = [&](uint32_t k0, uint32_t k1) -> sm_status {
+        for (uint32_t k = k0; k < k1; ++k) {
             const sm_status s = sm_count_ex(c, d_text, n, h_pats + h_pat_off[k],
                                             (uint32_t)(h_pat_off[k + 1] - h_pat_off[k]), pis[k].data(), &o,
                                             d_count, stream);
@@ -682,21 +688,29 @@ sm_status sm_tune_search(sm_ctx* c, const uint8_t* d_text, uint64_t n, const uin
         }
         return SM_OK;
     };
-    // mean ms per search of a plan: a warm-up pass, then the fastest of reps
-    auto time_plan = [&](const sm_tuning& t, float* ms) -> sm_status {
-        c->tune[mb][sb] = t;
-        sm_status s = pass();
+    // mean ms per search of a plan on each half: a warm-up pass, then the
+    // fastest of reps timed passes
+    auto time_half = [&](uint32_t k0, uint32_t k1, float* ms) -> sm_status {
+        sm_status s = SM_OK;
         float bestp = 1e30f;
         for (uint32_t r = 0; s == SM_OK && r < reps; ++r) {
             float x = 0;
             if (cudaEventRecord(e0, st) != cudaSuccess) s = fail(SM_ECUDA, "tuning timer");
-            if (s == SM_OK) s = pass();
+            if (s == SM_OK) s = pass(k0, k1);
             if (s == SM_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
                                cudaEventElapsedTime(&x, e0, e1) != cudaSuccess))
                 s = fail(SM_ECUDA, "tuning timer");
             bestp = std::min(bestp, x);
         }
-        *ms = bestp / (float)npats;
+        *ms = bestp / (float)std::max<uint32_t>(1, k1 - k0);
+        return s;
+    };
+    auto time_plan = [&](const sm_tuning& t, float (&ms)[2]) -> sm_status {
+        c->tune[mb][sb] = t;
+        sm_status s = pass(0, npats);
+        if (s == SM_OK) s = time_half(0, half, &ms[0]);
+        ms[1] = ms[0];
+        if (s == SM_OK && half < npats) s = time_half(half, npats, &ms[1]);
         return s;
     };
     auto same = [](const sm_tuning& a, const sm_tuning& b) {
@@ -705,15 +719,16 @@ sm_status sm_tune_search(sm_ctx* c, const uint8_t* d_text, uint64_t n, const uin
     sm_tuning cur = c->tune[mb][sb];
     cur.ms = 0;
     const sm_tuning start = cur;
-    float cur_ms = 0;
-    sm_status s = time_plan(cur, &cur_ms);
+    float cur_ms[2] = {0, 0};
+    sm_status s = time_plan(cur, cur_ms);
     auto consider = [&](sm_tuning cand) {
         if (s != SM_OK || same(cand, cur)) return;
-        float ms = 0;
-        s = time_plan(cand, &ms);
-        if (s == SM_OK && ms < 0.98f * cur_ms) {
+        float ms[2] = {0, 0};
+        s = time_plan(cand, ms);
+        if (s == SM_OK && ms[0] < 0.98f * cur_ms[0] && ms[1] < 0.98f * cur_ms[1]) {
             cur = cand;
-            cur_ms = ms;
+            cur_ms[0] = ms[0];
+            cur_ms[1] = ms[1];
         }
     };
     for (uint32_t r : {0u, 1u, 2u, 3u, 4u, 5u, 6u, 7u, 8u}) {
@@ -736,8 +751,9 @@ sm_status sm_tune_search(sm_ctx* c, const uint8_t* d_text, uint64_t n, const uin
     cudaFree(d_count);
     c->tune[mb][sb] = s == SM_OK ? cur : start;
     if (s != SM_OK) return s;
-    cur.ms = cur_ms;
-    c->tune[mb][sb].ms = cur_ms;
+    cur.ms = (cur_ms[0] * (float)half + cur_ms[1] * (float)(npats - half)) /
+             (float)(half < npats ? npats : half);
+    c->tune[mb][sb].ms = cur.ms;
     *best = cur;
     return SM_OK;
 }

@@ -144,6 +144,8 @@ struct WriteArgs {
 };
 constexpr int kWriteThreads = 32 * kConsumerWarps;
 cudaError_t launch_bitmap_write(uint32_t grid, cudaStream_t s, const WriteArgs& a);
+// Resident blocks per SM of the second pass.
+int bitmap_write_occupancy();
 // Between the passes: partials[b] = matches in tiles [b T, (b + 1) T), one block per range;
 // with tile_list (ntiles entries), also the list of each range's tiles with matches.
 cudaError_t launch_range_sums(uint32_t grid, cudaStream_t s, const uint32_t* warp_counts, uint64_t ntiles,

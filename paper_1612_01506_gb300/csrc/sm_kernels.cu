@@ -474,21 +474,19 @@ __global__ void __launch_bounds__(kWriteThreads) bitmap_write_kernel(const __gri
     const uint64_t t0 = (uint64_t)blockIdx.x * W.tiles_per_cta;
     const uint64_t t1 = min(t0 + W.tiles_per_cta, W.ntiles);
 
-    // first rank of the range: the counts of the earlier ranges
+    // first rank of the range: the counts of the earlier ranges (block 0
+    // sums all of them instead, for the truncation flag)
+    const uint32_t upto = blockIdx.x == 0 ? gridDim.x : blockIdx.x;
     uint64_t v = 0;
-    for (uint32_t i = tid; i < blockIdx.x; i += kWriteThreads) v += __ldcg(W.partials + i);
+    for (uint32_t i = tid; i < upto; i += kWriteThreads) v += __ldcg(W.partials + i);
     v = warp_sum_u64(v);
     if (lane == 0) red[warp] = v;
     __syncthreads();
     if (tid == 0) {
         uint64_t b = 0;
         for (int w = 0; w < kConsumerWarps; ++w) b += red[w];
-        base_s = b;
-        if (blockIdx.x == 0) {
-            uint64_t t = 0;
-            for (uint32_t i = 0; i < gridDim.x; ++i) t += __ldcg(W.partials + i);
-            if (t > W.cap) atomicOr(W.status, kStatusTrunc);
-        }
+        base_s = blockIdx.x == 0 ? 0 : b;
+        if (blockIdx.x == 0 && b > W.cap) atomicOr(W.status, kStatusTrunc);
     }
     __syncthreads();
     uint64_t base = base_s;
@@ -832,6 +830,13 @@ cudaError_t launch_scan(int mode, int kind, uint32_t grid, size_t smem, cudaStre
 int scan_occupancy(int mode, int kind, uint32_t m, size_t smem) {
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pick(mode, kind, m), kThreads, smem) != cudaSuccess)
+        return 0;
+    return nb;
+}
+
+int bitmap_write_occupancy() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bitmap_write_kernel, kWriteThreads, 0) != cudaSuccess)
         return 0;
     return nb;
 }

@@ -229,6 +229,36 @@ def test_report_truncation(torch, ctx, report_mode):
     assert sm.sm_sync(ctx) == sm.SM_OK   # the status was cleared
 
 
+@pytest.mark.parametrize("kind", [64, 4])
+def test_report_clustered_matches(torch, ctx, kind, report_mode):
+    """Warp-tiles whose matches are many or spread over many lanes next to
+    warp-tiles with few: runs of one symbol and copies of the pattern every
+    64 or 96 starts planted into a sparse background, so that the second
+    pass meets slots in list form with few and with many entries and in
+    bitmap form within one round of 32 warp-tiles, and rounds above and
+    below its position-buffer size."""
+    n = 40 * TILE + 999
+    t = synth.text(kind, n, seed=0, stream=23).copy()
+    sym = t[0]
+    ws = 2048                                        # starts per warp-tile
+    t[3 * ws + 100:3 * ws + 100 + 70] = sym          # one warp-tile, 69+ matches of sym sym
+    for j in range(20):                              # 20 matches on 20 lanes of one warp-tile
+        t[9 * ws + 96 * j:9 * ws + 96 * j + 2] = sym
+    for j in range(32):                              # every lane of one warp-tile: bitmap form
+        t[17 * ws + 64 * j + 5:17 * ws + 64 * j + 7] = sym
+    t[200 * ws:200 * ws + 3000] = sym                # a round with more than the buffer holds
+    p = bytes([sym, sym])
+    hist = oracle.histogram(t)
+    for off in (0, 7):
+        text = to_dev(torch, t, off)
+        want_pos, want = oracle.naive_report(p, t)
+        for kw in ({}, {"hist": hist, "pi": oracle.order_freq(p, hist)}):
+            pos, c, st = gpu_report(ctx, text, p, want, **kw)
+            assert st == sm.SM_OK and c == want and np.array_equal(pos, want_pos), (kind, off)
+        pos, c, st = gpu_report(ctx, text, p, want - 5, hist=hist)
+        assert st == sm.SM_ETRUNC and c == want and np.array_equal(pos, want_pos[:want - 5])
+
+
 def test_bounded_wait_reports_timeout(torch, ctx):
     # The test hook leaves tile 0's copy unissued: its bounded wait must expire,
     # the kernel must return, and the context must stay usable.

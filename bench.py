@@ -63,8 +63,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched-counting leg (256 MiB Markov text, 4096 patterns; on by default)")
     ap.add_argument("--batch-only", action="store_true", help="measure only the batched counting")
-    ap.add_argument("--serve", action="store_true",
-                    help="also measure the serving loop (4 GiB resident text, Poisson arrivals)")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="skip the serving leg (4 GiB resident text, Poisson arrivals; on by default)")
     ap.add_argument("--serve-only", action="store_true", help="measure only the serving loop")
     ap.add_argument("--no-latency", action="store_true",
                     help="skip the single-search latency leg (1 MiB ACGT text, m = 8; on by default)")
@@ -1036,7 +1036,7 @@ def main():
                 "sweep": res["detail"]}
         if not args.no_batch and world == 1:
             line["batch"] = run_batch(args, local)
-        if args.serve and world == 1:
+        if not args.no_serve and world == 1:
             line["serving"] = run_serve(args, local)
         if args.multi and world == 1:
             line["multi"] = run_multi(args, local)

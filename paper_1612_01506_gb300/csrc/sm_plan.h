@@ -30,6 +30,15 @@ namespace smk {
 // bits 13 + 2D .. 14 + 2D the number (0..3) of its other compares of class D.
 constexpr uint32_t kPlanMaxPeel = 16;   // largest r the cost model chooses
 constexpr uint32_t kPlanCandidates = 64;
+constexpr uint32_t kPlanMaxM = 4096;    // longest pattern planned (the library's SM_MAX_M)
+constexpr uint32_t kPlanWindows = 4;    // windows whose aligned compares join the greedy's pool
+
+// A set of compare indices below kPlanMaxM (positions in the order pi).
+struct PlanSet {
+    uint64_t w[kPlanMaxM / 64] = {};
+    bool has(uint32_t j) const { return (w[j >> 6] >> (j & 63u)) & 1u; }
+    void add(uint32_t j) { w[j >> 6] |= 1ull << (j & 63u); }
+};
 
 // Window groups a pattern of length m can have: e < 16 + m, so E <= (14 + m) / 16.
 constexpr uint32_t max_groups_for(uint32_t m) { return (14 + m) / 16 + 1; }
@@ -46,11 +55,11 @@ struct PlanCosts {
     double round = 350, iter = 450, iter_per_lane = 15;
 };
 
-// Modelled cost of peeling the set sel[0..k) (indices below 64; inmask has
-// their bits): the dense phase, then the zero test, the compaction and the
-// sparse rounds, which continue with the other compares in the order pi.
+// Modelled cost of peeling the set sel[0..k) (in: the same indices as a
+// set): the dense phase, then the zero test, the compaction and the sparse
+// rounds, which continue with the other compares in the order pi.
 inline double plan_cost(const uint32_t* v, uint32_t m, const double* freq, const uint32_t* sel, uint32_t k,
-                        uint64_t inmask) {
+                        const PlanSet& in) {
     const PlanCosts C;
     double cost = C.base, alive = 1.0;
     for (uint32_t a = 0; a < k; ++a) {
@@ -72,7 +81,7 @@ inline double plan_cost(const uint32_t* v, uint32_t m, const double* freq, const
     double a = alive;
     uint32_t iters = 0, i = 0;
     auto next = [&]() -> int64_t {
-        while (i < m && i < 64 && ((inmask >> i) & 1u)) ++i;
+        while (i < m && in.has(i)) ++i;
         return i < m ? (int64_t)i++ : -1;
     };
     while (iters < 64) {
@@ -98,7 +107,7 @@ inline double plan_cost(const uint32_t* v, uint32_t m, const double* freq, const
 // max_groups; *ng = number of groups.
 inline uint32_t plan_dense(const uint32_t* v, uint32_t m, const double* freq, uint32_t r_fixed, uint32_t* qc,
                            uint32_t* groups, uint32_t max_groups, uint32_t* ng) {
-    uint32_t sel[kPlanCandidates];
+    uint32_t sel[kPlanMaxPeel > kPlanCandidates ? kPlanMaxPeel : kPlanCandidates];
     uint32_t k = 0;
     bool implicit = false;   // a long forced peel: the first r compares of pi
     if (r_fixed || !freq) {
@@ -114,37 +123,82 @@ inline uint32_t plan_dense(const uint32_t* v, uint32_t m, const double* freq, ui
         double best = 1e300;
         uint32_t cand[kPlanMaxPeel];
         // prefixes of pi
-        for (uint32_t j = 0; j < top; ++j) cand[j] = j;
+        PlanSet in;
         for (uint32_t r = 1; r <= top; ++r) {
-            const double c = plan_cost(v, m, freq, cand, r, (r < 64 ? (1ull << r) : 0ull) - 1ull);
+            cand[r - 1] = r - 1;
+            in.add(r - 1);
+            const double c = plan_cost(v, m, freq, cand, r, in);
             if (c < best) {
                 best = c;
                 k = r;
                 for (uint32_t a = 0; a < r; ++a) sel[a] = cand[a];
             }
         }
-        // prefixes of the greedy order over the kPlanCandidates rarest
-        const uint32_t pool = m < kPlanCandidates ? m : kPlanCandidates;
-        uint64_t inmask = 0;
+        // prefixes of the greedy order by information per modelled cost over
+        // a pool: the kPlanCandidates rarest compares, the aligned compares
+        // of the kPlanWindows windows whose aligned compares carry the most
+        // information, and every compare of a window already loaded. On
+        // texts whose symbols are about equally frequent the rarest compares
+        // of a long pattern are spread over many windows, while one window's
+        // aligned compares cost one load and no shifts.
+        constexpr uint32_t kW = max_groups_for(kPlanMaxM);
+        const uint32_t nwin = max_groups_for(m);
+        uint16_t by_win[kW][16];   // compares of each window (j in the order pi), long patterns
+        uint8_t nby[kW];
+        if (m > kPlanCandidates) {
+            for (uint32_t E = 0; E < nwin; ++E) nby[E] = 0;
+            for (uint32_t j = 0; j < m; ++j) {
+                const uint32_t E = group_e(v[j]);
+                by_win[E][nby[E]++] = (uint16_t)j;
+            }
+        }
+        uint32_t pool[kPlanCandidates + 4 * kPlanWindows], np = 0;
+        const uint32_t nrare = m < kPlanCandidates ? m : kPlanCandidates;
+        for (uint32_t j = 0; j < nrare; ++j) pool[np++] = j;
+        if (m > kPlanCandidates) {
+            double wsum[kW];
+            for (uint32_t E = 0; E < nwin; ++E) {
+                wsum[E] = 0.0;
+                for (uint32_t t = 0; t < nby[E]; ++t)
+                    if (aligned(v[by_win[E][t]])) wsum[E] += -std::log(std::fmax(freq[by_win[E][t]], 1e-300));
+            }
+            for (uint32_t t = 0; t < kPlanWindows; ++t) {
+                int64_t pick = -1;
+                for (uint32_t E = 0; E < nwin; ++E)
+                    if (wsum[E] > 0.0 && (pick < 0 || wsum[E] > wsum[pick])) pick = E;
+                if (pick < 0) break;
+                for (uint32_t u = 0; u < nby[pick]; ++u) {
+                    const uint32_t j = by_win[pick][u];
+                    if (j >= kPlanCandidates && aligned(v[j])) pool[np++] = j;
+                }
+                wsum[pick] = 0.0;
+            }
+        }
+        PlanSet inmask;
         uint32_t wins[kPlanMaxPeel], nw = 0;   // windows of the compares taken so far
-        double info[kPlanCandidates];
-        for (uint32_t j = 0; j < pool; ++j) info[j] = -std::log(std::fmax(freq[j], 1e-300));
         for (uint32_t r = 1; r <= top; ++r) {
             double best_gain = -1.0;
             uint32_t pick = 0;
-            for (uint32_t j = 0; j < pool; ++j) {
-                if ((inmask >> j) & 1u) continue;
-                bool loaded = false;
-                for (uint32_t w = 0; w < nw; ++w) loaded = loaded || wins[w] == group_e(v[j]);
+            auto consider = [&](uint32_t j, bool loaded) {
+                if (inmask.has(j)) return;
                 const double cost = (loaded ? 0.0 : C.window) + (aligned(v[j]) ? C.cmp_aligned : C.cmp_shifted);
-                const double gain = info[j] / cost;
+                const double gain = -std::log(std::fmax(freq[j], 1e-300)) / cost;
                 if (gain > best_gain) {
                     best_gain = gain;
                     pick = j;
                 }
+            };
+            for (uint32_t p = 0; p < np; ++p) {
+                bool loaded = false;
+                for (uint32_t w = 0; w < nw; ++w) loaded = loaded || wins[w] == group_e(v[pool[p]]);
+                consider(pool[p], loaded);
             }
+            if (m > kPlanCandidates)   // (shorter patterns have every compare in the pool)
+                for (uint32_t w = 0; w < nw; ++w)
+                    for (uint32_t u = 0; u < nby[wins[w]]; ++u) consider(by_win[wins[w]][u], true);
+            if (best_gain < 0.0) break;   // every candidate is taken
             cand[r - 1] = pick;
-            inmask |= 1ull << pick;
+            inmask.add(pick);
             bool known = false;
             for (uint32_t w = 0; w < nw; ++w) known = known || wins[w] == group_e(v[pick]);
             if (!known) wins[nw++] = group_e(v[pick]);
@@ -185,11 +239,11 @@ inline uint32_t plan_dense(const uint32_t* v, uint32_t m, const double* freq, ui
         if (g >= max_groups) return 0;
         groups[g++] = desc;
     }
-    // the rest in the order pi (sel holds indices below kPlanCandidates = 64)
-    uint64_t taken = 0;
-    for (uint32_t a = 0; a < r && !implicit; ++a) taken |= 1ull << sel[a];
+    // the rest in the order pi
+    PlanSet taken;
+    for (uint32_t a = 0; a < r && !implicit; ++a) taken.add(sel[a]);
     for (uint32_t j = 0; j < m; ++j) {
-        const bool in = implicit ? j < r : (j < 64 && ((taken >> j) & 1u));
+        const bool in = implicit ? j < r : taken.has(j);
         if (!in) qc[o++] = v[j];
     }
     *ng = g;

@@ -215,14 +215,40 @@ class Server:
     def _run_alone(self, q: Query):
         """An arrival at an idle server: one single-pattern count over the
         whole text, planned under the text's own frequencies, as the query
-        would run alone."""
+        would run alone. A report query then waits for its count and, when
+        its position buffer is admitted, has its report enqueued right after
+        it on the same stream (the loop holds no other work); otherwise it
+        goes through the report queue."""
         slot = self.free_slots.pop()
         q.qid = slot
-        sm.sm_count(self.ctx, self.text, q.pattern, pi=sm.sm_order(q.pattern, self.hist), hist=self.hist,
-                    out=self.counters[slot:slot + 1], stream=self.stream)
+        pi = sm.sm_order(q.pattern, self.hist)
+        sm.sm_count(self.ctx, self.text, q.pattern, pi=pi, hist=self.hist, out=self.counters[slot:slot + 1],
+                    stream=self.stream)
         q.alone = True
-        self._finish([q])
         self.steps += 1
+        if q.kind != "report":
+            self._finish([q])
+            return
+        torch = self.torch
+        with torch.cuda.stream(self.stream):
+            self.host_counters[slot].copy_(self.counters[slot], non_blocking=True)
+        self.stream.synchronize()
+        q.count = int(self.host_counters[slot])
+        self.free_slots.append(slot)
+        need = max(q.count, 1) * 8
+        if self.report_wait or (need > self._room() and need > self._room(full=True)):
+            self.report_wait.append(q)
+            return
+        self.report_reserved += need
+        with torch.cuda.stream(self.stream):
+            pos = torch.empty(max(q.count, 1), dtype=torch.int64, device=self.dev)
+            cnt = torch.empty(1, dtype=torch.int64, device=self.dev)
+        sm.sm_report(self.ctx, self.text, q.pattern, q.count, pi=pi, out_pos=pos, out_count=cnt, stream=self.stream,
+                     hist=self.hist)
+        ev = torch.cuda.Event()
+        ev.record(self.stream)
+        q.positions = pos[: q.count]
+        self.reporting.append((ev, [q], need, False))
 
     def warm_up(self, patterns: list[bytes]):
         """Run a few queries through every path once (loads kernels, sizes buffers)."""
@@ -289,21 +315,29 @@ class Server:
             q.positions = pos[: q.count]
             self.reporting.append((ev, [q], need, False))
 
-    def _room(self) -> int:
+    def _room(self, full: bool = False) -> int:
         """Bytes a new report buffer may take now: what is left of the report
-        budget, and the device memory free for it -- the driver's free bytes
-        plus what torch's caching allocator holds unused, minus the reserve."""
+        budget, and the device memory free for it minus the reserve. The
+        quick figure counts only what the driver reports free (~10 us); the
+        full one adds what torch's caching allocator holds unused, whose
+        statistics cost ~0.1 ms a read -- a large part of a lone report's
+        latency -- so it is read only when the quick figure is too small
+        (the quick figure never exceeds the full one)."""
         torch = self.torch
         free, _ = torch.cuda.mem_get_info(self.dev)
-        cached = torch.cuda.memory_reserved(self.dev) - torch.cuda.memory_allocated(self.dev)
-        return min(self.report_budget - self.report_reserved, free + cached - self.memory_reserve)
+        if full:
+            free += torch.cuda.memory_reserved(self.dev) - torch.cuda.memory_allocated(self.dev)
+        return min(self.report_budget - self.report_reserved, free - self.memory_reserve)
 
     def _admit(self, q: Query, need: int, room: int) -> bool:
         """Whether the report at the head of the wait queue may go on: True
-        when it fits `room`; a report that never can (above the budget, or
-        above the free memory with no report in flight to give any back) is
-        answered with an error and taken off the queue (also True); False
-        when it has to wait for reports in flight."""
+        when it fits `room` (or the room read afresh); a report that never
+        can (above the budget, or above the free memory with no report in
+        flight to give any back) is answered with an error and taken off the
+        queue (also True); False when it has to wait for reports in flight."""
+        if need <= room:
+            return True
+        room = self._room(full=True)
         if need <= room:
             return True
         if need > self.report_budget or not self.report_reserved:

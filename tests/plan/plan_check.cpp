@@ -26,13 +26,17 @@ static int fail(const char* what, uint32_t m, uint32_t r) {
 // compares (one per word class at most) by class, then the others by class,
 // as the group descriptor counts them; qc must be a permutation of v.
 static int check_dense(std::mt19937_64& g) {
-    const uint32_t m = 1 + (uint32_t)(g() % 200);
+    // lengths up to 200, or up to 4096 (long patterns, where the greedy
+    // pool also takes aligned compares beyond the 64 rarest); frequencies
+    // spread out, or nearly equal (a uniform text)
+    const uint32_t m = 1 + (uint32_t)(g() % ((g() % 4 == 0) ? 4096 : 200));
     const uint32_t delta = (uint32_t)(g() % 16);
+    const bool flat = g() % 2 == 0;
     std::vector<uint32_t> v(m), qc(m), groups(max_groups_for(m));
     std::vector<double> freq(m);
     for (uint32_t j = 0; j < m; ++j) {
         v[j] = ((j + delta) << 8) | (uint32_t)(g() % 256);
-        freq[j] = 1.0 / (double)(1 + g() % 300);
+        freq[j] = flat ? 0.05 * (1.0 + 1e-3 * (double)(g() % 100)) : 1.0 / (double)(1 + g() % 300);
     }
     std::shuffle(v.begin(), v.end(), g);   // an order pi: positions in any order
     std::sort(freq.begin(), freq.end());  // rarest first

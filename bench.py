@@ -202,9 +202,9 @@ def make_workload(args, rank):
 
 
 def scan_traffic(n, record="scan_traffic.json"):
-    """DRAM bytes per launch (count) or per report (its kernels together) at
-    text size n from a committed ncu capture under profiles/, if the kernels'
-    sources are unchanged since (else None)."""
+    """DRAM bytes per count launch at text size n from a committed ncu
+    capture under profiles/, if the kernels' sources are unchanged since
+    (else None)."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", record)) as f:
@@ -217,6 +217,26 @@ def scan_traffic(n, record="scan_traffic.json"):
             return None
         per = sum(rec["dram_bytes_per_launch"]) / len(rec["dram_bytes_per_launch"])
         return round(per * n / rec["text_bytes"])
+    except (OSError, KeyError, ValueError, ZeroDivisionError):
+        return None
+
+
+def report_traffic_ratio(record="report_traffic.json"):
+    """DRAM bytes of a report's kernels over its algorithmic bytes n + 8 occ,
+    summed over the reports of a committed ncu capture under profiles/ (one
+    per (sigma, m) cell), if the sources it depends on are unchanged since
+    (else None)."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", record)) as f:
+            rec = json.load(f)
+        h = hashlib.sha256()
+        for src in rec["sources"]:
+            with open(os.path.join(ROOT, src), "rb") as g:
+                h.update(g.read())
+        if h.hexdigest() != rec["sources_sha256"]:
+            return None
+        return sum(c["dram_bytes"] for c in rec["cells"]) / sum(c["alg_bytes"] for c in rec["cells"])
     except (OSError, KeyError, ValueError, ZeroDivisionError):
         return None
 
@@ -374,10 +394,14 @@ def run_gpu(args, world, rank, local):
                         lambda k, m, j: args.n + 8 * occ[(k, m)][j])
     if roof_rep:
         roof_rep["bytes"] = "n + 8 * matches per report"
-        roof_rep["traffic"] = scan_traffic(args.n, "report_traffic.json")
-        if roof_rep["traffic"]:
+        # DRAM bytes per report: the captured ratio of traffic to n + 8 occ
+        # over one report per (sigma, m) cell, applied to this sweep's mean
+        ratio = report_traffic_ratio()
+        roof_rep["traffic"] = None
+        if ratio:
             mean_alg = statistics.mean(args.n + 8 * statistics.mean(occ[(k, m)]) for k in kinds for m in ms)
-            roof_rep["traffic_over_bytes"] = round(roof_rep["traffic"] / mean_alg, 4)
+            roof_rep["traffic"] = round(ratio * mean_alg)
+            roof_rep["traffic_over_bytes"] = round(ratio, 4)
 
     e2e = None
     if not args.no_e2e:

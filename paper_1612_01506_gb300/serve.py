@@ -15,7 +15,9 @@ least ``report_batch_min`` report queries wait, together with them in one
 batched report over the text (``sm_stepper_report``).
 
 A query that arrives while the server is idle runs at once as one
-single-pattern search over the whole text (``sm_count``), as it would alone.
+single-pattern search over the whole text (``sm_count``), as it would alone;
+so do up to ``burst_below`` arrivals while no batched query is in flight,
+one launch each (a batched pass pays off once several patterns share it).
 
 Every query's result is the same as when it runs alone (the tests check
 this against single calls and the CPU oracle).
@@ -153,6 +155,16 @@ class Server:
             self._run_alone(self.pending.popleft())
             self._poll()
             return
+        if not self.active and 0 < len(self.pending) <= self.burst_below and len(self.free_slots) >= len(self.pending):
+            # a few arrivals and no batched query in flight: one search each,
+            # back to back (one launch per pattern beats a batched pass over
+            # the text until several patterns share it)
+            single = []
+            while self.pending:
+                single.append(self._run_single(self.pending.popleft()))
+            self._finish(single)
+            self._poll()
+            return
         # admission: a free counter slot per query
         while self.pending and self.free_slots:
             q = self.pending.popleft()
@@ -211,6 +223,18 @@ class Server:
         ev = torch.cuda.Event()
         ev.record(self.stream)
         self.finishing.append((ev, finished, None))
+
+    def _run_single(self, q: Query) -> Query:
+        """Enqueue one single-pattern count of q over the whole text into a
+        counter slot (read back by _finish; a report query then goes through
+        the report queue)."""
+        slot = self.free_slots.pop()
+        q.qid = slot
+        sm.sm_count(self.ctx, self.text, q.pattern, pi=sm.sm_order(q.pattern, self.hist), hist=self.hist,
+                    out=self.counters[slot:slot + 1], stream=self.stream)
+        q.alone = True
+        self.steps += 1
+        return q
 
     def _run_alone(self, q: Query):
         """An arrival at an idle server: one single-pattern count over the

@@ -69,8 +69,8 @@ def parse():
     ap.add_argument("--no-latency", action="store_true",
                     help="skip the single-search latency leg (1 MiB ACGT text, m = 8; on by default)")
     ap.add_argument("--latency-only", action="store_true", help="measure only the single-search latency")
-    ap.add_argument("--multi", action="store_true",
-                    help="also measure counts and positions over 20,000 packed texts (~35 GB)")
+    ap.add_argument("--no-multi", action="store_true",
+                    help="skip the packed-texts leg (counts and positions over 20,000 texts, ~35 GB; on by default)")
     ap.add_argument("--multi-only", action="store_true", help="measure only the packed-texts batch")
     ap.add_argument("--multi-texts", type=int, default=20000)
     ap.add_argument("--tune-only", action="store_true",
@@ -1062,7 +1062,7 @@ def main():
             line["batch"] = run_batch(args, local)
         if not args.no_serve and world == 1:
             line["serving"] = run_serve(args, local)
-        if args.multi and world == 1:
+        if not args.no_multi and world == 1:
             line["multi"] = run_multi(args, local)
         if not args.no_latency and world == 1:
             line["latency"] = run_latency(args, local)

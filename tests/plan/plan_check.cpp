@@ -150,10 +150,37 @@ static int check_codes(std::mt19937_64& g) {
     return 0;
 }
 
+// Long patterns over a text whose symbols are about equally frequent: the
+// order pi (by frequency) scatters the pattern positions, but the peeled
+// compares must come from one 16-byte window, its aligned ones (one load and
+// no shifts), as for a short pattern.
+static int check_flat_long() {
+    std::mt19937_64 g(7);
+    for (uint32_t m : {128u, 1024u, 4096u}) {
+        std::vector<uint32_t> v(m), qc(m), groups(max_groups_for(m));
+        std::vector<double> freq(m);
+        std::vector<uint32_t> pos(m);
+        for (uint32_t j = 0; j < m; ++j) pos[j] = j;
+        std::shuffle(pos.begin(), pos.end(), g);
+        for (uint32_t j = 0; j < m; ++j) {
+            v[j] = (pos[j] << 8) | 65u;
+            freq[j] = 0.05 * (1.0 + 1e-4 * (double)j);   // rarest first, nearly equal
+        }
+        uint32_t ng = 0;
+        const uint32_t r = plan_dense(v.data(), m, freq.data(), 0, qc.data(), groups.data(),
+                                      (uint32_t)groups.size(), &ng);
+        if (r < 3 || ng != 1) return fail("flat long pattern: peel not taken from one window", m, r);
+        for (uint32_t a = 0; a < r; ++a)
+            if (((qc[a] >> 8) & 3u) != 0) return fail("flat long pattern: a shifted compare peeled", m, r);
+    }
+    return 0;
+}
+
 int main(int argc, char** argv) {
     const uint64_t seed = argc > 1 ? std::strtoull(argv[1], nullptr, 10) : 1;
     const int n = argc > 2 ? std::atoi(argv[2]) : 20000;
     std::mt19937_64 g(seed);
+    if (check_flat_long()) return 1;
     int checked = 0;
     for (int i = 0; i < n; ++i) {
         if (check_dense(g) || check_packed(g, 2) || check_packed(g, 1) || check_codes(g)) return 1;

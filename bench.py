@@ -84,7 +84,7 @@ def parse():
     ap.add_argument("--orders-kinds", default="markov95,20,4")
     ap.add_argument("--orders-ms", default=",".join(str(m) for m in range(4, 65, 4)))
     ap.add_argument("--orders-peels", default="0,2,3,5")
-    ap.add_argument("--serve-rates", default="200,1000,4000")
+    ap.add_argument("--serve-rates", default="100,200,500,1000,2000,4000")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--serve-chunk-mib", type=int, default=256, help="serving: text chunk per step (MiB)")
     ap.add_argument("--serve-report-batch-min", type=int, default=32,

@@ -16,8 +16,9 @@ batched report over the text (``sm_stepper_report``).
 
 A query that arrives while the server is idle runs at once as one
 single-pattern search over the whole text (``sm_count``), as it would alone;
-so do up to ``burst_below`` arrivals while no batched query is in flight,
-one launch each (a batched pass pays off once several patterns share it).
+so do arrivals while no batched query and at most ``burst_below`` single
+searches are in flight, one launch each (a batched pass pays off once
+several patterns share it).
 
 Every query's result is the same as when it runs alone (the tests check
 this against single calls and the CPU oracle).
@@ -155,10 +156,13 @@ class Server:
             self._run_alone(self.pending.popleft())
             self._poll()
             return
-        if not self.active and 0 < len(self.pending) <= self.burst_below and len(self.free_slots) >= len(self.pending):
-            # a few arrivals and no batched query in flight: one search each,
-            # back to back (one launch per pattern beats a batched pass over
-            # the text until several patterns share it)
+        singles = sum(1 for _, qs, _ in self.finishing for q in qs if q.alone)
+        if (not self.active and 0 < len(self.pending) and singles + len(self.pending) <= self.burst_below
+                and len(self.free_slots) >= len(self.pending)):
+            # a few arrivals, no batched query in flight and at most
+            # burst_below single searches: one search each, back to back (one
+            # launch per pattern beats a batched pass over the text until
+            # several patterns share it; beyond that the arrivals are batched)
             single = []
             while self.pending:
                 single.append(self._run_single(self.pending.popleft()))
@@ -434,9 +438,13 @@ class Server:
                     time.sleep(wait - 0.0003)
                 continue
             if not self.pending and not self.active and not self.report_wait and (self.finishing or self.reporting):
-                # only results in flight and nothing to step: wait for the oldest
-                # instead of polling (an arrival meanwhile joins right after)
-                (self.finishing or self.reporting)[0][0].synchronize()
+                # only results in flight and nothing to step: poll their events
+                # until one is done or the next arrival is due (blocking on the
+                # oldest count would hold back a report that ends first)
+                evs = [e[0] for e in self.finishing] + [e[0] for e in self.reporting]
+                due = order[i].arrival if i < len(order) else float("inf")
+                while not any(e.query() for e in evs) and self.now() < due:
+                    pass
             self.step()
             if max_steps is not None and self.steps >= max_steps:
                 break

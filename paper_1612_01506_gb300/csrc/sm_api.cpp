@@ -35,8 +35,12 @@ struct sm_ctx {
     size_t warp_counts_cap = 0;       // entries
     uint32_t* d_bitmaps = nullptr;    // report: per-(tile, warp) found bitmaps
     size_t bitmaps_cap = 0;           // words
-    uint2* d_tile_list = nullptr;     // rescanning report: tiles with matches, per range
-    size_t tile_list_cap = 0;         // entries
+    uint64_t* d_range_sums = nullptr; // rescanning report: matches per range of the write pass
+    size_t range_sums_cap = 0;        // entries
+    // d_warp_counts and d_range_sums are all zero (the rescanning report
+    // leaves them so); false after they were (re)allocated, after a
+    // tile-count pass wrote every count word, or after a failed launch
+    bool rescan_clean = false;
     uint32_t stages = 4;
     bool stages_fixed = false;        // set by SM_KNOB_STAGES; otherwise fewer stages may raise occupancy
     uint32_t grid_override = 0;
@@ -411,7 +415,7 @@ void sm_destroy(sm_ctx* c) {
     if (c->d_partials) cudaFree(c->d_partials);
     if (c->d_warp_counts) cudaFree(c->d_warp_counts);
     if (c->d_bitmaps) cudaFree(c->d_bitmaps);
-    if (c->d_tile_list) cudaFree(c->d_tile_list);
+    if (c->d_range_sums) cudaFree(c->d_range_sums);
     delete c;
 }
 
@@ -554,36 +558,63 @@ static sm_status search(sm_ctx* c, const uint8_t* d_text, uint64_t n, const uint
         st = grow(&c->d_partials, &c->partials_cap,
                   std::max<size_t>((size_t)std::max<uint64_t>(wranges, gr.grid), 256), "partials");
         if (st != SM_OK) return st;
+        const size_t cap_before = c->warp_counts_cap;
         st = grow(&c->d_warp_counts, &c->warp_counts_cap, (size_t)gr.ntiles * smk::kConsumerWarps,
                   "per-warp tile counts");
+        if (c->warp_counts_cap != cap_before) c->rescan_clean = false;
         if (st != SM_OK) return st;
         if (!rescan) {
             st = grow(&c->d_bitmaps, &c->bitmaps_cap, (size_t)gr.ntiles * smk::kConsumerWarps * smk::kBitmapWords,
                       "found bitmaps");
-            if (st != SM_OK) return st;
-        } else {
-            st = grow(&c->d_tile_list, &c->tile_list_cap, (size_t)gr.ntiles, "tile list");
             if (st != SM_OK) return st;
         }
     }
     smk::ScanArgs a = scan_args(c, d_text, n, m, pl, gr, d_count);
     cudaError_t e;
     if (rescan) {
-        // few tiles hold matches: count, noting the warp-tiles with matches,
-        // then scan those tiles again and write their positions
-        e = cudaMemsetAsync(c->d_warp_counts, 0, (size_t)gr.ntiles * smk::kConsumerWarps * sizeof(uint32_t), s);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+        // few tiles hold matches: count, noting the warp-tiles with matches
+        // and the matches per range of the write pass, then scan those tiles
+        // again and write their positions. Ranges of at most kWriteList
+        // tiles (the write pass lists a range's tiles in shared memory).
+        const uint64_t per_w = std::min<uint64_t>(gr.per_cta, smk::kWriteList);
+        const uint64_t nranges = (gr.ntiles + per_w - 1) / per_w;
+        const size_t rs_before = c->range_sums_cap;
+        st = grow(&c->d_range_sums, &c->range_sums_cap, (size_t)std::max<uint64_t>(nranges, 256), "range sums");
+        if (c->range_sums_cap != rs_before) c->rescan_clean = false;
+        if (st != SM_OK) return st;
+        // the write pass: its stages and the list, with one stage fewer as
+        // long as that keeps as many CTAs resident per SM as the first pass
+        auto wsmem_for = [&](uint32_t st) {
+            return smk::scan_smem_bytes(gr.stage_bytes, st, pl.kind) + smk::kWriteListBytes;
+        };
+        uint32_t wstages = gr.stages;
+        while (wstages > 2 && wsmem_for(wstages) > c->max_smem) --wstages;
+        const int occ1 = occupancy(c, mode1, pl.kind, m, gr.smem);
+        while (wstages > 2 && occupancy(c, smk::kModeWrite, pl.kind, m, wsmem_for(wstages)) < occ1) --wstages;
+        const size_t wsmem = wsmem_for(wstages);
+        if (wsmem > c->max_smem) return fail(SM_ENOTSUP, "pattern too long for shared memory");
+        if (!c->rescan_clean) {
+            e = cudaMemsetAsync(c->d_warp_counts, 0, c->warp_counts_cap * sizeof(uint32_t), s);
+            if (e == cudaSuccess) e = cudaMemsetAsync(c->d_range_sums, 0, c->range_sums_cap * sizeof(uint64_t), s);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+        }
+        c->rescan_clean = false;   // until both launches went in
+        a.range_sums = c->d_range_sums;
+        a.range_tiles = per_w;
         e = smk::launch_scan(mode1, pl.kind, gr.grid, gr.smem, s, a, pl.qc.data(), pl.groups.data());
         if (e != cudaSuccess) return cuda_fail(e, "scan launch");
-        e = smk::launch_range_sums(gr.grid, s, c->d_warp_counts, gr.ntiles, gr.per_cta, c->d_partials,
-                                   c->d_tile_list);
-        if (e != cudaSuccess) return cuda_fail(e, "range count launch");
         a.d_pos = d_pos;
         a.cap = cap;
-        a.tile_list = c->d_tile_list;
-        e = smk::launch_scan(smk::kModeWrite, pl.kind, gr.grid, gr.smem, s, a, pl.qc.data(), pl.groups.data());
-        return e == cudaSuccess ? SM_OK : cuda_fail(e, "report launch");
+        a.tiles_per_cta = per_w;
+        a.stages = wstages;
+        e = smk::launch_scan(smk::kModeWrite, pl.kind, (uint32_t)nranges, wsmem, s, a, pl.qc.data(),
+                             pl.groups.data());
+        if (e != cudaSuccess) return cuda_fail(e, "report launch");
+        c->rescan_clean = true;
+        return SM_OK;
     }
+    // the tile-count pass writes every count word of its tiles
+    if (report) c->rescan_clean = false;
     // a report with matches in many tiles: the tile-count pass (per-warp-tile
     // counts and found bits), the per-range counts, then the positions from
     // the found bits

@@ -72,7 +72,16 @@ struct ScanArgs {
     uint64_t* d_pos;         // report output
     uint64_t cap;            // report capacity
     uint64_t spin_ns;        // limit of every bounded wait, in ns
-    const uint2* tile_list;  // write mode: per range, its tiles with matches (range_sum_kernel) or null
+    // The rescanning report. Ranges of range_tiles tiles (the write mode's
+    // CTAs, at most kThreads tiles each): the sparse mode adds each nonzero
+    // per-(tile, warp) count into range_sums[tile / range_tiles]; the write
+    // mode takes its range's first rank from them and its tiles with matches
+    // from the count words, and leaves both arrays zero again (each CTA
+    // clears the count words it read, the last CTA the range sums). Null in
+    // the other reports: the write mode then takes the first ranks from
+    // partials (range_sum_kernel) and scans the count words as it goes.
+    uint64_t* range_sums;
+    uint64_t range_tiles;
 };
 
 struct HistArgs {
@@ -111,6 +120,12 @@ inline uint32_t packed_words_for(uint32_t stage_bytes, int kind = kKindPacked) {
 constexpr uint32_t kBitmapWords = kWarpStarts / 32;
 constexpr uint32_t kBitmapBytes = kConsumerWarps * kBitmapWords * 4;   // 2 KiB
 
+// The write mode with range sums lists its range's tiles with matches in
+// shared memory after the stages: per tile, its 8 warp offsets (16 bits
+// each), then (tile, matches).
+constexpr uint32_t kWriteList = kThreads;
+constexpr size_t kWriteListBytes = (size_t)kWriteList * 24;
+
 inline size_t scan_smem_bytes(uint32_t stage_bytes, uint32_t stages, int kind = kKindBytes, bool report = false) {
     const size_t mid = kind_packed(kind) ? (size_t)16 * packed_words_for(stage_bytes, kind)
                                          : kQueueBytes + (report ? kBitmapBytes : 0u);
@@ -146,9 +161,8 @@ constexpr int kWriteThreads = 32 * kConsumerWarps;
 cudaError_t launch_bitmap_write(uint32_t grid, cudaStream_t s, const WriteArgs& a);
 // Resident blocks per SM of the second pass.
 int bitmap_write_occupancy();
-// Between the passes: partials[b] = matches in tiles [b T, (b + 1) T), one block per range;
-// with tile_list (ntiles entries), also the list of each range's tiles with matches.
+// Between the passes: partials[b] = matches in tiles [b T, (b + 1) T), one block per range.
 cudaError_t launch_range_sums(uint32_t grid, cudaStream_t s, const uint32_t* warp_counts, uint64_t ntiles,
-                              uint64_t tiles_per_range, uint64_t* partials, uint2* tile_list = nullptr);
+                              uint64_t tiles_per_range, uint64_t* partials);
 
 }  // namespace smk

@@ -45,6 +45,13 @@ namespace {
 using namespace dev;
 
 
+// Warp w's first rank within its tile, from a write-list entry's eight
+// 16-bit warp offsets (a tile holds at most 16384 matches before warp 7).
+__device__ __forceinline__ uint32_t warp_offset(const uint4& wo, uint32_t w) {
+    const uint32_t x = w < 4 ? (w < 2 ? wo.x : wo.y) : (w < 6 ? wo.z : wo.w);
+    return (x >> (16u * (w & 1u))) & 0xFFFFu;
+}
+
 struct StageDesc {
     uint64_t tile;       // kEnd: no more tiles
     uint64_t offset;     // report: output offset of the tile's first match
@@ -71,6 +78,10 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
     uint32_t* sbms = reinterpret_cast<uint32_t*>(smem + kScanHeader + kQueueBytes);   // bytes, tile-count
     uint8_t* bufs = smem + kScanHeader +
                     (PACKED ? 16u * A.packed_words : kQueueBytes + (MODE == kModeTileCount ? kBitmapBytes : 0u));
+    // write mode with range sums: the range's tiles with matches, after the stages
+    uint4* wl_woff = reinterpret_cast<uint4*>(bufs + (size_t)A.stages * A.stage_bytes);   // [kWriteList]
+    uint2* wl_head = reinterpret_cast<uint2*>(wl_woff + kWriteList);                    // [kWriteList]
+    uint32_t* wl_n = reinterpret_cast<uint32_t*>(smem + 352);                            // [kConsumerWarps + 2]
 
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t SB = A.stage_bytes, S = A.stages, m = A.m, r = A.r, one = A.one;
@@ -84,6 +95,55 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
         }
         fence_mbar_init();
     }
+    if (MODE == kModeWrite) {
+        // first rank of the range: the counts of the earlier ranges, summed
+        // by all threads (block 0 sums every range instead, for the
+        // truncation flag); the producer adds up the warps' sums
+        const uint32_t upto = blockIdx.x == 0 ? gridDim.x : blockIdx.x;
+        const uint64_t* sums = A.range_sums ? A.range_sums : A.partials;
+        uint64_t v = 0;
+        for (uint32_t i = tid; i < upto; i += kThreads) v += __ldcg(sums + i);
+        v = warp_sum_u64(v);
+        if (lane == 0) red[warp] = v;
+        if (A.range_sums) {
+            // thread i: tile t_begin + i -> its matches and warp offsets; the
+            // tiles with matches are listed in order (warp ballots, then the
+            // warps' list lengths), and their count words cleared
+            const uint64_t tt = t_begin + tid;
+            uint32_t tot = 0;
+            uint4 wo = make_uint4(0u, 0u, 0u, 0u);
+            if (tt < t_end) {
+                uint4* src = reinterpret_cast<uint4*>(A.warp_counts + tt * kConsumerWarps);
+                const uint4 x = __ldcg(src), y = __ldcg(src + 1);
+                const uint32_t c[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
+                uint32_t o[8];
+#pragma unroll
+                for (int w = 0; w < kConsumerWarps; ++w) {
+                    o[w] = tot;
+                    tot += c[w] & kCountMask;
+                }
+                wo = make_uint4(o[0] | (o[1] << 16), o[2] | (o[3] << 16), o[4] | (o[5] << 16), o[6] | (o[7] << 16));
+                if (tot) {
+                    src[0] = make_uint4(0u, 0u, 0u, 0u);
+                    src[1] = make_uint4(0u, 0u, 0u, 0u);
+                }
+            }
+            const uint32_t bal = __ballot_sync(kFull, tot != 0u);
+            if (lane == 0) wl_n[warp] = __popc(bal);
+            __syncthreads();
+            uint32_t before = 0, all = 0;
+            for (int w = 0; w < kConsumerWarps + 1; ++w) {
+                before += w < (int)warp ? wl_n[w] : 0u;
+                all += wl_n[w];
+            }
+            if (tot) {
+                const uint32_t k = before + __popc(bal & ((1u << lane) - 1u));
+                wl_woff[k] = wo;
+                wl_head[k] = make_uint2((uint32_t)tt, tot);
+            }
+            if (tid == 0) wl_n[kConsumerWarps + 1] = all;
+        }
+    }
     __syncthreads();
 
     uint32_t my_count = 0;
@@ -91,17 +151,11 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
     if (warp == kConsumerWarps) {
         // ---------------------------------------------------------- producer
         uint64_t cursor = t_begin, running = 0;
-        uint2 lst = make_uint2(~0u, 0u);   // write mode with a tile list: 32 of its entries
         if (MODE == kModeWrite) {
             uint64_t b = 0;
-            for (uint32_t i = lane; i < blockIdx.x; i += 32) b += __ldcg(A.partials + i);
-            running = warp_sum_u64(b);
-            if (blockIdx.x == 0) {
-                uint64_t t = 0;
-                for (uint32_t i = lane; i < gridDim.x; i += 32) t += __ldcg(A.partials + i);
-                t = warp_sum_u64(t);
-                if (lane == 0 && t > A.cap) atomicOr(A.status, kStatusTrunc);
-            }
+            for (int w = 0; w < kConsumerWarps + 1; ++w) b += red[w];
+            running = blockIdx.x == 0 ? 0 : b;
+            if (blockIdx.x == 0 && lane == 0 && b > A.cap) atomicOr(A.status, kStatusTrunc);
         }
         uint32_t issued = 0;
         // counting modes: the claim of the next tile is in flight while the
@@ -125,23 +179,15 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
                     tile = t;
                     if (lane == 0) claim = atomicAdd(A.tile_next, 1ull);
                 }
-            } else if (A.tile_list) {
-                // next entry of the range's list of tiles with matches; the
-                // lanes hold 32 entries at a time
-                if (cursor < t_end) {
-                    const uint32_t i = (uint32_t)(cursor - t_begin);
-                    if ((i & 31u) == 0) {
-                        const uint64_t x = cursor + lane;
-                        lst = x < t_end ? __ldcg(A.tile_list + x) : make_uint2(~0u, 0u);
-                    }
-                    const uint32_t tt = __shfl_sync(kFull, lst.x, i & 31u);
-                    if (tt != ~0u) {
-                        tile = tt;
-                        tcount = __shfl_sync(kFull, lst.y, i & 31u);
-                        ++cursor;
-                    } else {
-                        cursor = t_end;
-                    }
+            } else if (A.range_sums) {
+                // next entry of the range's list of tiles with matches
+                // (cursor counts the entries taken)
+                const uint32_t i = (uint32_t)(cursor - t_begin);
+                if (i < wl_n[kConsumerWarps + 1]) {   // the list's length
+                    const uint2 h = wl_head[i];
+                    tile = h.x;
+                    tcount = h.y;
+                    ++cursor;
                 }
             } else {
                 // next tile with matches; lanes look at 4 tiles x 8 warp counts per step
@@ -207,7 +253,7 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
         constexpr uint32_t UB = BIN ? 32u : 16u;    // stage bytes per packed word
         const uint32_t units = SB / UB, b1 = A.b1, b2 = A.b2, gather = A.gather, PW = A.packed_words;
         const uint32_t u0 = warp * (kWarpStarts / UB) + lane;
-        for (uint32_t s = 0, phase = 0, t = 0;; ++t) {
+        for (uint32_t s = 0, phase = 0, t = 0;; ++t) {   // round t: list entries 2t, 2t + 1 (write mode)
             uint32_t* pw[2] = {pbuf + (t & 1u) * 2u * PW, pbuf + (t & 1u) * 2u * PW + PW};
             StageDesc d[2] = {{kEnd, 0}, {kEnd, 0}};
             bool ok = true;
@@ -257,9 +303,13 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
 #pragma unroll
                 for (int k = 0; k < 2; ++k)
                     if (k == 0 || two) {
-                        const uint32_t cw =
-                            lane < warp ? __ldcg(A.warp_counts + d[k].tile * kConsumerWarps + lane) & kCountMask : 0u;
-                        out[k] = d[k].offset + warp_sum_u32(cw);
+                        if (A.range_sums) {
+                            out[k] = d[k].offset + warp_offset(wl_woff[2 * t + k], warp);
+                        } else {
+                            const uint32_t cw = lane < warp
+                                ? __ldcg(A.warp_counts + d[k].tile * kConsumerWarps + lane) & kCountMask : 0u;
+                            out[k] = d[k].offset + warp_sum_u32(cw);
+                        }
                     }
             }
             const uint32_t* const pk[2] = {pw[0], two ? pw[1] : pw[0]};
@@ -283,8 +333,12 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
                 for (int k = 0; k < 2; ++k) {
                     if (k == 1 && !two) break;
                     const uint32_t wsum = warp_sum_u32(k == 0 ? c.x : c.y);
-                    if (lane == 0 && (MODE == kModeTileCount || wsum))
+                    if (lane == 0 && (MODE == kModeTileCount || wsum)) {
                         A.warp_counts[d[k].tile * kConsumerWarps + warp] = wsum | (ent[k] << 16);
+                        if (MODE == kModeSparse && A.range_sums)
+                            atomicAdd(reinterpret_cast<unsigned long long*>(A.range_sums + d[k].tile / A.range_tiles),
+                                      (unsigned long long)wsum);
+                    }
                 }
             }
             my_count += c.x + c.y;
@@ -297,7 +351,7 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
         uint32_t* q = queues + warp * kQueueCap;
         const uint32_t c0 = warp * (kWarpStarts / 16) + lane;   // lane's first 16-byte chunk in the tile
         const uint32_t wq = warp * (kWarpStarts / 4);           // warp's first word in the tile
-        for (uint32_t s = 0, phase = 0;; ) {
+        for (uint32_t s = 0, phase = 0, li = 0;; ++li) {   // li: the tile's list entry (write mode)
             const bool ok = __all_sync(kFull, wait_bounded(&full[s], phase, A.spin_ns));
             if (!ok) {
                 if (lane == 0) atomicOr(A.status, kStatusTimeout);
@@ -312,9 +366,13 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
 
             uint64_t out = 0;
             if (MODE == kModeWrite) {
-                const uint32_t cw =
-                    lane < warp ? __ldcg(A.warp_counts + d.tile * kConsumerWarps + lane) & kCountMask : 0u;
-                out = d.offset + warp_sum_u32(cw);
+                if (A.range_sums) {
+                    out = d.offset + warp_offset(wl_woff[li], warp);
+                } else {
+                    const uint32_t cw =
+                        lane < warp ? __ldcg(A.warp_counts + d.tile * kConsumerWarps + lane) & kCountMask : 0u;
+                    out = d.offset + warp_sum_u32(cw);
+                }
             }
             uint32_t* bm = MODE == kModeTileCount && A.bitmaps
                                ? A.bitmaps + (d.tile * kConsumerWarps + warp) * kBitmapWords : nullptr;
@@ -329,7 +387,12 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
             } else if (MODE == kModeSparse) {
                 if (__any_sync(kFull, tile_count != 0u)) {
                     const uint32_t wsum = warp_sum_u32(tile_count);
-                    if (lane == 0) A.warp_counts[d.tile * kConsumerWarps + warp] = wsum;
+                    if (lane == 0) {
+                        A.warp_counts[d.tile * kConsumerWarps + warp] = wsum;
+                        if (A.range_sums)
+                            atomicAdd(reinterpret_cast<unsigned long long*>(A.range_sums + d.tile / A.range_tiles),
+                                      (unsigned long long)wsum);
+                    }
                 }
             }
             my_count += tile_count;
@@ -342,7 +405,24 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
         }
     }
 
-    if (MODE == kModeWrite) return;
+    if (MODE == kModeWrite) {
+        if (A.range_sums) {
+            // every CTA has read the range sums: the last one clears them
+            __syncthreads();
+            if (tid == 0) {
+                __threadfence();
+                const uint32_t tk = atomicAdd(A.ticket, 1u);
+                *flag = (tk == gridDim.x - 1) ? 1u : 0u;
+            }
+            __syncthreads();
+            if (*flag) {
+                __threadfence();
+                for (uint32_t i = tid; i < gridDim.x; i += kThreads) A.range_sums[i] = 0ull;
+                if (tid == 0) *A.ticket = 0u;
+            }
+        }
+        return;
+    }
 
     // CTA total -> partials; the last CTA to finish writes the sum and
     // clears the ticket and the tile counter for the next launch. (A report
@@ -384,59 +464,24 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
 // counts of range b (tiles [b T, (b + 1) T), T = tiles_per_range) into
 // partials[b]. The tile-count pass writes only per-warp-tile counts; a
 // per-range atomic there put every warp of the GPU on the same few
-// addresses (tiles are claimed in order) and cost up to 2x the scan. With
-// tile_list (the rescanning report), the block also lists the range's tiles
-// with matches in order, (tile, matches) from tile_list[b T], ended by a
-// tile of ~0u when the list is shorter than the range.
+// addresses (tiles are claimed in order) and cost up to 2x the scan.
 __global__ void __launch_bounds__(kWriteThreads) range_sum_kernel(const uint32_t* __restrict__ warp_counts,
                                                                   uint64_t ntiles, uint64_t tiles_per_range,
-                                                                  uint64_t* __restrict__ partials,
-                                                                  uint2* __restrict__ tile_list) {
-    __shared__ uint32_t red[kWriteThreads / 32];
+                                                                  uint64_t* __restrict__ partials) {
     __shared__ uint64_t redl[kWriteThreads / 32];
-    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t tid = threadIdx.x, lane = tid & 31;
     const uint64_t t0 = (uint64_t)blockIdx.x * tiles_per_range;
     const uint64_t t1 = min(t0 + tiles_per_range, ntiles);
     uint64_t v = 0;
-    if (!tile_list) {
-        // a tile's 8 counts are two 16-byte words
-        const uint4* src = reinterpret_cast<const uint4*>(warp_counts + t0 * kConsumerWarps);
-        const uint64_t nv = t1 > t0 ? 2 * (t1 - t0) : 0;
-        for (uint64_t i = tid; i < nv; i += kWriteThreads) {
-            const uint4 x = __ldcg(src + i);
-            v += (uint64_t)(((x.x & kCountMask) + (x.y & kCountMask)) + ((x.z & kCountMask) + (x.w & kCountMask)));
-        }
-    } else {
-        // thread i: tile c + i of each step of kWriteThreads tiles; the tiles
-        // with matches are compacted in order (warp ballots, then the warps'
-        // counts through shared memory)
-        uint32_t listed = 0;
-        for (uint64_t c = t0; c < t1; c += kWriteThreads) {
-            const uint64_t t = c + tid;
-            uint32_t tot = 0;
-            if (t < t1) {
-                const uint4* src = reinterpret_cast<const uint4*>(warp_counts + t * kConsumerWarps);
-                const uint4 x = __ldcg(src), y = __ldcg(src + 1);
-                tot = ((x.x & kCountMask) + (x.y & kCountMask)) + ((x.z & kCountMask) + (x.w & kCountMask)) +
-                      ((y.x & kCountMask) + (y.y & kCountMask)) + ((y.z & kCountMask) + (y.w & kCountMask));
-            }
-            v += tot;
-            const uint32_t bal = __ballot_sync(kFull, tot != 0u);
-            if (lane == 0) red[warp] = __popc(bal);
-            __syncthreads();
-            uint32_t before = listed, all = 0;
-            for (uint32_t w = 0; w < kWriteThreads / 32; ++w) {
-                before += w < warp ? red[w] : 0u;
-                all += red[w];
-            }
-            if (tot) tile_list[t0 + before + __popc(bal & ((1u << lane) - 1u))] = make_uint2((uint32_t)t, tot);
-            listed += all;
-            __syncthreads();   // red is rewritten by the next step
-        }
-        if (tid == 0 && t0 + listed < t1) tile_list[t0 + listed] = make_uint2(~0u, 0u);
+    // a tile's 8 counts are two 16-byte words
+    const uint4* src = reinterpret_cast<const uint4*>(warp_counts + t0 * kConsumerWarps);
+    const uint64_t nv = t1 > t0 ? 2 * (t1 - t0) : 0;
+    for (uint64_t i = tid; i < nv; i += kWriteThreads) {
+        const uint4 x = __ldcg(src + i);
+        v += (uint64_t)(((x.x & kCountMask) + (x.y & kCountMask)) + ((x.z & kCountMask) + (x.w & kCountMask)));
     }
     v = warp_sum_u64(v);
-    if (lane == 0) redl[warp] = v;
+    if (lane == 0) redl[tid >> 5] = v;
     __syncthreads();
     if (tid == 0) {
         uint64_t t = 0;
@@ -853,8 +898,8 @@ cudaError_t scan_prepare(size_t max_smem) {
 }
 
 cudaError_t launch_range_sums(uint32_t grid, cudaStream_t s, const uint32_t* warp_counts, uint64_t ntiles,
-                              uint64_t tiles_per_range, uint64_t* partials, uint2* tile_list) {
-    range_sum_kernel<<<grid, kWriteThreads, 0, s>>>(warp_counts, ntiles, tiles_per_range, partials, tile_list);
+                              uint64_t tiles_per_range, uint64_t* partials) {
+    range_sum_kernel<<<grid, kWriteThreads, 0, s>>>(warp_counts, ntiles, tiles_per_range, partials);
     return cudaGetLastError();
 }
 

@@ -259,6 +259,59 @@ def test_report_clustered_matches(torch, ctx, kind, report_mode):
         assert st == sm.SM_ETRUNC and c == want and np.array_equal(pos, want_pos[:want - 5])
 
 
+def test_rescan_leaves_scratch_clear(torch, monkeypatch):
+    """The rescanning report leaves its per-warp-tile counts and per-range
+    sums zero for the next one (it clears what it read instead of zeroing
+    them before every report). A sequence on a fresh context that could
+    leave stale counts behind: back-to-back rescans, a larger text, a report
+    over found bits (which writes every count word), a truncated report, an
+    expired wait, and write-pass ranges that differ from the first pass's
+    CTAs (a small grid: ranges of at most 288 tiles)."""
+    c = sm.sm_create(0)
+    big = synth.text(20, 41 * TILE + 77, seed=0, stream=31)
+    small = synth.uniform(7 * TILE + 5, 2, seed=0, stream=32)
+    wide = synth.text(64, 300 * TILE + 11, seed=0, stream=34).copy()
+    r = np.random.default_rng(33)
+    pa, pb = (big[s:s + 3].tobytes() for s in r.integers(0, big.size - 3, size=2))
+    pw = wide[5:9].tobytes()
+    for s in (0, 150 * TILE, 287 * TILE + 3, 288 * TILE - 2, 289 * TILE, wide.size - 4):
+        wide[s:s + 4] = wide[5:9]                 # matches in the tiles around the range edges
+    tb, ts, tw = to_dev(torch, big, 3), to_dev(torch, small, 0), to_dev(torch, wide, 0)
+
+    def check(text, host, p, design, cap=None):
+        monkeypatch.setenv("SM_REPORT", design)
+        want_pos, want = oracle.naive_report(p, host)
+        pos, n, st = gpu_report(c, text, p, want if cap is None else cap)
+        k = want if cap is None else min(cap, want)
+        assert n == want and np.array_equal(pos, want_pos[:k]), (design, p)
+        assert st == (sm.SM_OK if k == want else sm.SM_ETRUNC)
+
+    check(ts, small, b"0110", "rescan")
+    check(tb, big, pa, "rescan")                  # the arrays grow
+    check(tb, big, pb, "rescan")
+    check(ts, small, b"01", "bits")               # every count word written
+    check(tb, big, pa, "rescan")
+    check(tb, big, big[:1].tobytes(), "rescan", cap=500)
+    check(tb, big, pb, "rescan")
+    sm.sm_set_knob(c, sm.SM_KNOB_SPIN_NS, 2_000_000)
+    sm.sm_set_knob(c, sm.SM_KNOB_TEST_SKIP_COPY, 1)
+    try:
+        monkeypatch.setenv("SM_REPORT", "rescan")
+        sm.sm_report(c, tb, pa, 1 << 16)
+        assert sm.sm_sync(c) == sm.SM_ETIMEOUT
+    finally:
+        sm.sm_set_knob(c, sm.SM_KNOB_TEST_SKIP_COPY, 0)
+        sm.sm_set_knob(c, sm.SM_KNOB_SPIN_NS, 1_000_000_000)
+    check(tb, big, pa, "rescan")
+    check(tb, big, pb, "rescan")
+    for grid in (1, 3, 0):                        # 300 tiles: ranges of 288 + 12, of 100, default
+        sm.sm_set_knob(c, sm.SM_KNOB_GRID, grid)
+        check(tw, wide, pw, "rescan")
+        check(tw, wide, pw, "rescan", cap=3)
+    check(tw, wide, pw, "bits")
+    check(tw, wide, pw, "rescan")
+
+
 def test_bounded_wait_reports_timeout(torch, ctx):
     # The test hook leaves tile 0's copy unissued: its bounded wait must expire,
     # the kernel must return, and the context must stay usable.

@@ -390,7 +390,8 @@ def run_gpu(args, world, rank, local):
     roof = roofline("count", "scan_kernel<count>", lambda k, m, j: args.n)
     if roof:
         roof["traffic"] = scan_traffic(args.n)
-    roof_rep = roofline("report", "report: scan_kernel<tile count> + range_sum_kernel + bitmap_write_kernel",
+    roof_rep = roofline("report", "report: scan_kernel<tile count> + range_sum_kernel + bitmap_write_kernel "
+                        "(found bits) or scan_kernel<sparse> + scan_kernel<write> (rescan)",
                         lambda k, m, j: args.n + 8 * occ[(k, m)][j])
     if roof_rep:
         roof_rep["bytes"] = "n + 8 * matches per report"

@@ -39,10 +39,12 @@ enum ScanMode : int {
     kModeTileCount = 1,  // as kModeCount, and per-(tile, warp) counts (and found bitmaps) for a
                          // report
     kModeWrite = 2,      // report: write ascending positions of tiles with matches; CTA b owns
-                         // tile range b (partials: per-range counts from launch_range_sums)
+                         // tile range b (its first rank from range_sums, else from the
+                         // per-range partials of launch_range_sums)
     kModeSparse = 3,     // as kModeCount, and the per-(tile, warp) counts that are not zero
-                         // (the array is zeroed first): the first pass of a report whose
-                         // matches fall in few tiles, which kModeWrite then scans again
+                         // and their per-range sums (both arrays zero on entry): the first
+                         // pass of a report whose matches fall in few tiles, which
+                         // kModeWrite then scans again
     kModes = 4
 };
 

@@ -425,8 +425,9 @@ __global__ void __launch_bounds__(kThreads, SMK_MIN_BLOCKS) scan_kernel(const __
     }
 
     // CTA total -> partials; the last CTA to finish writes the sum and
-    // clears the ticket and the tile counter for the next launch. (A report
-    // then overwrites the partials with per-range counts: range_sum_kernel.)
+    // clears the ticket and the tile counter for the next launch. (A
+    // found-bit report then overwrites the partials with per-range counts:
+    // range_sum_kernel.)
     const uint64_t ws = warp_sum_u64((uint64_t)my_count);
     if (lane == 0) red[warp] = ws;
     __threadfence();

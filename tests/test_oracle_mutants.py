@@ -3,7 +3,9 @@
 The mutated copies are compiled into a temporary folder on the CPU. This
 shows that the pins constrain the oracle: a dropped compare, a lost start, a
 reversed or shifted index, an off-by-one report, a broken histogram, a wrong
-tie order or a wrong fixed order is each caught.
+tie order, a wrong fixed order, a threaded split that loses the halo, a start
+or the offset of its positions, and a batch that searches the wrong text is
+each caught.
 """
 import os
 import subprocess
@@ -32,6 +34,14 @@ MUTANTS = {
                              "for (uint32_t r = 2; r < len; r += 3) out[k++] = pos[r - 1];   /* 2, 5, ...  */\n    for (uint32_t r = 3; r < len; r += 3) out[k++] = pos[r - 1];   /* 3, 6, ...  */"),
     "kmp_no_overlap": ("if (k == m) { ++c; k = fail[k - 1]; }", "if (k == m) { ++c; k = 0; }"),
     "hs_spaces_first": ("if (p[q] != 0x20) rest[nr++] = q;", "if (p[q] == 0x20) rest[nr++] = q;"),
+    "threads_no_halo": ("uint64_t len = j->s1 - j->s0 + j->m - 1;\n    j->count = j->s1",
+                        "uint64_t len = j->s1 - j->s0;\n    j->count = j->s1"),
+    "threads_positions_not_shifted": ("for (uint64_t i = 0; i < j->count && i < j->cap; ++i) j->pos[i] += j->s0;",
+                                      "for (uint64_t i = 0; i < j->count && i < j->cap; ++i) j->pos[i] += 0;"),
+    "threads_last_start_lost": ("jobs[k].s1 = starts * (uint64_t)(k + 1) / (uint64_t)nt;",
+                                "jobs[k].s1 = starts * (uint64_t)(k + 1) / (uint64_t)nt;\n"
+                                "        if (k + 1 == nt && jobs[k].s1 > jobs[k].s0) jobs[k].s1 -= 1;"),
+    "batch_first_text_only": ("const uint8_t* t = texts + text_off[x];", "const uint8_t* t = texts + text_off[0];"),
 }
 
 

@@ -584,8 +584,8 @@ static sm_status search(sm_ctx* c, const uint8_t* d_text, uint64_t n, const uint
         if (st != SM_OK) return st;
         // the write pass: its stages and the list, with one stage fewer as
         // long as that keeps as many CTAs resident per SM as the first pass
-        auto wsmem_for = [&](uint32_t st) {
-            return smk::scan_smem_bytes(gr.stage_bytes, st, pl.kind) + smk::kWriteListBytes;
+        auto wsmem_for = [&](uint32_t nst) {
+            return smk::scan_smem_bytes(gr.stage_bytes, nst, pl.kind) + smk::kWriteListBytes;
         };
         uint32_t wstages = gr.stages;
         while (wstages > 2 && wsmem_for(wstages) > c->max_smem) --wstages;
